@@ -1,0 +1,220 @@
+/*
+ * hsma.h -- C ABI of the GB300 HSMA pair-sum library (libhsma.so).
+ *
+ * The library evaluates the Harmonic Surface Mapping Algorithm (HSMA) of
+ * Liang, Yuan and Xu, "HSMA: An O(N) electrostatics package implemented in
+ * LAMMPS", for N point charges in
+ *   - a fully periodic box (HSMA3D; the sum of Sec. 2.1, Eq. 3), or
+ *   - a slab periodic in x and y between two planar dielectric interfaces
+ *     (HSMA2D; the image-charge sum of Sec. 2.1, Eq. 4).
+ * One evaluation runs the steps of Sec. 2.2 on one GPU:
+ *   near field  -- every particle against the images inside the auxiliary
+ *                  sphere B (periodic images; in 2D also reflection images);
+ *   check sums  -- the same images onto the monitoring points (and in 2D the
+ *                  DtN face grid) that feed the least-squares fit (Eq. 6);
+ *   fit + map   -- FP64 coefficients A_n^m of Eq. 5 and the Fibonacci surface
+ *                  charges on the sphere (Sec. 2.2, third step);
+ *   far field   -- the surface charges onto the particles;
+ *   assembly    -- E = 1/2 sum q_i Phi(r_i), F_i = -q_i grad Phi(r_i), and the
+ *                  per-atom potential (the outputs of Sec. 3.1).
+ *
+ * Units are Gaussian with eps_c = 1 (Sec. 2.1, Eq. 2) times the option
+ * "coulomb_prefactor" (default 1).
+ *
+ * Pointers.  Every array argument may be a host pointer or a CUDA device
+ * pointer of the current device; the library asks the CUDA runtime which.
+ * Arrays are plain C arrays of double: positions x are N*3 row-major
+ * (x0 y0 z0 x1 ...), charges q are N, forces are N*3 row-major, potential is N.
+ * The caller owns every array it passes.  hsma_eval copies the inputs before
+ * returning; hsma_submit copies them before returning, so the caller may
+ * reuse its buffers at once.  Results are written when hsma_eval returns
+ * HSMA_OK, or when hsma_poll returns HSMA_OK.  On any error the output arrays
+ * are left unspecified.
+ *
+ * Threads.  One handle must not be used by two host threads at once.  Calls
+ * on different handles are independent.
+ *
+ * Errors.  Every int-returning call returns HSMA_OK (0), HSMA_PENDING (1,
+ * hsma_poll only) or a negative HSMA_ERR_* code; hsma_last_error gives a
+ * one-line message for the last failing call on that handle.
+ */
+#ifndef HSMA_H
+#define HSMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HSMA_OK               0
+#define HSMA_PENDING          1
+#define HSMA_ERR_ARG        (-1)  /* bad argument: p < 1, M < (p+1)^2, |gamma| > 1,
+                                     N < 1, dims not 2 or 3, box <= 0, NULL pointer,
+                                     unknown option or ticket */
+#define HSMA_ERR_NOT_NEUTRAL (-2) /* |sum q| > 1e-10 sum |q| */
+#define HSMA_ERR_OUT_OF_SLAB (-3) /* 2D: some z not strictly inside (0, Lz) */
+#define HSMA_ERR_NOMEM      (-4)  /* a device or pinned-host allocation failed */
+#define HSMA_ERR_BUDGET     (-5)  /* serving: request larger than the HBM budget */
+#define HSMA_ERR_TIMEOUT    (-6)  /* a bounded device wait ran out */
+#define HSMA_ERR_CUDA       (-7)  /* any other CUDA runtime error */
+#define HSMA_ERR_NUMERIC    (-8)  /* the fit lost rank (degenerate geometry) */
+
+typedef struct hsma_ctx* hsma_t;
+
+/*
+ * hsma_create -- geometry-only preparation (the paper's "Init", Sec. 3.1).
+ *
+ * box:   Lx, Ly, Lz > 0.  3D: the periodic cell [0,Lx)x[0,Ly)x[0,Lz).
+ *        2D: periodic in x, y; charges must lie in 0 < z < Lz, with the
+ *        dielectric interfaces at z = 0 (bottom) and z = Lz (top).
+ * dims:  3 (HSMA3D) or 2 (HSMA2D).
+ * p:     harmonic order P of Eq. 5, >= 1; (p+1)^2 basis functions.
+ * M:     number of Fibonacci surface charges, >= (p+1)^2.
+ * gamma_top, gamma_bot: dielectric mismatches of the top and bottom media,
+ *        gamma = (eps_c - eps_out)/(eps_c + eps_out) in [-1, 1] (Sec. 2.1,
+ *        after Eq. 4).  Ignored when dims == 3.
+ * out:   receives the handle.
+ * Defaults (changeable with hsma_set_option before the first evaluation):
+ * lambda 1.3 (3D) / 1.6 (2D), n_monitor 2(p+1)^2 (Sec. 3.2), dtn_grid 80,
+ * precision 1 (FP32 pair arithmetic with compensated FP64 accumulation).
+ * The fit matrix is factored once (an SVD pseudo-inverse in FP64) at the
+ * first evaluation after a change, and reused by every evaluation.
+ * Errors: HSMA_ERR_ARG, HSMA_ERR_NOMEM, HSMA_ERR_CUDA.
+ */
+int hsma_create(const double box[3], int dims, int p, int M,
+                double gamma_top, double gamma_bot, hsma_t* out);
+
+/*
+ * hsma_set_option -- change one parameter (Sec. 3.2 lists the paper's set).
+ * Keys:
+ *   "lambda"            R_s = lambda * R_c, R_c = half the box diagonal; > 1.
+ *                       (lambda = 2.6 is the paper's lambda = 1.3 measured
+ *                       against the full diagonal.)
+ *   "n_monitor"         number of monitoring points N_m, >= (p+1)^2.
+ *   "precision"         0 = FP64 pair arithmetic, 1 = FP32 pair arithmetic
+ *                       with FP64-compensated accumulation (the paper's
+ *                       eps_tol switch of Sec. 3.2 picks FP64 below 1e-6).
+ *   "dtn_grid"          G, grid points per side on each 2D face (>= 4).
+ *   "coulomb_prefactor" multiplies energy, forces and potential.
+ *   "timing"            1 = record per-phase CUDA-event times (hsma_get_info).
+ *   "chunks"            source chunks per target tile of the near/check
+ *                       launch (0 = automatic).
+ * Errors: HSMA_ERR_ARG (unknown key or value out of range).
+ */
+int hsma_set_option(hsma_t h, const char* key, double value);
+
+/*
+ * hsma_set_stream -- run this handle's work on the given cudaStream_t
+ * (NULL = the library's own stream).  The stream must outlive its use.
+ */
+int hsma_set_stream(hsma_t h, void* stream);
+
+/*
+ * hsma_eval -- one full evaluation (the paper's "Compute", Sec. 3.1 / 2.2).
+ * x: N*3 positions, q: N charges (neutral to 1e-10 relative; the residual is
+ * removed as q_i -= sum q / N).  3D positions are wrapped into the box; in 2D
+ * x and y are wrapped and z must be inside (0, Lz).
+ * energy: 1 double (required).  forces: N*3 or NULL.
+ * Blocks until the results are written.
+ * Errors: HSMA_ERR_ARG, HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_OUT_OF_SLAB,
+ * HSMA_ERR_NOMEM, HSMA_ERR_NUMERIC, HSMA_ERR_TIMEOUT, HSMA_ERR_CUDA.
+ */
+int hsma_eval(hsma_t h, const double* x, const double* q, int64_t N,
+              double* energy, double* forces);
+
+/*
+ * hsma_eval_ex -- hsma_eval that also returns the per-atom potential
+ * Phi(r_i) (N doubles, prefactor applied) when potential is not NULL.
+ */
+int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
+                 double* energy, double* forces, double* potential);
+
+/*
+ * hsma_get_info -- one scalar about the handle or its last evaluation.
+ * Keys: "Rc", "Rs", "n_shifts", "n_check", "rank", "Ns" (images in B at the
+ * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
+ * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
+ * "tile_targets".
+ * Errors: HSMA_ERR_ARG for an unknown key.
+ */
+int hsma_get_info(hsma_t h, const char* key, double* value);
+
+/*
+ * hsma_get_array -- copy an intermediate of the last evaluation to host
+ * memory (for checking each step separately).  Names and lengths:
+ *   "check_points"  n_check*3  monitoring points, their wraps, 2D face grid
+ *   "check_phi"     n_check    Phi_B at the check points
+ *   "check_dz"      n_check    dPhi_B/dz at the check points
+ *   "coeffs"        (p+1)^2-1  A_n^m for n >= 1 in the basis (r/R_c)^n Y_nm
+ *   "surface_points" M*3       Fibonacci points on the sphere B
+ *   "surface_q"     M          surface charges Q_m
+ *   "grad"          N*3        grad Phi(r_i) (no prefactor)
+ * n is the capacity of out in doubles; fails with HSMA_ERR_ARG if too small.
+ */
+int hsma_get_array(hsma_t h, const char* name, double* out, int64_t n);
+
+/*
+ * hsma_geometry_array -- host-only (no GPU needed): build the geometry of a
+ * set-up exactly as hsma_create + options would, and copy one array of it:
+ *   "T"              M x nv  the composite map from the raw check vector v
+ *                    (3D: Phi_B at [monitoring points; wraps]; 2D: [Phi_B;
+ *                    dPhi_B/dz] at [monitoring points; wraps; top face;
+ *                    bottom face]) to the surface charges, row-major.  It is
+ *                    the fit of Sec. 2.2, Eq. 6 followed by the surface map.
+ *   "check_points"   n_check*3, "surface_points" M*3,
+ *   "shifts"         n_shift*5 (sx, sy, zs, zo, factor), identity first,
+ *   "sizes"          [n_check, nv, nA, rank, n_shift, Rc, Rs, Rs2].
+ * lam <= 0, n_monitor <= 0 or G <= 0 select the defaults.  n is the capacity
+ * of out in doubles.  Errors: HSMA_ERR_ARG, HSMA_ERR_NUMERIC.
+ */
+int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
+                        double gamma_bot, double lam, int n_monitor, int G,
+                        const char* name, double* out, int64_t n);
+
+/* hsma_destroy -- free every resource of the handle (NULL is allowed). */
+void hsma_destroy(hsma_t h);
+
+/* hsma_last_error -- message of the last failing call (never NULL). */
+const char* hsma_last_error(hsma_t h);
+
+/*
+ * Serving: continuous batching of independent HSMA3D requests (MD replicas,
+ * Monte Carlo trial states) on one GPU.
+ *
+ * hsma_server_create -- a request loop with at most `slots` requests on the
+ * device at once and `budget_bytes` of device memory for their state.
+ * precision as for hsma_set_option.  Requests that arrive while others run
+ * are admitted as slots and memory free up; their pair sums share launches.
+ * Each request's result is identical to an evaluation of it alone.
+ */
+int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* out);
+
+/*
+ * hsma_submit -- enqueue one 3D request (cubic or not: box[3]); non-blocking.
+ * Copies x and q before returning.  ticket receives the request id.
+ * Errors: HSMA_ERR_ARG, HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_BUDGET (the request
+ * alone exceeds the budget), HSMA_ERR_NOMEM.
+ */
+int hsma_submit(hsma_t server, const double* x, const double* q, int64_t N,
+                const double box[3], int p, int M, uint64_t* ticket);
+
+/*
+ * hsma_poll -- HSMA_PENDING while the request runs; HSMA_OK once energy (1
+ * double) and forces (N*3, or NULL) are written, after which the ticket is
+ * retired.  A negative code reports that request's failure.
+ */
+int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces);
+
+/*
+ * hsma_server_step -- let the request loop make progress from the calling
+ * thread (admit, launch one batch, retire finished requests).  Returns the
+ * number of requests still queued or running.  hsma_poll also advances it.
+ */
+int hsma_server_step(hsma_t server);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSMA_H */

@@ -1,0 +1,548 @@
+// C ABI of libhsma.so: handles, options, the evaluation pipeline (Sec. 2.2 of
+// the paper, in launch order) and diagnostics.  See include/hsma.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hsma.h"
+#include "api_internal.hpp"
+#include "geometry.hpp"
+#include "internal.hpp"
+
+using hsma::DevBuf;
+
+namespace hsma {
+
+int DevBuf::ensure(size_t bytes) {
+  if (bytes <= n) return 0;
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+  if (bytes == 0) return 0;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return -1;
+  }
+  n = bytes;
+  return 0;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Expected number of images in B, for planning only (the exact count is made
+// on the device).  3D: sphere volume over cell volume.  2D: per image layer,
+// the sphere's cross-section area at the layer centre over the cell area.
+double estimate_images(const Geometry& g, int64_t N) {
+  const double* L = g.par.box;
+  const double kPi = 3.14159265358979323846;
+  if (g.par.dims == 3) {
+    const double r = 4.0 * kPi / 3.0 * g.Rs * g.Rs * g.Rs / (L[0] * L[1] * L[2]);
+    return (double)N * std::min<double>((double)g.shifts.size(), std::max(1.0, r));
+  }
+  double tot = 0;
+  std::vector<double> zc;
+  for (const Shift& s : g.shifts)
+    if (s.sx == 0 && s.sy == 0) zc.push_back(s.zo);
+  for (double z : zc) tot += std::max(0.0, kPi * (g.Rs2 - z * z) / (L[0] * L[1]));
+  return (double)N * std::max(1.0, tot);
+}
+
+// Source chunks per target tile: the schedule has tiles*chunks equal-cost
+// items spread over `slots` resident CTAs; pick the count that fills the last
+// wave best while keeping chunks long enough to amortise their partials.
+int choose_chunks(int tiles, int slots, double n_src, int min_len) {
+  int best = 1;
+  double best_eff = -1;
+  for (int S = 1; S <= 512; ++S) {
+    if (S > 1 && n_src / S < min_len) break;
+    const long items = (long)tiles * S;
+    const long waves = (items + slots - 1) / slots;
+    const double eff = (double)items / (double)(waves * slots);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = S;
+    }
+  }
+  return best;
+}
+
+}  // namespace hsma
+
+using namespace hsma;
+
+static int fail(hsma_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+static int cuda_fail(hsma_ctx* h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? HSMA_ERR_NOMEM : HSMA_ERR_CUDA, m);
+}
+
+hsma_ctx::~hsma_ctx() {
+  for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
+                    &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
+                    &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
+                    &d_blke, &d_sc})
+    b->release();
+  if (h_sc) cudaFreeHost(h_sc);
+  for (int i = 0; i < hsma_ctx::kEvents; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+int hsma_ctx_init(hsma_ctx* h) {
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+  h->own_stream = true;
+  e = cudaMallocHost((void**)&h->h_sc, sizeof(DevScalars));
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMallocHost");
+  for (int i = 0; i < hsma_ctx::kEvents; ++i) {
+    e = cudaEventCreate(&h->ev[i]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+  }
+  if (h->d_sc.ensure(sizeof(DevScalars))) return fail(h, HSMA_ERR_NOMEM, "device scalars");
+  return HSMA_OK;
+}
+
+// Build and upload the geometry if an option changed since the last build.
+int ensure_geometry(hsma_ctx* h) {
+  if (!h->geo_dirty) return HSMA_OK;
+  std::string err;
+  int rc = build_geometry(h->gp, &h->geo, &err);
+  if (rc) return fail(h, rc, err);
+  const Geometry& g = h->geo;
+  std::vector<double> sh(g.shifts.size() * 5);
+  for (size_t i = 0; i < g.shifts.size(); ++i) {
+    sh[5 * i] = g.shifts[i].sx;
+    sh[5 * i + 1] = g.shifts[i].sy;
+    sh[5 * i + 2] = g.shifts[i].zs;
+    sh[5 * i + 3] = g.shifts[i].zo;
+    sh[5 * i + 4] = g.shifts[i].f;
+  }
+  struct Up { DevBuf* b; const void* src; size_t bytes; };
+  const Up ups[] = {
+      {&h->d_shifts, sh.data(), sh.size() * 8},
+      {&h->d_check, g.check_pts.data(), g.check_pts.size() * 8},
+      {&h->d_P, g.P.data(), g.P.size() * 8},
+      {&h->d_W, g.W.data(), g.W.size() * 8},
+      {&h->d_ysurf, g.ysurf.data(), g.ysurf.size() * 8},
+  };
+  for (const Up& u : ups) {
+    if (u.b->ensure(u.bytes)) return fail(h, HSMA_ERR_NOMEM, "geometry upload");
+    cudaError_t e = cudaMemcpyAsync(u.b->p, u.src, u.bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
+  }
+  const size_t M = g.par.M;
+  if (h->d_v.ensure((size_t)g.nv * 8) || h->d_A.ensure((size_t)g.nA * 8) ||
+      h->d_cphi.ensure((size_t)g.n_check * 8) || h->d_cdz.ensure((size_t)g.n_check * 8) ||
+      h->d_Q.ensure(M * 8) || h->d_s32.ensure(M * 16) || h->d_s64.ensure(M * 32))
+    return fail(h, HSMA_ERR_NOMEM, "geometry buffers");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
+  h->geo_dirty = false;
+  h->plan_N = -1;
+  return HSMA_OK;
+}
+
+// Launch plan and buffers for N particles.
+int ensure_plan(hsma_ctx* h, int64_t N) {
+  if (h->plan_N == N) return HSMA_OK;
+  const Geometry& g = h->geo;
+  const int prec = h->precision;
+  const int tpt = (prec == 0) ? 1 : h->tpt;
+  const int tile = pair_tile_targets(prec, tpt);
+  const int slots = pair_slots(prec, tpt);
+  h->n_tgt1 = (int)N + g.n_check;
+  h->tiles1 = (h->n_tgt1 + tile - 1) / tile;
+  h->ns_est = estimate_images(g, N);
+  h->chunks1 = h->chunks_opt > 0 ? h->chunks_opt
+                                  : choose_chunks(h->tiles1, slots, h->ns_est, prec == 0 ? 512 : 1024);
+  h->grid1 = (int)std::min<long>((long)h->tiles1 * h->chunks1, slots);
+  h->tiles2 = ((int)N + tile - 1) / tile;
+  h->chunks2 = choose_chunks(h->tiles2, slots, g.par.M, 256);
+  h->grid2 = (int)std::min<long>((long)h->tiles2 * h->chunks2, slots);
+  h->slots = slots;
+  const size_t n = (size_t)N, nt = (size_t)h->n_tgt1;
+  const size_t nblk = (n + 255) / 256;
+  const size_t simg = n * g.shifts.size();  // upper bound on images in B
+  bool bad = h->d_x.ensure(n * 24) || h->d_q.ensure(n * 8) || h->d_xc.ensure(n * 24) ||
+             h->d_cnt.ensure(n * 4) || h->d_blk.ensure(nblk * 4) || h->d_blkq.ensure(nblk * 8) ||
+             h->d_blkaq.ensure(nblk * 8) || h->d_forces.ensure(n * 24) || h->d_pot.ensure(n * 8) ||
+             h->d_grad.ensure(n * 24) || h->d_blke.ensure(nblk * 8) ||
+             h->d_part.ensure((size_t)h->chunks1 * 4 * nt * 8) ||
+             h->d_fpart.ensure((size_t)h->chunks2 * 4 * n * 8);
+  if (prec == 0)
+    bad = bad || h->d_src64.ensure(simg * 32) || h->d_tgt64.ensure(nt * 32);
+  else
+    bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16);
+  if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
+  h->plan_N = N;
+  return HSMA_OK;
+}
+
+// Enqueue one evaluation on h->stream; inputs already in d_x, d_q.
+int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
+  const Geometry& g = h->geo;
+  const int prec = h->precision;
+  const int tpt = (prec == 0) ? 1 : h->tpt;
+  cudaStream_t s = h->stream;
+  const bool tm = h->timing != 0;
+  if (tm) cudaEventRecord(h->ev[0], s);
+  cudaMemsetAsync(h->d_sc.p, 0, sizeof(DevScalars), s);
+  PrepArgs a;
+  a.x = (const double*)h->d_x.p;
+  a.q = (const double*)h->d_q.p;
+  a.N = (int)N;
+  a.dims = g.par.dims;
+  for (int d = 0; d < 3; ++d) a.L[d] = g.par.box[d];
+  a.Rs2 = g.Rs2;
+  a.shifts = (const double*)h->d_shifts.p;
+  a.n_shift = (int)g.shifts.size();
+  a.check_pts = (const double*)h->d_check.p;
+  a.n_check = g.n_check;
+  a.xc = (double*)h->d_xc.p;
+  a.cnt = (int*)h->d_cnt.p;
+  a.blk = (int*)h->d_blk.p;
+  a.blk_q = (double*)h->d_blkq.p;
+  a.blk_aq = (double*)h->d_blkaq.p;
+  a.sc = (DevScalars*)h->d_sc.p;
+  a.src32 = prec ? (float4*)h->d_src32.p : nullptr;
+  a.tgt32 = prec ? (float4*)h->d_tgt32.p : nullptr;
+  a.src64 = prec ? nullptr : (double4_32a*)h->d_src64.p;
+  a.tgt64 = prec ? nullptr : (double4_32a*)h->d_tgt64.p;
+  const int nblk = (int)((N + 255) / 256);
+  cudaError_t e = launch_prep(a, nblk, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "prep launch");
+  if (tm) cudaEventRecord(h->ev[1], s);
+
+  PairArgs p1;
+  p1.tgt = prec ? (const void*)h->d_tgt32.p : (const void*)h->d_tgt64.p;
+  p1.n_tgt = h->n_tgt1;
+  p1.src = prec ? (const void*)h->d_src32.p : (const void*)h->d_src64.p;
+  p1.n_src = 0;
+  p1.sc = (const DevScalars*)h->d_sc.p;
+  p1.n_diag = (int)N;
+  p1.n_tiles = h->tiles1;
+  p1.n_chunks = h->chunks1;
+  p1.part = (double*)h->d_part.p;
+  p1.ld = h->n_tgt1;
+  e = launch_pair(prec, tpt, p1, h->grid1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
+  if (tm) cudaEventRecord(h->ev[2], s);
+
+  e = launch_fit(g.par.dims, (const double*)h->d_part.p, h->chunks1, h->n_tgt1, (int)N, g.n_check,
+                 (const double*)h->d_P.p, g.nA, g.nv, (const double*)h->d_W.p, g.par.M,
+                 (const double*)h->d_ysurf.p, (double*)h->d_v.p, (double*)h->d_A.p,
+                 (double*)h->d_cphi.p, (double*)h->d_cdz.p, (double*)h->d_Q.p,
+                 prec ? (float4*)h->d_s32.p : nullptr, prec ? nullptr : (double4_32a*)h->d_s64.p, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "fit launch");
+  if (tm) cudaEventRecord(h->ev[3], s);
+
+  PairArgs p2;
+  p2.tgt = p1.tgt;
+  p2.n_tgt = (int)N;
+  p2.src = prec ? (const void*)h->d_s32.p : (const void*)h->d_s64.p;
+  p2.n_src = g.par.M;
+  p2.sc = nullptr;
+  p2.n_diag = 0;
+  p2.n_tiles = h->tiles2;
+  p2.n_chunks = h->chunks2;
+  p2.part = (double*)h->d_fpart.p;
+  p2.ld = (int)N;
+  e = launch_pair(prec, tpt, p2, h->grid2, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "far launch");
+  if (tm) cudaEventRecord(h->ev[4], s);
+
+  e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1, (const double*)h->d_fpart.p,
+                      h->chunks2, (int)N, (const double*)h->d_q.p, (int)N, h->pref,
+                      (DevScalars*)h->d_sc.p, forces_dev, pot_dev, (double*)h->d_grad.p,
+                      (double*)h->d_blke.p, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble launch");
+  if (tm) cudaEventRecord(h->ev[5], s);
+  e = cudaMemcpyAsync(h->h_sc, h->d_sc.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "result copy");
+  return HSMA_OK;
+}
+
+int finish_eval(hsma_ctx* h, double* energy) {
+  const DevScalars& r = *h->h_sc;
+  h->last_Ns = r.Ns;
+  if (h->timing) {
+    float t;
+    const int pairs[6][2] = {{0, 5}, {0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
+    for (int i = 0; i < 6; ++i) {
+      cudaEventElapsedTime(&t, h->ev[pairs[i][0]], h->ev[pairs[i][1]]);
+      h->times[i] = t;
+    }
+  }
+  if (r.flags & FLAG_OUT_OF_SLAB) return fail(h, HSMA_ERR_OUT_OF_SLAB, "some z outside (0, Lz)");
+  if (r.flags & FLAG_NOT_NEUTRAL) return fail(h, HSMA_ERR_NOT_NEUTRAL, "system not neutral");
+  if (r.flags & FLAG_TIMEOUT) return fail(h, HSMA_ERR_TIMEOUT, "device wait timed out");
+  if (energy) *energy = r.energy;
+  return HSMA_OK;
+}
+
+static int eval_impl(hsma_ctx* h, const double* x, const double* q, int64_t N, double* energy,
+                     double* forces, double* potential) {
+  if (!h) return HSMA_ERR_ARG;
+  if (h->is_server) return fail(h, HSMA_ERR_ARG, "handle is a server; use hsma_submit");
+  if (!x || !q || !energy) return fail(h, HSMA_ERR_ARG, "NULL x, q or energy");
+  if (N < 1 || N > (int64_t)1 << 28) return fail(h, HSMA_ERR_ARG, "N out of range");
+  int rc = ensure_geometry(h);
+  if (rc) return rc;
+  rc = ensure_plan(h, N);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemcpyAsync(h->d_x.p, x, (size_t)N * 24, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q.p, q, (size_t)N * 8, cudaMemcpyDefault, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
+  const bool fdev = forces && is_device_ptr(forces);
+  const bool pdev = potential && is_device_ptr(potential);
+  rc = enqueue_eval(h, N, fdev ? forces : (double*)h->d_forces.p, pdev ? potential : (double*)h->d_pot.p);
+  if (rc) return rc;
+  if (forces && !fdev) {
+    e = cudaMemcpyAsync(forces, h->d_forces.p, (size_t)N * 24, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force copy");
+  }
+  if (potential && !pdev) {
+    e = cudaMemcpyAsync(potential, h->d_pot.p, (size_t)N * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "potential copy");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "evaluation");
+  h->last_N = N;
+  return finish_eval(h, energy);
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int hsma_create(const double box[3], int dims, int p, int M, double gamma_top, double gamma_bot,
+                hsma_t* out) {
+  if (!out || !box) return HSMA_ERR_ARG;
+  *out = nullptr;
+  if (dims != 2 && dims != 3) return HSMA_ERR_ARG;
+  if (p < 1 || p > 40 || M < (p + 1) * (p + 1)) return HSMA_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0) || !std::isfinite(box[d])) return HSMA_ERR_ARG;
+  if (dims == 2 && (!(std::fabs(gamma_top) <= 1) || !(std::fabs(gamma_bot) <= 1))) return HSMA_ERR_ARG;
+  hsma_ctx* h = new (std::nothrow) hsma_ctx();
+  if (!h) return HSMA_ERR_NOMEM;
+  h->gp.dims = dims;
+  for (int d = 0; d < 3; ++d) h->gp.box[d] = box[d];
+  h->gp.p = p;
+  h->gp.M = M;
+  h->gp.lam = (dims == 3) ? 1.3 : 1.6;
+  h->gp.n_monitor = 2 * (p + 1) * (p + 1);
+  h->gp.gtop = (dims == 2) ? gamma_top : 0.0;
+  h->gp.gbot = (dims == 2) ? gamma_bot : 0.0;
+  h->gp.G = 80;
+  int rc = hsma_ctx_init(h);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return HSMA_OK;
+}
+
+int hsma_set_option(hsma_t h, const char* key, double v) {
+  if (!h || !key) return HSMA_ERR_ARG;
+  const std::string k(key);
+  if (k == "lambda") {
+    if (!(v > 1.0) || !std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "lambda must be > 1");
+    h->gp.lam = v;
+    h->geo_dirty = true;
+  } else if (k == "n_monitor") {
+    const int p = h->gp.p;
+    if (!(v >= (p + 1) * (p + 1)) || v > 1e6) return fail(h, HSMA_ERR_ARG, "n_monitor must be >= (p+1)^2");
+    h->gp.n_monitor = (int)v;
+    h->geo_dirty = true;
+  } else if (k == "precision") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "precision must be 0 or 1");
+    h->precision = (int)v;
+    h->plan_N = -1;
+  } else if (k == "dtn_grid") {
+    if (!(v >= 4) || v > 1024) return fail(h, HSMA_ERR_ARG, "dtn_grid must be in [4, 1024]");
+    h->gp.G = (int)v;
+    h->geo_dirty = true;
+  } else if (k == "coulomb_prefactor") {
+    if (!std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "prefactor must be finite");
+    h->pref = v;
+  } else if (k == "timing") {
+    h->timing = (v != 0);
+  } else if (k == "chunks") {
+    if (!(v >= 0) || v > 4096) return fail(h, HSMA_ERR_ARG, "chunks must be in [0, 4096]");
+    h->chunks_opt = (int)v;
+    h->plan_N = -1;
+  } else if (k == "targets_per_thread") {
+    if (v != 1 && v != 2 && v != 4) return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2 or 4");
+    h->tpt = (int)v;
+    h->plan_N = -1;
+  } else {
+    return fail(h, HSMA_ERR_ARG, "unknown option " + k);
+  }
+  return HSMA_OK;
+}
+
+int hsma_set_stream(hsma_t h, void* stream) {
+  if (!h) return HSMA_ERR_ARG;
+  if (stream) {
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->own_stream = false;
+    h->stream = (cudaStream_t)stream;
+  } else if (!h->own_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+    h->own_stream = true;
+  }
+  return HSMA_OK;
+}
+
+int hsma_eval(hsma_t h, const double* x, const double* q, int64_t N, double* energy, double* forces) {
+  return eval_impl(h, x, q, N, energy, forces, nullptr);
+}
+
+int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N, double* energy,
+                 double* forces, double* potential) {
+  return eval_impl(h, x, q, N, energy, forces, potential);
+}
+
+int hsma_get_info(hsma_t h, const char* key, double* value) {
+  if (!h || !key || !value) return HSMA_ERR_ARG;
+  const std::string k(key);
+  if (!h->is_server && (k == "Rc" || k == "Rs" || k == "n_shifts" || k == "n_check" || k == "rank")) {
+    int rc = ensure_geometry(h);
+    if (rc) return rc;
+  }
+  const Geometry& g = h->geo;
+  if (k == "Rc") *value = g.Rc;
+  else if (k == "Rs") *value = g.Rs;
+  else if (k == "n_shifts") *value = (double)g.shifts.size();
+  else if (k == "n_check") *value = g.n_check;
+  else if (k == "rank") *value = g.rank;
+  else if (k == "Ns") *value = h->last_Ns;
+  else if (k == "t_total_ms") *value = h->times[0];
+  else if (k == "t_prep_ms") *value = h->times[1];
+  else if (k == "t_near_ms") *value = h->times[2];
+  else if (k == "t_fit_ms") *value = h->times[3];
+  else if (k == "t_far_ms") *value = h->times[4];
+  else if (k == "t_assemble_ms") *value = h->times[5];
+  else if (k == "chunks") *value = h->chunks1;
+  else if (k == "far_chunks") *value = h->chunks2;
+  else if (k == "grid") *value = h->grid1;
+  else if (k == "slots") *value = h->slots;
+  else if (k == "tile_targets") *value = pair_tile_targets(h->precision, h->precision ? h->tpt : 1);
+  else return fail(h, HSMA_ERR_ARG, "unknown info key " + k);
+  return HSMA_OK;
+}
+
+int hsma_get_array(hsma_t h, const char* name, double* out, int64_t n) {
+  if (!h || !name || !out) return HSMA_ERR_ARG;
+  const std::string k(name);
+  const Geometry& g = h->geo;
+  if (h->geo_dirty) return fail(h, HSMA_ERR_ARG, "no evaluation yet");
+  const void* src = nullptr;
+  int64_t len = 0;
+  bool host = false;
+  if (k == "check_points") { src = g.check_pts.data(); len = g.n_check * 3; host = true; }
+  else if (k == "surface_points") { src = g.ysurf.data(); len = (int64_t)g.par.M * 3; host = true; }
+  else if (k == "check_phi") { src = h->d_cphi.p; len = g.n_check; }
+  else if (k == "check_dz") { src = h->d_cdz.p; len = g.n_check; }
+  else if (k == "coeffs") { src = h->d_A.p; len = g.nA; }
+  else if (k == "surface_q") { src = h->d_Q.p; len = g.par.M; }
+  else if (k == "grad") { src = h->d_grad.p; len = h->last_N * 3; }
+  else return fail(h, HSMA_ERR_ARG, "unknown array " + k);
+  if (n < len) return fail(h, HSMA_ERR_ARG, "output too small for " + k);
+  if (host) {
+    std::memcpy(out, src, (size_t)len * 8);
+    return HSMA_OK;
+  }
+  cudaError_t e = cudaMemcpy(out, src, (size_t)len * 8, cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(h, e, "array copy");
+  return HSMA_OK;
+}
+
+void hsma_destroy(hsma_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  server_shutdown(h);
+  delete h;
+}
+
+const char* hsma_last_error(hsma_t h) {
+  if (!h) return "NULL handle";
+  return h->err.c_str();
+}
+
+}  // extern "C"
+
+extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
+                                   double gamma_bot, double lam, int n_monitor, int G,
+                                   const char* name, double* out, int64_t n) {
+  if (!box || !name || !out) return HSMA_ERR_ARG;
+  if (dims != 2 && dims != 3) return HSMA_ERR_ARG;
+  GeoParams gp;
+  gp.dims = dims;
+  for (int d = 0; d < 3; ++d) gp.box[d] = box[d];
+  gp.p = p;
+  gp.M = M;
+  gp.lam = lam > 0 ? lam : (dims == 3 ? 1.3 : 1.6);
+  gp.n_monitor = n_monitor > 0 ? n_monitor : 2 * (p + 1) * (p + 1);
+  gp.gtop = dims == 2 ? gamma_top : 0.0;
+  gp.gbot = dims == 2 ? gamma_bot : 0.0;
+  gp.G = G > 0 ? G : 80;
+  Geometry g;
+  std::string err;
+  const int rc = build_geometry(gp, &g, &err);
+  if (rc) return rc;
+  const std::string k(name);
+  std::vector<double> v;
+  if (k == "T") {
+    v.assign((size_t)M * g.nv, 0.0);
+    for (int m = 0; m < M; ++m)
+      for (int r = 0; r < g.nA; ++r) {
+        const double w = g.W[(size_t)m * g.nA + r];
+        const double* prow = &g.P[(size_t)r * g.nv];
+        double* o = &v[(size_t)m * g.nv];
+        for (int c = 0; c < g.nv; ++c) o[c] += w * prow[c];
+      }
+  } else if (k == "check_points") {
+    v = g.check_pts;
+  } else if (k == "surface_points") {
+    v = g.ysurf;
+  } else if (k == "shifts") {
+    for (const Shift& s : g.shifts) v.insert(v.end(), {s.sx, s.sy, s.zs, s.zo, s.f});
+  } else if (k == "sizes") {
+    v = {(double)g.n_check, (double)g.nv, (double)g.nA, (double)g.rank, (double)g.shifts.size(),
+         g.Rc, g.Rs, g.Rs2};
+  } else {
+    return HSMA_ERR_ARG;
+  }
+  if ((int64_t)v.size() > n) return HSMA_ERR_ARG;
+  std::memcpy(out, v.data(), v.size() * 8);
+  return HSMA_OK;
+}

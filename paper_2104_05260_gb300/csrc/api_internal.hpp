@@ -1,0 +1,68 @@
+// The handle behind hsma_t and the helpers the API and the request loop share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "geometry.hpp"
+#include "internal.hpp"
+
+namespace hsma {
+
+// A device allocation that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  int ensure(size_t bytes);   // 0 or -1 (allocation failed)
+  void release();
+};
+
+struct Server;  // request loop state (serve.cpp)
+
+bool is_device_ptr(const void* ptr);
+double estimate_images(const Geometry& g, int64_t N);
+int choose_chunks(int tiles, int slots, double n_src, int min_len);
+
+}  // namespace hsma
+
+struct hsma_ctx {
+  static constexpr int kEvents = 6;
+  bool is_server = false;
+  hsma::GeoParams gp;
+  int precision = 1;
+  double pref = 1.0;
+  int timing = 0;
+  int chunks_opt = 0;
+  int tpt = 2;
+  bool geo_dirty = true;
+  hsma::Geometry geo;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // geometry-sized device buffers
+  hsma::DevBuf d_shifts, d_check, d_P, d_W, d_ysurf, d_v, d_A, d_cphi, d_cdz, d_Q, d_s32, d_s64;
+  // N-sized device buffers
+  hsma::DevBuf d_x, d_q, d_xc, d_cnt, d_blk, d_blkq, d_blkaq, d_src32, d_src64, d_tgt32, d_tgt64,
+      d_part, d_fpart, d_forces, d_pot, d_grad, d_blke, d_sc;
+  hsma::DevScalars* h_sc = nullptr;  // pinned
+  cudaEvent_t ev[kEvents] = {};
+  double times[6] = {0, 0, 0, 0, 0, 0};
+  // plan for plan_N particles
+  int64_t plan_N = -1;
+  int n_tgt1 = 0, tiles1 = 0, chunks1 = 1, grid1 = 1;
+  int tiles2 = 0, chunks2 = 1, grid2 = 1, slots = 1;
+  double ns_est = 0;
+  int64_t last_N = 0;
+  int last_Ns = 0;
+  hsma::Server* srv = nullptr;
+  ~hsma_ctx();
+};
+
+int hsma_ctx_init(hsma_ctx* h);
+int ensure_geometry(hsma_ctx* h);
+int ensure_plan(hsma_ctx* h, int64_t N);
+int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev);
+int finish_eval(hsma_ctx* h, double* energy);
+void server_shutdown(hsma_ctx* h);

@@ -1,0 +1,80 @@
+// Declarations shared by the host API (api.cpp, serve.cpp) and the device
+// kernels (kernels.cu).  Everything here is internal to libhsma.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hsma {
+
+// Per-evaluation scalars that live on the device, so the whole evaluation can
+// be enqueued without a host round trip.
+struct DevScalars {
+  double qsum, qabs, qcorr;  // sum q, sum |q|, neutral residual per ion
+  double energy;             // 1/2 pref sum q_i Phi_i
+  int Ns;                    // images in B (identity section + compacted rest)
+  int flags;                 // FLAG_* bits
+};
+
+enum { FLAG_NOT_NEUTRAL = 1, FLAG_OUT_OF_SLAB = 2, FLAG_TIMEOUT = 4 };
+
+// Inputs of the three prep kernels (wrap/centre, sphere membership, images).
+struct PrepArgs {
+  const double* x;       // N*3, API coordinates
+  const double* q;       // N
+  int N;
+  int dims;
+  double L[3];
+  double Rs2;
+  const double* shifts;  // n_shift*5 (sx, sy, zs, zo, f); identity first
+  int n_shift;
+  const double* check_pts;  // n_check*3 (box-centred)
+  int n_check;
+  double* xc;            // N*3 box-centred FP64 positions
+  int* cnt;              // N: non-identity images of each source inside B
+  int* blk;              // per-block image counts -> exclusive offsets
+  double* blk_q;
+  double* blk_aq;
+  DevScalars* sc;
+  float4* src32;         // images (x, y, z, q): FP32 path, or NULL
+  double4_32a* src64;        // images: FP64 path, or NULL
+  float4* tgt32;         // targets: N particles then n_check check points
+  double4_32a* tgt64;
+};
+
+// One generic pair-sum launch: targets x sources -> per-chunk partial sums of
+// (phi, dphi/dx, dphi/dy, dphi/dz) in FP64, part[(chunk*4 + c)*ld + t].
+struct PairArgs {
+  const void* tgt;       // float4* or double4_32a*
+  int n_tgt;
+  const void* src;       // float4* or double4_32a* (x, y, z, q)
+  int n_src;             // used when sc == NULL
+  const DevScalars* sc;  // when not NULL, the source count is sc->Ns
+  int n_diag;            // target t and source t (t < n_diag) are the same ion
+  int n_tiles;           // target tiles
+  int n_chunks;          // source chunks per target tile
+  double* part;
+  int ld;
+};
+
+struct PairPlan {
+  int tpt;               // targets per thread (FP32 path)
+  int threads;           // threads per CTA
+  int n_tiles, n_chunks, grid;
+};
+
+// Plans and launches; all return cudaError_t of the launch.
+int pair_tile_targets(int precision, int tpt);
+cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s);
+cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s);
+int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
+cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
+                       const double* P, int nA, int nv, const double* W, int M,
+                       const double* ysurf, double* v, double* A, double* cphi, double* cdz,
+                       double* Q, float4* s32, double4_32a* s64, cudaStream_t s);
+cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,
+                            int f_chunks, int fld, const double* q, int N, double pref,
+                            DevScalars* sc, double* forces, double* pot, double* grad,
+                            double* blk_e, cudaStream_t s);
+
+}  // namespace hsma

@@ -1,0 +1,487 @@
+// Device kernels of one HSMA evaluation (Sec. 2.2 of the paper), sm_103a.
+//
+//  prep   wrap/centre in FP64, sphere membership of every image in FP64
+//         (|x|^2 < R_s^2 in the order ((x*x + y*y) + z*z), never contracted
+//         into FMAs, so the decision is the one the FP64 reference makes),
+//         neutrality sums, and a deterministic compaction of the images in B
+//         into one list: section 0 holds the identity image of every source
+//         in source order, section 1 the other images, source-major.
+//  pair   generic direct sum targets x sources -> phi and grad phi.  The near
+//         field (Sec. 2.2, first and last steps), the check-point sums
+//         (Sec. 2.2, Eq. 6) and the far field of the surface charges all run
+//         through it.  FP32 pair arithmetic (rsqrt on the MUFU pipe) with
+//         TwoSum-compensated float-float accumulation per target, or an FP64
+//         twin.  Sources are staged through shared memory and broadcast to
+//         every thread; each CTA walks (target tile, source chunk) items of a
+//         static schedule, and every item writes its own FP64 partial, so the
+//         result does not depend on which CTA ran it.
+//  fit    FP64: combine the check-point partials in fixed order, A = P v,
+//         Q = W A (the least-squares solve and the surface map of Sec. 2.2).
+//  assemble  Phi_i, F_i = -q_i grad Phi_i, E = 1/2 sum q_i Phi_i (Sec. 3.1),
+//         with fixed-order tree reductions (no floating-point atomics).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.hpp"
+
+namespace hsma {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double wrap_centre(double x, double L) {
+  // (x - L*floor(x/L)) - L/2, each operation rounded separately
+  const double f = floor(__ddiv_rn(x, L));
+  return __dsub_rn(__dsub_rn(x, __dmul_rn(L, f)), 0.5 * L);
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  // fixed-order tree over the block's threads (deterministic)
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ int block_excl_scan_i(int v, int* sh, int* total) {
+  // Hillis-Steele inclusive scan in shared memory, then shift
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < NT; off <<= 1) {
+    const int t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  const int incl = sh[threadIdx.x];
+  *total = sh[NT - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// ------------------------------------------------------------------ prep
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_count(PrepArgs a) {
+  __shared__ double shd[kPrepThreads];
+  __shared__ int shi[kPrepThreads];
+  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
+  int c = 0;
+  double qj = 0.0, aq = 0.0;
+  if (j < a.N) {
+    const double x = a.x[3 * (size_t)j], y = a.x[3 * (size_t)j + 1], z = a.x[3 * (size_t)j + 2];
+    const double xc = wrap_centre(x, a.L[0]);
+    const double yc = wrap_centre(y, a.L[1]);
+    double zc;
+    if (a.dims == 3) {
+      zc = wrap_centre(z, a.L[2]);
+    } else {
+      if (!(z > 0.0 && z < a.L[2])) atomicOr(&a.sc->flags, FLAG_OUT_OF_SLAB);
+      zc = __dsub_rn(z, 0.5 * a.L[2]);
+    }
+    a.xc[3 * (size_t)j] = xc;
+    a.xc[3 * (size_t)j + 1] = yc;
+    a.xc[3 * (size_t)j + 2] = zc;
+    for (int s = 1; s < a.n_shift; ++s) {
+      const double* sh = a.shifts + 5 * s;
+      const double px = __dadd_rn(xc, sh[0]);
+      const double py = __dadd_rn(yc, sh[1]);
+      const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+      c += (r2 < a.Rs2) ? 1 : 0;
+    }
+    a.cnt[j] = c;
+    qj = a.q[j];
+    aq = fabs(qj);
+  }
+  int tot;
+  block_excl_scan_i<kPrepThreads>(c, shi, &tot);
+  const double bq = block_sum_d<kPrepThreads>(qj, shd);
+  const double baq = block_sum_d<kPrepThreads>(aq, shd);
+  if (threadIdx.x == 0) {
+    a.blk[blockIdx.x] = tot;
+    a.blk_q[blockIdx.x] = bq;
+    a.blk_aq[blockIdx.x] = baq;
+  }
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_prep_scan(PrepArgs a, int nblk) {
+  __shared__ double shd[kScanThreads];
+  __shared__ int shi[kScanThreads];
+  const int per = (nblk + kScanThreads - 1) / kScanThreads;
+  const int b0 = threadIdx.x * per;
+  const int b1 = min(nblk, b0 + per);
+  int c = 0;
+  double q = 0.0, aq = 0.0;
+  for (int b = b0; b < b1; ++b) {
+    c += a.blk[b];
+    q += a.blk_q[b];
+    aq += a.blk_aq[b];
+  }
+  int tot;
+  int off = block_excl_scan_i<kScanThreads>(c, shi, &tot);
+  const double sq = block_sum_d<kScanThreads>(q, shd);
+  const double saq = block_sum_d<kScanThreads>(aq, shd);
+  for (int b = b0; b < b1; ++b) {
+    const int v = a.blk[b];
+    a.blk[b] = off;
+    off += v;
+  }
+  if (threadIdx.x == 0) {
+    a.sc->Ns = a.N + tot;
+    a.sc->qsum = sq;
+    a.sc->qabs = saq;
+    a.sc->qcorr = sq / (double)a.N;
+    if (fabs(sq) > 1e-10 * saq) atomicOr(&a.sc->flags, FLAG_NOT_NEUTRAL);
+  }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
+  __shared__ int shi[kPrepThreads];
+  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
+  const int c = (j < a.N) ? a.cnt[j] : 0;
+  int tot;
+  const int local = block_excl_scan_i<kPrepThreads>(c, shi, &tot);
+  if (j < a.N) {
+    int o = a.N + a.blk[blockIdx.x] + local;
+    const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
+    const double qj = a.q[j] - a.sc->qcorr;
+    if (a.src32) {
+      a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
+      a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
+    }
+    if (a.src64) {
+      a.src64[j] = make_double4_32a(xc, yc, zc, qj);
+      a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
+    }
+    for (int s = 1; s < a.n_shift; ++s) {
+      const double* sh = a.shifts + 5 * s;
+      const double px = __dadd_rn(xc, sh[0]);
+      const double py = __dadd_rn(yc, sh[1]);
+      const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+      if (r2 < a.Rs2) {
+        const double qs = sh[4] * qj;
+        if (a.src32) a.src32[o] = make_float4((float)px, (float)py, (float)pz, (float)qs);
+        if (a.src64) a.src64[o] = make_double4_32a(px, py, pz, qs);
+        ++o;
+      }
+    }
+  }
+  if (j < a.n_check) {
+    const double* cp = a.check_pts + 3 * (size_t)j;
+    if (a.tgt32) a.tgt32[a.N + j] = make_float4((float)cp[0], (float)cp[1], (float)cp[2], 0.f);
+    if (a.tgt64) a.tgt64[a.N + j] = make_double4_32a(cp[0], cp[1], cp[2], 0.0);
+  }
+}
+
+cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
+  k_prep_count<<<nblk, kPrepThreads, 0, s>>>(a);
+  k_prep_scan<<<1, kScanThreads, 0, s>>>(a, nblk);
+  const int n = a.N > a.n_check ? a.N : a.n_check;
+  k_prep_emit<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pair sums
+constexpr int kPairThreads = 256;
+constexpr int kTile32 = 256;   // images per shared-memory tile (FP32 path)
+constexpr int kTile64 = 128;   // images per tile (FP64 path)
+constexpr float kFar = 1.0e18f;
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  // Knuth TwoSum: hi + v = s + err exactly; err is carried in lo
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (v - bb);
+  hi = s;
+  lo += err;
+}
+
+template <int TPT>
+__global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
+  __shared__ float4 sh[kTile32];
+  const float4* __restrict__ tgt = (const float4*)a.tgt;
+  const float4* __restrict__ src = (const float4*)a.src;
+  const int ns = a.sc ? a.sc->Ns : a.n_src;
+  int per = (ns + a.n_chunks - 1) / a.n_chunks;
+  per = (per + kTile32 - 1) / kTile32 * kTile32;
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+    const int t0 = tile * kPairThreads * TPT;
+    float tx[TPT], ty[TPT], tz[TPT];
+    float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int t = t0 + threadIdx.x + k * kPairThreads;
+      const float4 v = (t < a.n_tgt) ? tgt[t] : make_float4(kFar, kFar, kFar, 0.f);
+      tx[k] = v.x; ty[k] = v.y; tz[k] = v.z;
+      hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
+    }
+    const int s0 = chunk * per;
+    const int s1 = min(ns, s0 + per);
+    for (int sb = s0; sb < s1; sb += kTile32) {
+      const int n = min(kTile32, s1 - sb);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
+      __syncthreads();
+      float p[TPT], gx[TPT], gy[TPT], gz[TPT];
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) p[k] = gx[k] = gy[k] = gz[k] = 0.f;
+      const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n);
+      if (!diag) {
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+          const float4 s = sh[i];
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) {
+            const float dx = s.x - tx[k], dy = s.y - ty[k], dz = s.z - tz[k];
+            float r2 = dx * dx;
+            r2 = fmaf(dy, dy, r2);
+            r2 = fmaf(dz, dz, r2);
+            const float inv = rsqrtf(r2);
+            const float qi = s.w * inv;
+            p[k] += qi;
+            const float q3 = qi * (inv * inv);
+            gx[k] = fmaf(q3, dx, gx[k]);
+            gy[k] = fmaf(q3, dy, gy[k]);
+            gz[k] = fmaf(q3, dz, gz[k]);
+          }
+        }
+      } else {
+        for (int i = 0; i < n; ++i) {
+          const float4 s = sh[i];
+          const int sidx = sb + i;
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) {
+            const int t = t0 + threadIdx.x + k * kPairThreads;
+            const float dx = s.x - tx[k], dy = s.y - ty[k], dz = s.z - tz[k];
+            float r2 = dx * dx;
+            r2 = fmaf(dy, dy, r2);
+            r2 = fmaf(dz, dz, r2);
+            // only an ion (t < n_diag) meets its own identity image
+            const float inv = (sidx == t && t < a.n_diag) ? 0.f : rsqrtf(r2);
+            const float qi = s.w * inv;
+            p[k] += qi;
+            const float q3 = qi * (inv * inv);
+            gx[k] = fmaf(q3, dx, gx[k]);
+            gy[k] = fmaf(q3, dy, gy[k]);
+            gz[k] = fmaf(q3, dz, gz[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) {
+        two_sum_add(hp[k], lp[k], p[k]);
+        two_sum_add(hx[k], lx[k], gx[k]);
+        two_sum_add(hy[k], ly[k], gy[k]);
+        two_sum_add(hz[k], lz[k], gz[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int t = t0 + threadIdx.x + k * kPairThreads;
+      if (t < a.n_tgt) {
+        double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+        o[0] = (double)hp[k] + (double)lp[k];
+        o[(size_t)a.ld] = (double)hx[k] + (double)lx[k];
+        o[2 * (size_t)a.ld] = (double)hy[k] + (double)ly[k];
+        o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
+  __shared__ double4_32a sh[kTile64];
+  const double4_32a* __restrict__ tgt = (const double4_32a*)a.tgt;
+  const double4_32a* __restrict__ src = (const double4_32a*)a.src;
+  const int ns = a.sc ? a.sc->Ns : a.n_src;
+  int per = (ns + a.n_chunks - 1) / a.n_chunks;
+  per = (per + kTile64 - 1) / kTile64 * kTile64;
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+    const int t = tile * kPairThreads + threadIdx.x;
+    const double4_32a tv = (t < a.n_tgt) ? tgt[t] : make_double4_32a(1e18, 1e18, 1e18, 0.0);
+    double p = 0, gx = 0, gy = 0, gz = 0;
+    const int s0 = chunk * per;
+    const int s1 = min(ns, s0 + per);
+    const int t0 = tile * kPairThreads;
+    for (int sb = s0; sb < s1; sb += kTile64) {
+      const int n = min(kTile64, s1 - sb);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
+      __syncthreads();
+      const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads) && (t0 < sb + n);
+      for (int i = 0; i < n; ++i) {
+        const double4_32a s = sh[i];
+        const double dx = s.x - tv.x, dy = s.y - tv.y, dz = s.z - tv.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        double inv = rsqrt(r2);
+        if (diag && sb + i == t && t < a.n_diag) inv = 0.0;
+        const double qi = s.w * inv;
+        p += qi;
+        const double q3 = qi * inv * inv;
+        gx += q3 * dx;
+        gy += q3 * dy;
+        gz += q3 * dz;
+      }
+    }
+    if (t < a.n_tgt) {
+      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+      o[0] = p;
+      o[(size_t)a.ld] = gx;
+      o[2 * (size_t)a.ld] = gy;
+      o[3 * (size_t)a.ld] = gz;
+    }
+  }
+}
+
+int pair_tile_targets(int precision, int tpt) {
+  return precision == 0 ? kPairThreads : kPairThreads * tpt;
+}
+
+static const void* pair_fn(int precision, int tpt) {
+  if (precision == 0) return (const void*)k_pair_f64;
+  if (tpt == 1) return (const void*)k_pair_f32<1>;
+  if (tpt == 2) return (const void*)k_pair_f32<2>;
+  return (const void*)k_pair_f32<4>;
+}
+
+int pair_slots(int precision, int tpt) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fn(precision, tpt), kPairThreads, 0);
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s) {
+  if (grid < 1) grid = 1;
+  if (precision == 0) k_pair_f64<<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 1) k_pair_f32<1><<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 2) k_pair_f32<2><<<grid, kPairThreads, 0, s>>>(a);
+  else k_pair_f32<4><<<grid, kPairThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fit + map
+constexpr int kFitThreads = 256;
+
+__global__ void k_check_combine(const double* part, int n_chunks, int ld, int N, int n_check,
+                                int dims, double* v, double* cphi, double* cdz) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_check) return;
+  double p = 0.0, d = 0.0;
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    p += part[((size_t)ch * 4 + 0) * ld + N + c];
+    d += part[((size_t)ch * 4 + 3) * ld + N + c];
+  }
+  v[c] = p;
+  if (dims == 2) v[n_check + c] = d;
+  cphi[c] = p;
+  cdz[c] = d;
+}
+
+__global__ void __launch_bounds__(kFitThreads) k_gemv_rows(const double* P, int nv, const double* v, double* A) {
+  __shared__ double sh[kFitThreads];
+  const double* row = P + (size_t)blockIdx.x * nv;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nv; k += kFitThreads) s += row[k] * v[k];
+  s = block_sum_d<kFitThreads>(s, sh);
+  if (threadIdx.x == 0) A[blockIdx.x] = s;
+}
+
+__global__ void k_surface(const double* W, int M, int nA, const double* A, const double* ysurf,
+                          double* Q, float4* s32, double4_32a* s64) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double s = 0.0;
+  const double* w = W + (size_t)m * nA;
+  for (int r = 0; r < nA; ++r) s += w[r] * A[r];
+  Q[m] = s;
+  const double x = ysurf[3 * m], y = ysurf[3 * m + 1], z = ysurf[3 * m + 2];
+  if (s32) s32[m] = make_float4((float)x, (float)y, (float)z, (float)s);
+  if (s64) s64[m] = make_double4_32a(x, y, z, s);
+}
+
+cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
+                       const double* P, int nA, int nv, const double* W, int M,
+                       const double* ysurf, double* v, double* A, double* cphi, double* cdz,
+                       double* Q, float4* s32, double4_32a* s64, cudaStream_t s) {
+  k_check_combine<<<(n_check + 255) / 256, 256, 0, s>>>(part, n_chunks, ld, N, n_check, dims, v, cphi, cdz);
+  k_gemv_rows<<<nA, kFitThreads, 0, s>>>(P, nv, v, A);
+  k_surface<<<(M + 127) / 128, 128, 0, s>>>(W, M, nA, A, ysurf, Q, s32, s64);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ assembly
+constexpr int kAsmThreads = 256;
+
+__global__ void __launch_bounds__(kAsmThreads) k_assemble(const double* part, int n_chunks, int ld,
+                                                          const double* fpart, int f_chunks, int fld,
+                                                          const double* q, int N, double pref,
+                                                          const DevScalars* sc, double* forces,
+                                                          double* pot, double* grad, double* blk_e) {
+  __shared__ double sh[kAsmThreads];
+  const int i = blockIdx.x * kAsmThreads + threadIdx.x;
+  double e = 0.0;
+  if (i < N) {
+    double g[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0;
+      for (int ch = 0; ch < n_chunks; ++ch) s += part[((size_t)ch * 4 + c) * ld + i];
+      double f = 0.0;
+      for (int ch = 0; ch < f_chunks; ++ch) f += fpart[((size_t)ch * 4 + c) * fld + i];
+      g[c] = s + f;
+    }
+    const double qi = q[i] - sc->qcorr;
+    if (forces) {
+      forces[3 * (size_t)i] = -pref * qi * g[1];
+      forces[3 * (size_t)i + 1] = -pref * qi * g[2];
+      forces[3 * (size_t)i + 2] = -pref * qi * g[3];
+    }
+    if (pot) pot[i] = pref * g[0];
+    if (grad) {
+      grad[3 * (size_t)i] = g[1];
+      grad[3 * (size_t)i + 1] = g[2];
+      grad[3 * (size_t)i + 2] = g[3];
+    }
+    e = qi * g[0];
+  }
+  e = block_sum_d<kAsmThreads>(e, sh);
+  if (threadIdx.x == 0) blk_e[blockIdx.x] = e;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_energy(const double* blk_e, int nblk, double pref, DevScalars* sc) {
+  __shared__ double sh[kScanThreads];
+  const int per = (nblk + kScanThreads - 1) / kScanThreads;
+  const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
+  double s = 0.0;
+  for (int b = b0; b < b1; ++b) s += blk_e[b];
+  s = block_sum_d<kScanThreads>(s, sh);
+  if (threadIdx.x == 0) sc->energy = 0.5 * pref * s;
+}
+
+cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,
+                            int f_chunks, int fld, const double* q, int N, double pref,
+                            DevScalars* sc, double* forces, double* pot, double* grad,
+                            double* blk_e, cudaStream_t s) {
+  const int nblk = (N + kAsmThreads - 1) / kAsmThreads;
+  k_assemble<<<nblk, kAsmThreads, 0, s>>>(part, n_chunks, ld, fpart, f_chunks, fld, q, N, pref, sc,
+                                          forces, pot, grad, blk_e);
+  k_energy<<<1, kScanThreads, 0, s>>>(blk_e, nblk, pref, sc);
+  return cudaGetLastError();
+}
+
+}  // namespace hsma

@@ -1,0 +1,99 @@
+"""CPU-only checks of the C-ABI library: it builds, loads and exports every
+symbol include/hsma.h declares, and its host geometry (sphere, image shifts,
+check points, and the composite fit + surface map of Sec. 2.2) agrees with the
+oracle's.  No GPU and no device call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hsma.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsma_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(P):
+    names = declared_symbols()
+    assert "hsma_eval" in names and "hsma_submit" in names and len(names) >= 14
+    L = P.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in P.SIGNATURES, n
+
+
+def test_binding_has_no_fallback(P, monkeypatch):
+    monkeypatch.setattr(P, "_lib", None)
+    monkeypatch.setattr(P, "LIB_PATH", "/nonexistent/libhsma.so")
+    with pytest.raises(RuntimeError):
+        P.lib()
+
+
+def sizes(P, box, dims, p, M, **kw):
+    s = P.hsma_geometry_array(box, dims, p, M, "sizes", 8, **kw)
+    return dict(n_check=int(s[0]), nv=int(s[1]), nA=int(s[2]), rank=int(s[3]),
+                n_shift=int(s[4]), Rc=s[5], Rs=s[6], Rs2=s[7])
+
+
+@pytest.mark.parametrize("box,p,M,lam", [((10.0, 10.0, 10.0), 6, 800, 0.0),
+                                         ((7.0, 9.0, 11.0), 8, 1000, 0.0),
+                                         ((10.0, 10.0, 10.0), 10, 4000, 2.6)])
+def test_geometry_3d_matches_oracle(P, box, p, M, lam):
+    from oracle import hsma
+    st = hsma.make_setup(box, 3, p, M, lam=(lam or None))
+    sz = sizes(P, box, 3, p, M, lam=lam)
+    assert sz["Rs2"] == st.Rs2 and sz["Rs"] == st.Rs     # bitwise: same FP64 op order
+    assert sz["rank"] == sz["nA"] == (p + 1) ** 2 - 1
+    assert sz["n_shift"] == len(st.shifts)
+    sh = P.hsma_geometry_array(box, 3, p, M, "shifts", 5 * sz["n_shift"], lam=lam).reshape(-1, 5)
+    assert sorted(map(tuple, sh)) == sorted(map(tuple, st.shifts))   # bitwise
+    cp = P.hsma_geometry_array(box, 3, p, M, "check_points", 3 * sz["n_check"], lam=lam)
+    assert np.allclose(cp.reshape(-1, 3), st.check_pts, rtol=0, atol=1e-12)
+    ys = P.hsma_geometry_array(box, 3, p, M, "surface_points", 3 * M, lam=lam).reshape(-1, 3)
+    assert np.allclose(ys, st.ysurf, rtol=0, atol=1e-12)
+    T = P.hsma_geometry_array(box, 3, p, M, "T", M * sz["nv"], lam=lam).reshape(M, sz["nv"])
+    To = st.W @ st.P
+    assert np.abs(T - To).max() < 1e-9 * np.abs(To).max()
+
+
+@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.0, 0.0), (0.95, 0.95), (0.5, -0.3)])
+def test_geometry_2d_matches_oracle(P, gam):
+    from oracle import hsma
+    box, p, M, G = (20.0, 20.0, 10.0), 6, 600, 16
+    st = hsma.make_setup(box, 2, p, M, gam[0], gam[1], dtn_grid=G)
+    sz = sizes(P, box, 2, p, M, gamma_top=gam[0], gamma_bot=gam[1], G=G)
+    assert sz["Rs2"] == st.Rs2
+    assert sz["rank"] == (p + 1) ** 2 - 1
+    kw = dict(gamma_top=gam[0], gamma_bot=gam[1], G=G)
+    sh = P.hsma_geometry_array(box, 2, p, M, "shifts", 5 * sz["n_shift"], **kw).reshape(-1, 5)
+    assert sorted(map(tuple, sh)) == sorted(map(tuple, st.shifts))
+    cp = P.hsma_geometry_array(box, 2, p, M, "check_points", 3 * sz["n_check"], **kw)
+    assert np.allclose(cp.reshape(-1, 3), st.check_pts, rtol=0, atol=1e-12)
+    T = P.hsma_geometry_array(box, 2, p, M, "T", M * sz["nv"], **kw).reshape(M, sz["nv"])
+    To = st.W @ st.P
+    assert T.shape == To.shape
+    assert np.abs(T - To).max() < 1e-8 * np.abs(To).max()
+
+
+def test_geometry_rejects_bad_arguments(P):
+    with pytest.raises(P.HSMAError):
+        P.hsma_geometry_array((10, 10, 10), 3, 6, 10, "sizes", 8)       # M < (p+1)^2
+    with pytest.raises(P.HSMAError):
+        P.hsma_geometry_array((10, 10, 10), 4, 6, 800, "sizes", 8)      # dims
+    with pytest.raises(P.HSMAError):
+        P.hsma_geometry_array((10, 10, 10), 3, 6, 800, "sizes", 8, lam=0.9)
+    with pytest.raises(P.HSMAError):
+        P.hsma_geometry_array((20, 20, 10), 2, 6, 800, "sizes", 8, gamma_top=1.2)

@@ -1,0 +1,251 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: relative energy error <= 1e-6 for the FP64 path and <= 1e-5 for
+the FP32-compute path; forces are compared by their relative RMS error, with
+the bound written next to each check.  Integer work (the set of images in the
+sphere B) must match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import hsma as O
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = {0: 1e-6, 1: 1e-5}
+F_TOL = {0: 1e-6, 1: 2e-5}      # relative RMS of the per-ion forces
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def frms(F, Fr):
+    return math.sqrt(np.mean(np.sum((F - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1)))
+
+
+def pot_err(pot, ref):
+    d = pot - ref
+    return math.sqrt(np.mean((d - d.mean()) ** 2) / np.mean(ref ** 2))
+
+
+def run(P, c, x, q, prec, **opt):
+    h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=prec, **opt)
+    E, F, pot = h.eval(x, q, potential=True)
+    return h, E, F, pot
+
+
+def check_full(P, c, x, q, prec, st=None, **opt):
+    st = st or O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
+                            dtn_grid=c.dtn_grid, **{k: v for k, v in opt.items() if k == "n_monitor"})
+    ref = O.evaluate(st, x, q)
+    h, E, F, pot = run(P, c, x, q, prec, **opt)
+    assert int(h.info("Ns")) == ref["Ns"]                      # same images in B, exactly
+    assert rel(E, ref["energy"]) <= E_TOL[prec], (E, ref["energy"])
+    assert frms(F, ref["forces"]) <= F_TOL[prec]
+    # the per-ion potential is fixed only up to an additive constant (A_0^0 is
+    # dropped; for a neutral system energy and forces do not see it), so it is
+    # compared after removing the mean offset
+    assert pot_err(pot, ref["phi"]) <= F_TOL[prec]
+    # each step on its own: check-point sums, surface charges
+    nc = int(h.info("n_check"))
+    cphi = h.array("check_phi", nc)
+    assert np.abs(cphi - ref["check_phi"]).max() <= 10 * E_TOL[prec] * np.abs(ref["check_phi"]).max()
+    # surface charges, judged by the far field they produce at the ions (their
+    # high-order parts are amplified by lambda^n in the map but decay as
+    # (r/R_s)^n inside the box)
+    Q = h.array("surface_q", c.M)
+    fphi, _ = O.pair_field(ref["xc"], st.ysurf, Q)
+    d = fphi - ref["far_phi"]
+    assert math.sqrt(np.mean((d - d.mean()) ** 2) / np.mean(ref["phi"] ** 2)) <= F_TOL[prec]
+    if prec == 0:
+        assert np.abs(Q - ref["Q"]).max() <= 100 * E_TOL[prec] * np.abs(ref["Q"]).max()
+    h.close()
+    return E, ref
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cfg1_full(P, prec):
+    c = workloads.case(1)                          # N = 1000, L = 10, p = 6, M = 800
+    x, q = workloads.electrolyte(c)
+    check_full(P, c, x, q, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,val", [(2, (1, -1)), (3, (2, -1)), (258, (1, -1)), (1001, (2, -1)),
+                                   (2050, (3, -1))])
+def test_ragged_and_tiny_sizes(P, prec, N, val):
+    L = 10.0 * (N / 1000) ** (1 / 3)
+    c = workloads.small_case(N, dims=3, box=(L, L, L), p=4, M=200, valences=val, seed=N)
+    x, q = workloads.electrolyte(c)
+    check_full(P, c, x, q, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_positions_on_boundaries_and_outside(P, prec):
+    L = 6.0
+    c = workloads.small_case(40, dims=3, box=(L, L, L), p=4, M=200, seed=3)
+    x, q = workloads.electrolyte(c)
+    # exact box edges, exact wrap ties, and far-away periodic copies
+    x[0] = [0.0, 0.0, 0.0]
+    x[1] = [L, L / 2, -L]
+    x[2] = [-1e-300, 2.5 * L, 7 * L + 0.25]
+    x[3] = [L / 2, L / 2, L / 2]
+    x[4] = [-3 * L + 1.0, 1e3 * L + 2.0, L - 1e-12]
+    check_full(P, c, x, q, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_literal_sphere_radius_125_cells(P, prec):
+    L = 5.0
+    c = workloads.small_case(200, dims=3, box=(L, L, L), p=10, M=2000, lam=2.6, seed=5)
+    x, q = workloads.electrolyte(c)
+    st = O.make_setup(c.box, 3, 10, 2000, lam=2.6, n_monitor=200)
+    assert len(st.shifts) == 125
+    check_full(P, c, x, q, prec, st=st, **{"lambda": 2.6, "n_monitor": 200})
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.0, 0.0), (0.95, 0.95), (0.6, 0.0)])
+def test_2d_small(P, prec, gam):
+    c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam,
+                             G=24, seed=13)
+    x, q = workloads.electrolyte(c)
+    # next to the walls: 1e-6 for FP64; FP32 box-centred coordinates resolve
+    # an ion-face distance d to ~1e-6/d^2 in the face check sums, so 0.1 there
+    d = 1e-6 if prec == 0 else 0.1
+    x[0, 2] = d                          # bottom wall
+    x[1, 2] = 10.0 - d                   # top wall
+    check_full(P, c, x, q, prec, dtn_grid=24)
+
+
+def test_errors_are_reported(P):
+    c = workloads.small_case(20, dims=2, box=(20.0, 20.0, 10.0), p=4, M=200, G=8)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 2, 4, 200, 0.5, 0.5, dtn_grid=8)
+    bad = x.copy(); bad[3, 2] = 10.0
+    with pytest.raises(P.HSMAError) as e:
+        h.eval(bad, q)
+    assert e.value.code == -3
+    q2 = q.copy(); q2[0] += 0.5
+    with pytest.raises(P.HSMAError) as e:
+        h.eval(x, q2)
+    assert e.value.code == -2
+    with pytest.raises(P.HSMAError) as e:
+        h.set_option("lambda", 0.5)
+    assert e.value.code == -1
+    with pytest.raises(P.HSMAError):
+        h.set_option("no_such_option", 1)
+    E, F, _ = h.eval(x, q)              # the handle still works after errors
+    assert np.isfinite(E) and np.all(np.isfinite(F))
+    h.close()
+
+
+def test_repeatable_bitwise(P):
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, c.p, c.M)
+    E1, F1, _ = h.eval(x, q)
+    E2, F2, _ = h.eval(x, q)
+    assert E1 == E2 and np.array_equal(F1, F2)
+    h.close()
+
+
+def test_device_pointers(P):
+    torch = pytest.importorskip("torch")
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, c.p, c.M)
+    E0, F0, p0 = h.eval(x, q, potential=True)
+    xd = torch.from_numpy(x).cuda()
+    qd = torch.from_numpy(q).cuda()
+    E1, F1, p1 = h.eval(xd, qd, potential=True)
+    assert F1.is_cuda and E1 == E0
+    assert np.array_equal(F1.cpu().numpy(), F0) and np.array_equal(p1.cpu().numpy(), p0)
+    h.close()
+
+
+# ------------------------------------------------------------ full-size cases
+def sampled(P, c, prec, n_samp, margin=0.0, **opt):
+    """Full-size run; oracle on a sample of targets plus all check points."""
+    x, q = workloads.electrolyte(c, margin=margin)
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(c.N, n_samp, replace=False))
+    st = O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
+                      dtn_grid=c.dtn_grid)
+    ref = O.evaluate(st, x, q, targets=idx)
+    h, E, F, pot = run(P, c, x, q, prec, **opt)
+    assert int(h.info("Ns")) == ref["Ns"]
+    assert frms(F[idx], ref["forces"]) <= F_TOL[prec]
+    assert pot_err(pot[idx], ref["phi"]) <= F_TOL[prec]
+    Q = h.array("surface_q", c.M)
+    assert np.abs(Q - ref["Q"]).max() <= 100 * E_TOL[prec] * np.abs(ref["Q"]).max()
+    h.close()
+    return E
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cfg2_100k_sampled(P, prec):
+    sampled(P, workloads.case(2), prec, 48)
+
+
+def test_cfg2_energy_fp32_vs_fp64(P):
+    # the whole-system energy of the FP32 path against the FP64 path (the FP64
+    # path itself is pinned to the oracle above)
+    c = workloads.case(2)
+    x, q = workloads.electrolyte(c)
+    _, E64, _, _ = run(P, c, x, q, 0)
+    _, E32, _, _ = run(P, c, x, q, 1)
+    assert rel(E32, E64) <= E_TOL[1]
+
+
+def test_cfg5_262k_sampled(P):
+    sampled(P, workloads.case(5), 1, 24)
+
+
+@pytest.mark.parametrize("gam", [-0.95, 0.0, 0.95])
+def test_cfg3_2d_20k_stagewise(P, gam):
+    # 2D, N = 20000, G = 80: the oracle cannot redo all 13124 check targets in
+    # seconds, so each step is checked on its own: check-point sums on a
+    # sample, the fit + map from the GPU's own check values, and near + far at
+    # sampled particles.
+    c = workloads.case(3, gamma=gam)
+    x, q = workloads.electrolyte(c)
+    st = O.make_setup(c.box, 2, c.p, c.M, gam, gam, lam=c.lam, dtn_grid=c.dtn_grid)
+    h, E, F, pot = run(P, c, x, q, 1)
+    xc, qc = O.prepare_inputs(st, x, q)
+    ipos, iq, isrc, isid = O.near_set(st, xc, qc)
+    assert int(h.info("Ns")) == len(iq)
+    nc = int(h.info("n_check"))
+    cphi = h.array("check_phi", nc)
+    cdz = h.array("check_dz", nc)
+    rng = np.random.default_rng(7)
+    ci = np.sort(rng.choice(nc, 200, replace=False))
+    ophi, ograd = O.pair_field(st.check_pts[ci], ipos, iq)
+    assert np.abs(cphi[ci] - ophi).max() <= 1e-5 * np.abs(ophi).max()
+    assert np.abs(cdz[ci] - ograd[:, 2]).max() <= 1e-5 * np.abs(ograd[:, 2]).max()
+    Q = h.array("surface_q", c.M)
+    Qo = st.W @ (st.P @ np.concatenate([cphi, cdz]))
+    assert np.abs(Q - Qo).max() <= 1e-9 * np.abs(Qo).max()
+    ti = np.sort(rng.choice(c.N, 32, replace=False))
+    s0 = O.self_shift(st)
+    self_idx = np.full(c.N, -1)
+    m0 = isid == s0
+    self_idx[isrc[m0]] = np.nonzero(m0)[0]
+    nphi, ngrad = O.pair_field(xc[ti], ipos, iq, exclude=self_idx[ti])
+    fphi, fgrad = O.pair_field(xc[ti], st.ysurf, Q)
+    Fr = -qc[ti, None] * (ngrad + fgrad)
+    assert frms(F[ti], Fr) <= F_TOL[1]
+    h.close()
