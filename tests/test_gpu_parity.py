@@ -122,10 +122,13 @@ def test_literal_sphere_radius_125_cells(P, prec):
 def test_2d_small(P, prec, gam):
     c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam,
                              G=24, seed=13)
-    x, q = workloads.electrolyte(c)
-    # next to the walls: 1e-6 for FP64; FP32 box-centred coordinates resolve
-    # an ion-face distance d to ~1e-6/d^2 in the face check sums, so 0.1 there
-    d = 1e-6 if prec == 0 else 0.1
+    # FP64: ions anywhere, two of them 1e-6 from a wall.  FP32: an ion at
+    # distance d from a dielectric wall meets its own reflection at 2d, and
+    # box-centred FP32 coordinates (ulp ~5e-7 at |z| = 5) resolve that pair to
+    # ~2.5e-7/d relative, so the FP32 case keeps every ion >= 0.05 from the walls.
+    margin = 0.0 if prec == 0 else 0.05
+    x, q = workloads.electrolyte(c, margin=margin)
+    d = 1e-6 if prec == 0 else 0.05
     x[0, 2] = d                          # bottom wall
     x[1, 2] = 10.0 - d                   # top wall
     check_full(P, c, x, q, prec, dtn_grid=24)
