@@ -43,6 +43,7 @@ SIGNATURES = {
     "hsma_server_step": (_I, [_P]),
     "hsma_geometry_array": (_I, [ctypes.POINTER(_D), _I, _I, _I, _D, _D, _D, _I, _I,
                                  ctypes.c_char_p, _P, _L]),
+    "hsma_pair_sum_static": (_I, [_P, _L, _P, _L, _P, _I, _P]),
 }
 
 _lib = None
@@ -212,6 +213,21 @@ def hsma_geometry_array(box, dims, p, M, name, n, gamma_top=0.0, gamma_bot=0.0, 
                                    ctypes.c_void_p(out.ctypes.data), int(n))
     if rc != HSMA_OK:
         raise HSMAError(rc, "hsma_geometry_array(" + name + ") failed")
+    return out
+
+
+def hsma_pair_sum_static(targets, sources, out, precision=1, stream_ptr=0):
+    """Direct pair sum with the library's static scratch (no device allocation).
+
+    targets (n_t, 3), sources (n_s, 4: x, y, z, q) and out (n_t, 4: phi,
+    dphi/dx, dphi/dy, dphi/dz) are float64 CUDA tensors; the work is enqueued
+    on the given stream and is complete when that stream reaches it.
+    """
+    nt, ns = int(targets.shape[0]), int(sources.shape[0])
+    rc = lib().hsma_pair_sum_static(_ptr(targets, 3 * nt), nt, _ptr(sources, 4 * ns), ns,
+                                    _ptr(out, 4 * nt), int(precision), ctypes.c_void_p(stream_ptr))
+    if rc != HSMA_OK:
+        raise HSMAError(rc, "hsma_pair_sum_static failed")
     return out
 
 
