@@ -297,7 +297,7 @@ def main():
     peak_instr = SMS * FP32_LANES * mhz * 1e6 / 1e12          # T lane-instr/s
     t_near = float(np.mean(near_ms)) / 1e3
     achieved = pairs_near * FP32_INSTR_PER_PAIR / t_near / 1e12
-    roof = {"bound": "alu", "kernel": "k_pair_f32 (near field + check points)",
+    roof = {"bound": "alu", "kernel": "k_pair_f32x2<1> (near field + check points)",
             "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s",
             "frac": achieved / peak_instr, "traffic": None,
             "flops_view": {"achieved_tflops": pairs_near * FLOP_PER_PAIR / t_near / 1e12,

@@ -105,7 +105,7 @@ hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
-                    &d_blke, &d_sc})
+                    &d_blke, &d_sc, &d_ioff, &d_self})
     b->release();
   if (h_sc) cudaFreeHost(h_sc);
   for (int i = 0; i < hsma_ctx::kEvents; ++i)
@@ -197,7 +197,8 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   if (prec == 0)
     bad = bad || h->d_src64.ensure(simg * 32) || h->d_tgt64.ensure(nt * 32);
   else
-    bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16);
+    bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16) ||
+          h->d_ioff.ensure(n * 4) || h->d_self.ensure(n * 32);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
   h->plan_N = N;
   return HSMA_OK;
@@ -233,8 +234,12 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   a.tgt32 = prec ? (float4*)h->d_tgt32.p : nullptr;
   a.src64 = prec ? nullptr : (double4_32a*)h->d_src64.p;
   a.tgt64 = prec ? nullptr : (double4_32a*)h->d_tgt64.p;
+  a.ioff = prec ? (int*)h->d_ioff.p : nullptr;
   const int nblk = (int)((N + 255) / 256);
   cudaError_t e = launch_prep(a, nblk, s);
+  // FP32 path: each ion's own shifted images are summed in FP64 here and
+  // skipped by the FP32 pair kernel
+  if (e == cudaSuccess && prec) e = launch_self_images(a, (double*)h->d_self.p, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "prep launch");
   if (tm) cudaEventRecord(h->ev[1], s);
 
@@ -249,6 +254,8 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   p1.n_chunks = h->chunks1;
   p1.part = (double*)h->d_part.p;
   p1.ld = h->n_tgt1;
+  p1.ioff = prec ? (const int*)h->d_ioff.p : nullptr;
+  p1.icnt = prec ? (const int*)h->d_cnt.p : nullptr;
   e = launch_pair(prec, tpt, p1, h->grid1, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
   if (tm) cudaEventRecord(h->ev[2], s);
@@ -277,7 +284,8 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   if (tm) cudaEventRecord(h->ev[4], s);
 
   e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1, (const double*)h->d_fpart.p,
-                      h->chunks2, (int)N, (const double*)h->d_q.p, (int)N, h->pref,
+                      h->chunks2, (int)N, prec ? (const double*)h->d_self.p : nullptr,
+                      (const double*)h->d_q.p, (int)N, h->pref,
                       (DevScalars*)h->d_sc.p, forces_dev, pot_dev, (double*)h->d_grad.p,
                       (double*)h->d_blke.p, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble launch");
@@ -399,7 +407,8 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->chunks_opt = (int)v;
     h->plan_N = -1;
   } else if (k == "targets_per_thread") {
-    if (v != 1 && v != 2 && v != 4) return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2 or 4");
+    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14)
+      return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2, 4 (scalar) or 12, 14 (packed)");
     h->tpt = (int)v;
     h->plan_N = -1;
   } else {

@@ -40,6 +40,7 @@ struct PrepArgs {
   double4_32a* src64;        // images: FP64 path, or NULL
   float4* tgt32;         // targets: N particles then n_check check points
   double4_32a* tgt64;
+  int* ioff;             // N: first section-1 image of each ion, or NULL
 };
 
 // One generic pair-sum launch: targets x sources -> per-chunk partial sums of
@@ -55,6 +56,10 @@ struct PairArgs {
   int n_chunks;          // source chunks per target tile
   double* part;
   int ld;
+  // FP32 path: ion t (t < n_diag) also skips its own section-1 images
+  // [ioff[t], ioff[t] + icnt[t]); those terms are added in FP64 elsewhere.
+  const int* ioff = nullptr;
+  const int* icnt = nullptr;
 };
 
 struct PairPlan {
@@ -73,8 +78,10 @@ cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N
                        const double* ysurf, double* v, double* A, double* cphi, double* cdz,
                        double* Q, float4* s32, double4_32a* s64, cudaStream_t s);
 cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,
-                            int f_chunks, int fld, const double* q, int N, double pref,
-                            DevScalars* sc, double* forces, double* pot, double* grad,
+                            int f_chunks, int fld, const double* self, const double* q, int N,
+                            double pref, DevScalars* sc, double* forces, double* pot, double* grad,
                             double* blk_e, cudaStream_t s);
+// FP64 sum of every ion's own shifted images in B: self[c*N + i], c = phi, grad.
+cudaError_t launch_self_images(const PrepArgs& a, double* self, cudaStream_t s);
 
 }  // namespace hsma

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
   const int local = block_excl_scan_i<kPrepThreads>(c, shi, &tot);
   if (j < a.N) {
     int o = a.N + a.blk[blockIdx.x] + local;
+    if (a.ioff) a.ioff[j] = o;
     const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
     const double qj = a.q[j] - a.sc->qcorr;
     if (a.src32) {
@@ -191,6 +192,10 @@ cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ pair sums
+#ifndef HSMA_PAIR_UNROLL
+#define HSMA_PAIR_UNROLL 8     // images per unrolled step of the FP32 inner loops
+#endif
+constexpr int kUnroll = HSMA_PAIR_UNROLL;
 constexpr int kPairThreads = 256;
 constexpr int kTile32 = 256;   // images per shared-memory tile (FP32 path)
 constexpr int kTile64 = 128;   // images per tile (FP64 path)
@@ -203,6 +208,17 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   const float err = (hi - (s - bb)) + (v - bb);
   hi = s;
   lo += err;
+}
+
+// Section-1 index range holding the own images of the ions in the target
+// tile [t0, t0 + tt) (images are emitted source-major, so it is contiguous).
+__device__ __forceinline__ void own_range(const PairArgs& a, int t0, int tt, int* lo, int* hi) {
+  *lo = 0;
+  *hi = 0;
+  if (!a.ioff || t0 >= a.n_diag) return;
+  const int tl = min(t0 + tt, a.n_diag) - 1;
+  *lo = a.ioff[t0];
+  *hi = a.ioff[tl] + a.icnt[tl];
 }
 
 template <int TPT>
@@ -226,6 +242,16 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
       tx[k] = v.x; ty[k] = v.y; tz[k] = v.z;
       hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
     }
+    int so[TPT], sc[TPT];   // own section-1 image range of each ion target
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int t = t0 + threadIdx.x + k * kPairThreads;
+      const bool ion = a.ioff && t < a.n_diag;
+      so[k] = ion ? a.ioff[t] : 0;
+      sc[k] = ion ? a.icnt[t] : 0;
+    }
+    int lo1 = 0, hi1 = 0;
+    own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
     const int s0 = chunk * per;
     const int s1 = min(ns, s0 + per);
     for (int sb = s0; sb < s1; sb += kTile32) {
@@ -236,9 +262,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
       float p[TPT], gx[TPT], gy[TPT], gz[TPT];
 #pragma unroll
       for (int k = 0; k < TPT; ++k) p[k] = gx[k] = gy[k] = gz[k] = 0.f;
-      const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n);
+      const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
+                        (sb < hi1 && lo1 < sb + n);
       if (!diag) {
-#pragma unroll 4
+#pragma unroll kUnroll
         for (int i = 0; i < n; ++i) {
           const float4 s = sh[i];
 #pragma unroll
@@ -267,8 +294,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
             float r2 = dx * dx;
             r2 = fmaf(dy, dy, r2);
             r2 = fmaf(dz, dz, r2);
-            // only an ion (t < n_diag) meets its own identity image
-            const float inv = (sidx == t && t < a.n_diag) ? 0.f : rsqrtf(r2);
+            // an ion (t < n_diag) skips its identity image and, on the FP32
+            // path, its own shifted images (added in FP64 by k_self_images)
+            const bool own = (sidx == t && t < a.n_diag) || (unsigned)(sidx - so[k]) < (unsigned)sc[k];
+            const float inv = own ? 0.f : rsqrtf(r2);
             const float qi = s.w * inv;
             p[k] += qi;
             const float q3 = qi * (inv * inv);
@@ -284,6 +313,143 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
         two_sum_add(hx[k], lx[k], gx[k]);
         two_sum_add(hy[k], ly[k], gy[k]);
         two_sum_add(hz[k], lz[k], gz[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int t = t0 + threadIdx.x + k * kPairThreads;
+      if (t < a.n_tgt) {
+        double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+        o[0] = (double)hp[k] + (double)lp[k];
+        o[(size_t)a.ld] = (double)hx[k] + (double)lx[k];
+        o[2 * (size_t)a.ld] = (double)hy[k] + (double)ly[k];
+        o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
+      }
+    }
+  }
+}
+
+// Packed FP32x2 variant: the same per-pair arithmetic on two targets at once
+// with Blackwell's paired FP32 instructions (FADD2/FMUL2/FFMA2), so one issued
+// instruction does the work of two.  Each thread holds 2*NP targets as NP
+// pairs; a shared-memory image is stored twice over, (x, x, y, y) and
+// (z, z, q, q), so every operand is already a pair.
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
+  __shared__ float4 sh[2 * kTile32];
+  const float4* __restrict__ tgt = (const float4*)a.tgt;
+  const float4* __restrict__ src = (const float4*)a.src;
+  constexpr int TPT = 2 * NP;
+  const int ns = a.sc ? a.sc->Ns : a.n_src;
+  int per = (ns + a.n_chunks - 1) / a.n_chunks;
+  per = (per + kTile32 - 1) / kTile32 * kTile32;
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+    const int t0 = tile * kPairThreads * TPT;
+    // pair k holds targets t0 + tid + (2k)*256 and t0 + tid + (2k+1)*256, negated
+    float2 nx[NP], ny[NP], nz[NP];
+    float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+      const int tb = ta + kPairThreads;
+      const float4 va = (ta < a.n_tgt) ? tgt[ta] : make_float4(kFar, kFar, kFar, 0.f);
+      const float4 vb = (tb < a.n_tgt) ? tgt[tb] : make_float4(kFar, kFar, kFar, 0.f);
+      nx[k] = make_float2(-va.x, -vb.x);
+      ny[k] = make_float2(-va.y, -vb.y);
+      nz[k] = make_float2(-va.z, -vb.z);
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
+    int so[TPT], sc[TPT];   // own section-1 image range of each ion target
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int t = t0 + threadIdx.x + k * kPairThreads;
+      const bool ion = a.ioff && t < a.n_diag;
+      so[k] = ion ? a.ioff[t] : 0;
+      sc[k] = ion ? a.icnt[t] : 0;
+    }
+    int lo1 = 0, hi1 = 0;
+    own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
+    const int s0 = chunk * per;
+    const int s1 = min(ns, s0 + per);
+    for (int sb = s0; sb < s1; sb += kTile32) {
+      const int n = min(kTile32, s1 - sb);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += kPairThreads) {
+        const float4 v = src[sb + i];
+        sh[2 * i] = make_float4(v.x, v.x, v.y, v.y);
+        sh[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
+      }
+      __syncthreads();
+      float2 p[NP], gx[NP], gy[NP], gz[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) p[k] = gx[k] = gy[k] = gz[k] = make_float2(0.f, 0.f);
+      const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
+                        (sb < hi1 && lo1 < sb + n);
+      if (!diag) {
+#pragma unroll kUnroll
+        for (int i = 0; i < n; ++i) {
+          const float4 A = sh[2 * i], B = sh[2 * i + 1];
+          const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+          const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const float2 dx = __fadd2_rn(sx, nx[k]);
+            const float2 dy = __fadd2_rn(sy, ny[k]);
+            const float2 dz = __fadd2_rn(sz, nz[k]);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 qi = __fmul2_rn(sq, inv);
+            p[k] = __fadd2_rn(p[k], qi);
+            const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+            gx[k] = __ffma2_rn(q3, dx, gx[k]);
+            gy[k] = __ffma2_rn(q3, dy, gy[k]);
+            gz[k] = __ffma2_rn(q3, dz, gz[k]);
+          }
+        }
+      } else {
+        for (int i = 0; i < n; ++i) {
+          const float4 A = sh[2 * i], B = sh[2 * i + 1];
+          const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+          const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+          const int sidx = sb + i;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+            const int tb = ta + kPairThreads;
+            const float2 dx = __fadd2_rn(sx, nx[k]);
+            const float2 dy = __fadd2_rn(sy, ny[k]);
+            const float2 dz = __fadd2_rn(sz, nz[k]);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            // an ion skips its identity image and its own shifted images
+            const bool owna = (sidx == ta && ta < a.n_diag) || (unsigned)(sidx - so[2 * k]) < (unsigned)sc[2 * k];
+            const bool ownb = (sidx == tb && tb < a.n_diag) || (unsigned)(sidx - so[2 * k + 1]) < (unsigned)sc[2 * k + 1];
+            const float2 inv = make_float2(owna ? 0.f : rsqrtf(r2.x), ownb ? 0.f : rsqrtf(r2.y));
+            const float2 qi = __fmul2_rn(sq, inv);
+            p[k] = __fadd2_rn(p[k], qi);
+            const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+            gx[k] = __ffma2_rn(q3, dx, gx[k]);
+            gy[k] = __ffma2_rn(q3, dy, gy[k]);
+            gz[k] = __ffma2_rn(q3, dz, gz[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        two_sum_add(hp[2 * k], lp[2 * k], p[k].x);
+        two_sum_add(hp[2 * k + 1], lp[2 * k + 1], p[k].y);
+        two_sum_add(hx[2 * k], lx[2 * k], gx[k].x);
+        two_sum_add(hx[2 * k + 1], lx[2 * k + 1], gx[k].y);
+        two_sum_add(hy[2 * k], ly[2 * k], gy[k].x);
+        two_sum_add(hy[2 * k + 1], ly[2 * k + 1], gy[k].y);
+        two_sum_add(hz[2 * k], lz[2 * k], gz[k].x);
+        two_sum_add(hz[2 * k + 1], lz[2 * k + 1], gz[k].y);
       }
     }
 #pragma unroll
@@ -346,15 +512,22 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
   }
 }
 
+// Kernel variants of the FP32 path, by code: 1, 2, 4 = scalar FP32 with that
+// many targets per thread; 12, 14 = packed FP32x2 with 2 or 4 targets.
 int pair_tile_targets(int precision, int tpt) {
-  return precision == 0 ? kPairThreads : kPairThreads * tpt;
+  if (precision == 0) return kPairThreads;
+  return kPairThreads * (tpt > 10 ? tpt - 10 : tpt);
 }
 
 static const void* pair_fn(int precision, int tpt) {
   if (precision == 0) return (const void*)k_pair_f64;
-  if (tpt == 1) return (const void*)k_pair_f32<1>;
-  if (tpt == 2) return (const void*)k_pair_f32<2>;
-  return (const void*)k_pair_f32<4>;
+  switch (tpt) {
+    case 1: return (const void*)k_pair_f32<1>;
+    case 2: return (const void*)k_pair_f32<2>;
+    case 12: return (const void*)k_pair_f32x2<1>;
+    case 14: return (const void*)k_pair_f32x2<2>;
+    default: return (const void*)k_pair_f32<4>;
+  }
 }
 
 int pair_slots(int precision, int tpt) {
@@ -371,6 +544,8 @@ cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream
   if (precision == 0) k_pair_f64<<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 1) k_pair_f32<1><<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 2) k_pair_f32<2><<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 12) k_pair_f32x2<1><<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 14) k_pair_f32x2<2><<<grid, kPairThreads, 0, s>>>(a);
   else k_pair_f32<4><<<grid, kPairThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -430,7 +605,8 @@ constexpr int kAsmThreads = 256;
 
 __global__ void __launch_bounds__(kAsmThreads) k_assemble(const double* part, int n_chunks, int ld,
                                                           const double* fpart, int f_chunks, int fld,
-                                                          const double* q, int N, double pref,
+                                                          const double* self, const double* q, int N,
+                                                          double pref,
                                                           const DevScalars* sc, double* forces,
                                                           double* pot, double* grad, double* blk_e) {
   __shared__ double sh[kAsmThreads];
@@ -443,6 +619,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(const double* part, in
       for (int ch = 0; ch < n_chunks; ++ch) s += part[((size_t)ch * 4 + c) * ld + i];
       double f = 0.0;
       for (int ch = 0; ch < f_chunks; ++ch) f += fpart[((size_t)ch * 4 + c) * fld + i];
+      if (self) s += self[(size_t)c * N + i];
       g[c] = s + f;
     }
     const double qi = q[i] - sc->qcorr;
@@ -474,13 +651,51 @@ __global__ void __launch_bounds__(kScanThreads) k_energy(const double* blk_e, in
 }
 
 cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,
-                            int f_chunks, int fld, const double* q, int N, double pref,
-                            DevScalars* sc, double* forces, double* pot, double* grad,
+                            int f_chunks, int fld, const double* self, const double* q, int N,
+                            double pref, DevScalars* sc, double* forces, double* pot, double* grad,
                             double* blk_e, cudaStream_t s) {
   const int nblk = (N + kAsmThreads - 1) / kAsmThreads;
-  k_assemble<<<nblk, kAsmThreads, 0, s>>>(part, n_chunks, ld, fpart, f_chunks, fld, q, N, pref, sc,
-                                          forces, pot, grad, blk_e);
+  k_assemble<<<nblk, kAsmThreads, 0, s>>>(part, n_chunks, ld, fpart, f_chunks, fld, self, q, N, pref,
+                                          sc, forces, pot, grad, blk_e);
   k_energy<<<1, kScanThreads, 0, s>>>(blk_e, nblk, pref, sc);
+  return cudaGetLastError();
+}
+
+// Every ion's interaction with its own shifted images inside B, in FP64 from
+// the FP64 positions (an ion near a dielectric wall sits very close to its own
+// reflection; FP32 box-centred coordinates cannot resolve that distance).
+// The membership test repeats the prep kernels' FP64 arithmetic exactly.
+__global__ void __launch_bounds__(kPrepThreads) k_self_images(PrepArgs a, double* self) {
+  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
+  if (j >= a.N) return;
+  const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
+  const double qj = a.q[j] - a.sc->qcorr;
+  double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int s = 1; s < a.n_shift; ++s) {
+    const double* sh = a.shifts + 5 * s;
+    const double px = __dadd_rn(xc, sh[0]);
+    const double py = __dadd_rn(yc, sh[1]);
+    const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+    if (r2 < a.Rs2) {
+      const double dx = px - xc, dy = py - yc, dz = pz - zc;
+      const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
+      const double qi = sh[4] * qj * inv;
+      const double q3 = qi * inv * inv;
+      p += qi;
+      gx += q3 * dx;
+      gy += q3 * dy;
+      gz += q3 * dz;
+    }
+  }
+  self[j] = p;
+  self[(size_t)a.N + j] = gx;
+  self[2 * (size_t)a.N + j] = gy;
+  self[3 * (size_t)a.N + j] = gz;
+}
+
+cudaError_t launch_self_images(const PrepArgs& a, double* self, cudaStream_t s) {
+  k_self_images<<<(a.N + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a, self);
   return cudaGetLastError();
 }
 

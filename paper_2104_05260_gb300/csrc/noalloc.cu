@@ -98,7 +98,7 @@ extern "C" int hsma_pair_sum_static(const double* targets, int64_t n_tgt, const 
     cudaGetLastError();
     return HSMA_ERR_CUDA;
   }
-  const int tpt = 2;
+  const int tpt = 12;  // packed FP32x2 pair kernel
   const int tile = pair_tile_targets(precision, tpt);
   const int slots = pair_slots(precision, tpt);
   const int tiles = (int)((n_tgt + tile - 1) / tile);
