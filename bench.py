@@ -146,6 +146,102 @@ def oracle_sample(c, x, q, n_targets, seed=99):
                         t_targets=t3 - t2, Ns=len(iq))
 
 
+def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None):
+    """Served workload: independent HSMA3D requests, Poisson arrivals.
+
+    Requests: neutral +-1 electrolytes at density 0.1, N log-uniform in
+    [1000, 50000] (even), p in {6, 8, 10}, M = 4 p^2 + 400.  The arrival rate
+    is 0.8 x the one-at-a-time FP32 capacity measured here on a sample of the
+    same requests.  Reports served evals/s, p50/p99 latency (completion -
+    arrival, host clock) and the one-at-a-time FP64 and FP32 forms on a
+    stratified sample, extrapolated to the whole stream.
+    """
+    shapes = workloads.serving_stream(n_req, seed=seed)
+    reqs = []
+    for r in shapes:
+        c = workloads.small_case(r["N"], dims=3, box=r["box"], p=r["p"], M=r["M"], seed=r["seed"])
+        x, q = workloads.electrolyte(c)
+        reqs.append((c, x, q))
+    order = np.argsort([c.N for c, _, _ in reqs])
+    sample = order[np.linspace(0, n_req - 1, n_sample).astype(int)]
+
+    def one_at_a_time(prec, idx):
+        hs = {}
+        res = {}
+        for i in idx:
+            c, x, q = reqs[i]
+            h = P.HSMA(c.box, 3, c.p, c.M, precision=prec)
+            h.eval(x, q)                       # set-up + warm-up, untimed
+            t0 = time.perf_counter()
+            E, F, _ = h.eval(x, q)
+            res[i] = (time.perf_counter() - t0, E, F)
+            h.close()
+        return res
+
+    r32 = one_at_a_time(1, sample)
+    r64 = one_at_a_time(0, sample)
+    # the sample is stratified by N: scale its mean to the whole stream
+    t32 = np.mean([r32[i][0] for i in sample])
+    t64 = np.mean([r64[i][0] for i in sample])
+    rate = 0.8 / t32
+    arrivals = workloads.poisson_arrivals(n_req, rate, seed=seed)
+
+    server = P.hsma_server_create(slots, budget, 1)
+    for p in (6, 8, 10):                       # build the three unit geometries, untimed
+        c, x, q = next(r for r in reqs if r[0].p == p)
+        t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
+        while P.hsma_poll(server, t, c.N) is None:
+            pass
+    tickets = [None] * n_req
+    done_t = np.zeros(n_req)
+    out = [None] * n_req
+    nxt = 0
+    pending = set()
+    t_start = time.perf_counter()
+    while nxt < n_req or pending:
+        now = time.perf_counter() - t_start
+        while nxt < n_req and arrivals[nxt] <= now:
+            c, x, q = reqs[nxt]
+            tickets[nxt] = P.hsma_submit(server, x, q, c.box, c.p, c.M)
+            pending.add(nxt)
+            nxt += 1
+        for i in list(pending):
+            r = P.hsma_poll(server, tickets[i], reqs[i][0].N)
+            if r is not None:
+                done_t[i] = time.perf_counter() - t_start
+                out[i] = r
+                pending.discard(i)
+        if not pending and nxt < n_req:
+            time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t_start))))
+    P.hsma_destroy(server)
+    lat = (done_t - arrivals) * 1e3
+    span = done_t.max() - arrivals[0]
+    de = [abs(out[i][0] - r64[i][1]) / abs(r64[i][1]) for i in sample]
+    # the same error against the energy scale 1/2 sum |q_i Phi_i| (|E| itself can
+    # nearly cancel in a random neutral configuration)
+    des = []
+    for i in sample:
+        c, x, q = reqs[i]
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=0)
+        _, _, pot = h.eval(x, q, forces=False, potential=True)
+        h.close()
+        des.append(abs(out[i][0] - r64[i][1]) / (0.5 * float(np.sum(np.abs(q * pot)))))
+    df = [math.sqrt(np.mean(np.sum((out[i][1] - r64[i][2]) ** 2, 1)) / np.mean(np.sum(r64[i][2] ** 2, 1)))
+          for i in sample]
+    return {"workload": f"{n_req} requests, N log-uniform [1e3, 5e4], p in {{6,8,10}}, M = 4p^2+400, "
+                        f"rho = 0.1, Poisson arrivals at {rate:.1f}/s (0.8 x one-at-a-time FP32 capacity)",
+            "slots": slots, "budget_bytes": budget,
+            "evals_per_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_N": float(np.mean([c.N for c, _, _ in reqs])),
+            "one_at_a_time_fp64_evals_per_s": 1.0 / t64, "one_at_a_time_fp32_evals_per_s": 1.0 / t32,
+            "served_vs_fp64": (n_req / span) * t64,
+            "sample": f"{n_sample} requests stratified by N, timed one at a time",
+            "max_rel_energy_err_vs_fp64": float(max(de)),
+            "median_rel_energy_err_vs_fp64": float(np.median(de)),
+            "max_energy_err_over_energy_scale": float(max(des)),
+            "max_rel_force_rms_vs_fp64": float(max(df))}
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -184,6 +280,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     c = workloads.case(2)
@@ -341,6 +438,8 @@ def main():
             "sampled_ions": 400,
             "rel_force_rms": float(math.sqrt(np.mean(np.sum((Fg - Fo) ** 2, 1)) / np.mean(np.sum(Fo ** 2, 1)))),
             "rel_energy_vs_fp64_gpu": fp64["fp32_vs_fp64_rel_energy"] if fp64 else None}
+    if not args.no_serve:
+        line["serve"] = serve_bench(P)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -204,14 +204,19 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   return HSMA_OK;
 }
 
-// Enqueue one evaluation on h->stream; inputs already in d_x, d_q.
-int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
+// Geometry arrays on the device: the handle's own, or a shared unit-box
+// geometry (serving) that the kernels scale by h->gscale.
+static const double* geo_P(hsma_ctx* h) { return h->ext_P ? h->ext_P : (const double*)h->d_P.p; }
+static const double* geo_W(hsma_ctx* h) { return h->ext_W ? h->ext_W : (const double*)h->d_W.p; }
+static const double* geo_Y(hsma_ctx* h) { return h->ext_Y ? h->ext_Y : (const double*)h->d_ysurf.p; }
+static const double* geo_C(hsma_ctx* h) { return h->ext_C ? h->ext_C : (const double*)h->d_check.p; }
+
+// Stage 1: wrap/centre, sphere membership, image list, check-point targets
+// (and on the FP32 path each ion's own images in FP64).
+int stage_prep(hsma_ctx* h, int64_t N) {
   const Geometry& g = h->geo;
   const int prec = h->precision;
-  const int tpt = (prec == 0) ? 1 : h->tpt;
   cudaStream_t s = h->stream;
-  const bool tm = h->timing != 0;
-  if (tm) cudaEventRecord(h->ev[0], s);
   cudaMemsetAsync(h->d_sc.p, 0, sizeof(DevScalars), s);
   PrepArgs a;
   a.x = (const double*)h->d_x.p;
@@ -222,8 +227,9 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   a.Rs2 = g.Rs2;
   a.shifts = (const double*)h->d_shifts.p;
   a.n_shift = (int)g.shifts.size();
-  a.check_pts = (const double*)h->d_check.p;
+  a.check_pts = geo_C(h);
   a.n_check = g.n_check;
+  a.cscale = h->gscale;
   a.xc = (double*)h->d_xc.p;
   a.cnt = (int*)h->d_cnt.p;
   a.blk = (int*)h->d_blk.p;
@@ -241,8 +247,13 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   // skipped by the FP32 pair kernel
   if (e == cudaSuccess && prec) e = launch_self_images(a, (double*)h->d_self.p, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "prep launch");
-  if (tm) cudaEventRecord(h->ev[1], s);
+  return HSMA_OK;
+}
 
+// Stage 2 arguments: near field + check points (targets: ions then check
+// points; sources: the images in B, counted on the device).
+PairArgs near_args(hsma_ctx* h, int64_t N) {
+  const int prec = h->precision;
   PairArgs p1;
   p1.tgt = prec ? (const void*)h->d_tgt32.p : (const void*)h->d_tgt64.p;
   p1.n_tgt = h->n_tgt1;
@@ -256,42 +267,77 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   p1.ld = h->n_tgt1;
   p1.ioff = prec ? (const int*)h->d_ioff.p : nullptr;
   p1.icnt = prec ? (const int*)h->d_cnt.p : nullptr;
-  e = launch_pair(prec, tpt, p1, h->grid1, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
-  if (tm) cudaEventRecord(h->ev[2], s);
+  return p1;
+}
 
-  e = launch_fit(g.par.dims, (const double*)h->d_part.p, h->chunks1, h->n_tgt1, (int)N, g.n_check,
-                 (const double*)h->d_P.p, g.nA, g.nv, (const double*)h->d_W.p, g.par.M,
-                 (const double*)h->d_ysurf.p, (double*)h->d_v.p, (double*)h->d_A.p,
-                 (double*)h->d_cphi.p, (double*)h->d_cdz.p, (double*)h->d_Q.p,
-                 prec ? (float4*)h->d_s32.p : nullptr, prec ? nullptr : (double4_32a*)h->d_s64.p, s);
+// Stage 3: combine the check-point partials, A = P v, Q = W A (FP64).
+int stage_fit(hsma_ctx* h, int64_t N) {
+  const Geometry& g = h->geo;
+  const int prec = h->precision;
+  cudaError_t e = launch_fit(g.par.dims, (const double*)h->d_part.p, h->chunks1, h->n_tgt1, (int)N,
+                             g.n_check, geo_P(h), g.nA, g.nv, geo_W(h), g.par.M, geo_Y(h), h->gscale,
+                             (double*)h->d_v.p, (double*)h->d_A.p, (double*)h->d_cphi.p,
+                             (double*)h->d_cdz.p, (double*)h->d_Q.p,
+                             prec ? (float4*)h->d_s32.p : nullptr,
+                             prec ? nullptr : (double4_32a*)h->d_s64.p, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "fit launch");
-  if (tm) cudaEventRecord(h->ev[3], s);
+  return HSMA_OK;
+}
 
+// Stage 4 arguments: far field (targets: ions; sources: surface charges).
+PairArgs far_args(hsma_ctx* h, int64_t N) {
+  const int prec = h->precision;
   PairArgs p2;
-  p2.tgt = p1.tgt;
+  p2.tgt = prec ? (const void*)h->d_tgt32.p : (const void*)h->d_tgt64.p;
   p2.n_tgt = (int)N;
   p2.src = prec ? (const void*)h->d_s32.p : (const void*)h->d_s64.p;
-  p2.n_src = g.par.M;
+  p2.n_src = h->geo.par.M;
   p2.sc = nullptr;
   p2.n_diag = 0;
   p2.n_tiles = h->tiles2;
   p2.n_chunks = h->chunks2;
   p2.part = (double*)h->d_fpart.p;
   p2.ld = (int)N;
-  e = launch_pair(prec, tpt, p2, h->grid2, s);
+  return p2;
+}
+
+// Stage 5: potentials, forces, energy; scalars back to pinned host memory.
+int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
+  const int prec = h->precision;
+  cudaError_t e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1,
+                                  (const double*)h->d_fpart.p, h->chunks2, (int)N,
+                                  prec ? (const double*)h->d_self.p : nullptr,
+                                  (const double*)h->d_q.p, (int)N, h->pref, (DevScalars*)h->d_sc.p,
+                                  forces_dev, pot_dev, (double*)h->d_grad.p, (double*)h->d_blke.p,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_sc, h->d_sc.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble launch");
+  return HSMA_OK;
+}
+
+// Enqueue one evaluation on h->stream; inputs already in d_x, d_q.
+int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
+  const int prec = h->precision;
+  const int tpt = (prec == 0) ? 1 : h->tpt;
+  cudaStream_t s = h->stream;
+  const bool tm = h->timing != 0;
+  if (tm) cudaEventRecord(h->ev[0], s);
+  int rc = stage_prep(h, N);
+  if (rc) return rc;
+  if (tm) cudaEventRecord(h->ev[1], s);
+  cudaError_t e = launch_pair(prec, tpt, near_args(h, N), h->grid1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
+  if (tm) cudaEventRecord(h->ev[2], s);
+  rc = stage_fit(h, N);
+  if (rc) return rc;
+  if (tm) cudaEventRecord(h->ev[3], s);
+  e = launch_pair(prec, tpt, far_args(h, N), h->grid2, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "far launch");
   if (tm) cudaEventRecord(h->ev[4], s);
-
-  e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1, (const double*)h->d_fpart.p,
-                      h->chunks2, (int)N, prec ? (const double*)h->d_self.p : nullptr,
-                      (const double*)h->d_q.p, (int)N, h->pref,
-                      (DevScalars*)h->d_sc.p, forces_dev, pot_dev, (double*)h->d_grad.p,
-                      (double*)h->d_blke.p, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "assemble launch");
+  rc = stage_assemble(h, N, forces_dev, pot_dev);
+  if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[5], s);
-  e = cudaMemcpyAsync(h->h_sc, h->d_sc.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "result copy");
   return HSMA_OK;
 }
 

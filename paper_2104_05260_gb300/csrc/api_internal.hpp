@@ -57,6 +57,13 @@ struct hsma_ctx {
   int64_t last_N = 0;
   int last_Ns = 0;
   hsma::Server* srv = nullptr;
+  // shared geometry arrays (serving): used instead of d_P, d_W, d_ysurf,
+  // d_check when set; check points, W and surface points are scaled by gscale
+  const double* ext_P = nullptr;
+  const double* ext_W = nullptr;
+  const double* ext_Y = nullptr;
+  const double* ext_C = nullptr;
+  double gscale = 1.0;
   ~hsma_ctx();
 };
 
@@ -64,5 +71,11 @@ int hsma_ctx_init(hsma_ctx* h);
 int ensure_geometry(hsma_ctx* h);
 int ensure_plan(hsma_ctx* h, int64_t N);
 int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev);
+int stage_prep(hsma_ctx* h, int64_t N);
+hsma::PairArgs near_args(hsma_ctx* h, int64_t N);
+int stage_fit(hsma_ctx* h, int64_t N);
+hsma::PairArgs far_args(hsma_ctx* h, int64_t N);
+int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev);
+int plan_for(hsma_ctx* h, int64_t N);
 int finish_eval(hsma_ctx* h, double* energy);
 void server_shutdown(hsma_ctx* h);

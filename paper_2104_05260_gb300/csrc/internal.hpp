@@ -28,8 +28,9 @@ struct PrepArgs {
   double Rs2;
   const double* shifts;  // n_shift*5 (sx, sy, zs, zo, f); identity first
   int n_shift;
-  const double* check_pts;  // n_check*3 (box-centred)
+  const double* check_pts;  // n_check*3 (box-centred), multiplied by cscale
   int n_check;
+  double cscale;
   double* xc;            // N*3 box-centred FP64 positions
   int* cnt;              // N: non-identity images of each source inside B
   int* blk;              // per-block image counts -> exclusive offsets
@@ -73,10 +74,16 @@ int pair_tile_targets(int precision, int tpt);
 cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s);
 cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s);
 int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
+// One launch over several packed-FP32 pair sums (descs and start in device
+// memory; start has n_desc + 1 entries, start[n_desc] = total items).
+cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
+                               cudaStream_t s);
+int pair_ragged_slots();
+// scale multiplies W and ysurf (a geometry built for the box divided by scale)
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
                        const double* P, int nA, int nv, const double* W, int M,
-                       const double* ysurf, double* v, double* A, double* cphi, double* cdz,
-                       double* Q, float4* s32, double4_32a* s64, cudaStream_t s);
+                       const double* ysurf, double scale, double* v, double* A, double* cphi,
+                       double* cdz, double* Q, float4* s32, double4_32a* s64, cudaStream_t s);
 cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,
                             int f_chunks, int fld, const double* self, const double* q, int N,
                             double pref, DevScalars* sc, double* forces, double* pot, double* grad,

@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
   }
   if (j < a.n_check) {
     const double* cp = a.check_pts + 3 * (size_t)j;
-    if (a.tgt32) a.tgt32[a.N + j] = make_float4((float)cp[0], (float)cp[1], (float)cp[2], 0.f);
-    if (a.tgt64) a.tgt64[a.N + j] = make_double4_32a(cp[0], cp[1], cp[2], 0.0);
+    const double c0 = a.cscale * cp[0], c1 = a.cscale * cp[1], c2 = a.cscale * cp[2];
+    if (a.tgt32) a.tgt32[a.N + j] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
+    if (a.tgt64) a.tgt64[a.N + j] = make_double4_32a(c0, c1, c2, 0.0);
   }
 }
 
@@ -335,16 +336,14 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
 // pairs; a shared-memory image is stored twice over, (x, x, y, y) and
 // (z, z, q, q), so every operand is already a pair.
 template <int NP>
-__global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
-  __shared__ float4 sh[2 * kTile32];
+__device__ __forceinline__ void pair_item_f32x2(const PairArgs& a, int item, float4* sh) {
   const float4* __restrict__ tgt = (const float4*)a.tgt;
   const float4* __restrict__ src = (const float4*)a.src;
   constexpr int TPT = 2 * NP;
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  {
     const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
     const int t0 = tile * kPairThreads * TPT;
     // pair k holds targets t0 + tid + (2k)*256 and t0 + tid + (2k+1)*256, negated
@@ -466,6 +465,46 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
   }
 }
 
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
+  __shared__ float4 sh[2 * kTile32];
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2<NP>(a, item, sh);
+}
+
+// Ragged launch over several independent pair sums (requests of the serving
+// loop): item i belongs to the descriptor d with start[d] <= i < start[d+1].
+// Each item writes only its own descriptor's partials, so every request's
+// result is the same whatever else shares the launch.
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged(const PairArgs* __restrict__ descs,
+                                                             const int* __restrict__ start,
+                                                             int n_desc) {
+  __shared__ float4 sh[2 * kTile32];
+  const int total = start[n_desc];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int d = 0;
+    while (d + 1 < n_desc && start[d + 1] <= item) ++d;
+    const PairArgs a = descs[d];
+    pair_item_f32x2<NP>(a, item - start[d], sh);
+  }
+}
+
+cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
+                               cudaStream_t s) {
+  if (grid < 1) grid = 1;
+  k_pair_ragged<1><<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
+  return cudaGetLastError();
+}
+
+int pair_ragged_slots() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged<1>, kPairThreads, 0);
+  return sms * (per < 1 ? 1 : per);
+}
+
 __global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
   __shared__ double4_32a sh[kTile64];
   const double4_32a* __restrict__ tgt = (const double4_32a*)a.tgt;
@@ -578,25 +617,26 @@ __global__ void __launch_bounds__(kFitThreads) k_gemv_rows(const double* P, int 
 }
 
 __global__ void k_surface(const double* W, int M, int nA, const double* A, const double* ysurf,
-                          double* Q, float4* s32, double4_32a* s64) {
+                          double scale, double* Q, float4* s32, double4_32a* s64) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   double s = 0.0;
   const double* w = W + (size_t)m * nA;
   for (int r = 0; r < nA; ++r) s += w[r] * A[r];
+  s *= scale;   // W and the surface points of a geometry built for a box scaled by 1/scale
   Q[m] = s;
-  const double x = ysurf[3 * m], y = ysurf[3 * m + 1], z = ysurf[3 * m + 2];
+  const double x = scale * ysurf[3 * m], y = scale * ysurf[3 * m + 1], z = scale * ysurf[3 * m + 2];
   if (s32) s32[m] = make_float4((float)x, (float)y, (float)z, (float)s);
   if (s64) s64[m] = make_double4_32a(x, y, z, s);
 }
 
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
                        const double* P, int nA, int nv, const double* W, int M,
-                       const double* ysurf, double* v, double* A, double* cphi, double* cdz,
-                       double* Q, float4* s32, double4_32a* s64, cudaStream_t s) {
+                       const double* ysurf, double scale, double* v, double* A, double* cphi,
+                       double* cdz, double* Q, float4* s32, double4_32a* s64, cudaStream_t s) {
   k_check_combine<<<(n_check + 255) / 256, 256, 0, s>>>(part, n_chunks, ld, N, n_check, dims, v, cphi, cdz);
   k_gemv_rows<<<nA, kFitThreads, 0, s>>>(P, nv, v, A);
-  k_surface<<<(M + 127) / 128, 128, 0, s>>>(W, M, nA, A, ysurf, Q, s32, s64);
+  k_surface<<<(M + 127) / 128, 128, 0, s>>>(W, M, nA, A, ysurf, scale, Q, s32, s64);
   return cudaGetLastError();
 }
 

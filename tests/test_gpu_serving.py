@@ -1,0 +1,109 @@
+"""The request loop (hsma_submit / hsma_poll): served results against the
+regular evaluation and the oracle, bitwise identity of a request alone and in
+a mix, and admission by the device-memory budget."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import hsma as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def request(N, p, seed):
+    L = (N / 0.1) ** (1 / 3)
+    c = workloads.small_case(N, dims=3, box=(L, L, L), p=p, M=4 * p * p + 400, seed=seed)
+    x, q = workloads.electrolyte(c)
+    return c, x, q
+
+
+def serve_all(P, server, reqs):
+    tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
+    out = [None] * len(reqs)
+    for _ in range(200000):
+        for i, t in enumerate(tickets):
+            if out[i] is None:
+                out[i] = P.hsma_poll(server, t, reqs[i][0].N)
+        if all(o is not None for o in out):
+            return out
+    raise AssertionError("requests did not finish")
+
+
+def frms(F, Fr):
+    return math.sqrt(np.mean(np.sum((F - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1)))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_served_results_match_eval_and_oracle(P, prec):
+    reqs = [request(N, p, s) for N, p, s in ((1000, 6, 1), (3000, 8, 2), (514, 10, 3), (8000, 6, 4))]
+    server = P.hsma_server_create(8, 4e9, prec)
+    out = serve_all(P, server, reqs)
+    P.hsma_destroy(server)
+    for (c, x, q), (E, F) in zip(reqs, out):
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=prec)
+        E0, F0, _ = h.eval(x, q)
+        h.close()
+        assert abs(E - E0) <= 1e-9 * abs(E0)
+        assert frms(F, F0) <= 1e-8
+    c, x, q = reqs[0]
+    ref = O.evaluate(O.make_setup(c.box, 3, c.p, c.M), x, q)
+    tol = 1e-6 if prec == 0 else 1e-5
+    assert abs(out[0][0] - ref["energy"]) <= tol * abs(ref["energy"])
+
+
+def test_request_is_bitwise_the_same_alone_and_in_a_mix(P):
+    a = request(2000, 8, 11)
+    others = [request(N, p, s) for N, p, s in ((6000, 10, 12), (1200, 6, 13), (20000, 8, 14))]
+    s1 = P.hsma_server_create(8, 8e9, 1)
+    Ea, Fa = serve_all(P, s1, [a])[0]
+    P.hsma_destroy(s1)
+    s2 = P.hsma_server_create(8, 8e9, 1)
+    mix = serve_all(P, s2, [others[0], a, others[1], others[2]])
+    P.hsma_destroy(s2)
+    Eb, Fb = mix[1]
+    assert Ea == Eb and np.array_equal(Fa, Fb)
+
+
+def test_admission_by_budget(P):
+    reqs = [request(N, 6, s) for N, s in ((1000, 21), (1500, 22), (800, 23))]
+    # too small for any request
+    tiny = P.hsma_server_create(4, 1e5, 1)
+    with pytest.raises(P.HSMAError) as e:
+        P.hsma_submit(tiny, reqs[0][1], reqs[0][2], reqs[0][0].box, 6, 544)
+    assert e.value.code == -5
+    P.hsma_destroy(tiny)
+    # room for one request at a time: all still finish, one after another
+    one = P.hsma_server_create(4, 4e8, 1)
+    out = serve_all(P, one, reqs)
+    P.hsma_destroy(one)
+    for (c, x, q), (E, F) in zip(reqs, out):
+        h = P.HSMA(c.box, 3, c.p, c.M)
+        E0, _, _ = h.eval(x, q)
+        h.close()
+        assert abs(E - E0) <= 1e-9 * abs(E0)
+
+
+def test_submit_rejects_bad_requests(P):
+    server = P.hsma_server_create(2, 1e9, 1)
+    c, x, q = request(100, 6, 31)
+    q2 = q.copy(); q2[0] += 1.0
+    with pytest.raises(P.HSMAError) as e:
+        P.hsma_submit(server, x, q2, c.box, 6, 544)
+    assert e.value.code == -2
+    with pytest.raises(P.HSMAError) as e:
+        P.hsma_submit(server, x, q, c.box, 6, 10)
+    assert e.value.code == -1
+    with pytest.raises(P.HSMAError):
+        P.hsma_poll(server, 12345, 100)
+    P.hsma_destroy(server)
