@@ -259,6 +259,53 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
             "max_rel_force_rms_vs_fp64": float(max(df))}
 
 
+def other_cases(P, torch, dev, stream):
+    """Evaluations/s of the other workload shapes (inputs resident in HBM),
+    FP32 and FP64 paths, with the FP32 energy error against the FP64 path."""
+    out = {}
+    cases = [(workloads.case(1), 20, 5), (workloads.case(3, -0.95), 20, 3),
+             (workloads.case(3, 0.0), 20, 3), (workloads.case(3, 0.95), 20, 3),
+             (workloads.case(5), 5, 0)]
+    for c, n32, n64 in cases:
+        x, q = workloads.electrolyte(c)
+        xd = torch.from_numpy(x).to(dev)
+        qd = torch.from_numpy(q).to(dev)
+        fd = torch.empty((c.N, 3), dtype=torch.float64, device=dev)
+        rec = {"N": c.N, "p": c.p, "M": c.M}
+        energies = {}
+        for prec, n in ((1, n32), (0, n64)):
+            if n == 0:
+                continue
+            h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=prec,
+                       dtn_grid=c.dtn_grid)
+            P.hsma_set_stream(h.h, stream.cuda_stream)
+            e = np.zeros(1)
+            for _ in range(2):
+                P.hsma_eval_into(h.h, xd, qd, c.N, e, fd)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                P.hsma_eval_into(h.h, xd, qd, c.N, e, fd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / n
+            key = "fp32" if prec else "fp64"
+            rec[key + "_evals_per_s"] = 1e3 / ms
+            if prec:
+                Ns = int(P.hsma_get_info(h.h, "Ns"))
+                nck = int(P.hsma_get_info(h.h, "n_check"))
+                rec["N_s"] = Ns
+                rec["pairs_per_eval"] = (c.N + nck) * Ns + c.N * c.M
+                rec["fp32_pair_ints_per_s"] = rec["pairs_per_eval"] * 1e3 / ms
+            energies[prec] = float(e[0])
+            h.close()
+        if 0 in energies:
+            rec["fp32_vs_fp64_rel_energy"] = abs(energies[1] - energies[0]) / abs(energies[0])
+        out[c.name] = rec
+    return out
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -302,6 +349,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-other-cases", action="store_true")
     ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -364,6 +412,10 @@ def main():
     energy = float(ebuf[0])
     Ns = int(P.hsma_get_info(h.h, "Ns"))
     n_check = int(P.hsma_get_info(h.h, "n_check"))
+    kern = {12: "k_pair_f32x2<1>", 14: "k_pair_f32x2<2>", 1: "k_pair_f32<1>", 2: "k_pair_f32<2>",
+            4: "k_pair_f32<4>"}.get(int(P.hsma_get_info(h.h, "kernel")), "k_pair_f32")
+    plan = {"kernel": kern, "chunks": int(P.hsma_get_info(h.h, "chunks")),
+            "grid": int(P.hsma_get_info(h.h, "grid")), "tile_targets": int(P.hsma_get_info(h.h, "tile_targets"))}
     pairs_near = (N + n_check) * Ns
     pairs_far = N * c.M
     pairs = pairs_near + pairs_far
@@ -416,7 +468,7 @@ def main():
     peak_instr = SMS * FP32_LANES * mhz * 1e6 / 1e12          # T lane-instr/s
     t_near = float(np.mean(near_ms)) / 1e3
     achieved = pairs_near * FP32_INSTR_PER_PAIR / t_near / 1e12
-    roof = {"bound": "alu", "kernel": "k_pair_f32x2<1> (near field + check points)",
+    roof = {"bound": "alu", "kernel": plan["kernel"] + " (near field + check points)",
             "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s",
             "frac": achieved / peak_instr, "traffic": None,
             "flops_view": {"achieved_tflops": pairs_near * FLOP_PER_PAIR / t_near / 1e12,
@@ -441,7 +493,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": c.name, "N": N, "p": c.p, "M": c.M, "lambda": c.lam,
                        "N_s": Ns, "n_check": n_check, "precision": "fp32-compute/fp64-accumulate",
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
+                       "plan": plan},
             "pair_ints_per_s": pairs * ws / (ms_step / 1e3), "pairs_per_eval": pairs,
             "energy": energy, "roofline": roof,
             "e2e": {"value": ws / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": N * 32,
@@ -462,6 +515,8 @@ def main():
             "rel_energy_vs_fp64_gpu": fp64["fp32_vs_fp64_rel_energy"] if fp64 else None}
     if not args.no_serve:
         line["serve"] = serve_bench(P)
+    if not args.no_other_cases:
+        line["other_cases"] = other_cases(P, torch, dev, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -99,7 +99,15 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "coulomb_prefactor" multiplies energy, forces and potential.
  *   "timing"            1 = record per-phase CUDA-event times (hsma_get_info).
  *   "chunks"            source chunks per target tile of the near/check
- *                       launch (0 = automatic).
+ *                       launch (0 = automatic or autotuned).
+ *   "autotune"          1 (default) = on the first evaluation of each N, time
+ *                       the near/check launch for a few kernel variants and
+ *                       chunk counts and keep the fastest (cached per process
+ *                       by N and check-point count); 0 = fixed heuristic.
+ *   "targets_per_thread" kernel variant: 1, 2, 4 (scalar FP32) or 12, 14
+ *                       (packed FP32x2, 2 or 4 targets); turns autotune off.
+ *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
+ *                       CUDA graph captured on the first evaluation of each N.
  * Errors: HSMA_ERR_ARG (unknown key or value out of range).
  */
 int hsma_set_option(hsma_t h, const char* key, double value);
@@ -135,7 +143,7 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * Keys: "Rc", "Rs", "n_shifts", "n_check", "rank", "Ns" (images in B at the
  * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
- * "tile_targets".
+ * "far_chunks", "grid", "slots", "kernel", "tile_targets".
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);

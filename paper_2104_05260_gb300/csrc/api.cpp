@@ -6,7 +6,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -107,6 +110,7 @@ hsma_ctx::~hsma_ctx() {
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
                     &d_blke, &d_sc, &d_ioff, &d_self})
     b->release();
+  if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
   for (int i = 0; i < hsma_ctx::kEvents; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
@@ -164,7 +168,15 @@ int ensure_geometry(hsma_ctx* h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
   h->geo_dirty = false;
   h->plan_N = -1;
+  h->tuned_N = -1;
+  h->tuned_chunks = 0;
   return HSMA_OK;
+}
+
+void drop_graph(hsma_ctx* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->graph_N = -1;
 }
 
 // Launch plan and buffers for N particles.
@@ -180,6 +192,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   h->ns_est = estimate_images(g, N);
   h->chunks1 = h->chunks_opt > 0 ? h->chunks_opt
                                   : choose_chunks(h->tiles1, slots, h->ns_est, prec == 0 ? 512 : 1024);
+  if (h->tuned_chunks > 0 && h->tuned_N == N) h->chunks1 = h->tuned_chunks;
   h->grid1 = (int)std::min<long>((long)h->tiles1 * h->chunks1, slots);
   h->tiles2 = ((int)N + tile - 1) / tile;
   h->chunks2 = choose_chunks(h->tiles2, slots, g.par.M, 256);
@@ -192,7 +205,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
              h->d_cnt.ensure(n * 4) || h->d_blk.ensure(nblk * 4) || h->d_blkq.ensure(nblk * 8) ||
              h->d_blkaq.ensure(nblk * 8) || h->d_forces.ensure(n * 24) || h->d_pot.ensure(n * 8) ||
              h->d_grad.ensure(n * 24) || h->d_blke.ensure(nblk * 8) ||
-             h->d_part.ensure((size_t)h->chunks1 * 4 * nt * 8) ||
+             h->d_part.ensure((size_t)std::max(h->chunks1, h->part_chunks_min) * 4 * nt * 8) ||
              h->d_fpart.ensure((size_t)h->chunks2 * 4 * n * 8);
   if (prec == 0)
     bad = bad || h->d_src64.ensure(simg * 32) || h->d_tgt64.ensure(nt * 32);
@@ -201,6 +214,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
           h->d_ioff.ensure(n * 4) || h->d_self.ensure(n * 32);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
   h->plan_N = N;
+  drop_graph(h);
   return HSMA_OK;
 }
 
@@ -348,7 +362,10 @@ int finish_eval(hsma_ctx* h, double* energy) {
     float t;
     const int pairs[6][2] = {{0, 5}, {0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}};
     for (int i = 0; i < 6; ++i) {
-      cudaEventElapsedTime(&t, h->ev[pairs[i][0]], h->ev[pairs[i][1]]);
+      if (cudaEventElapsedTime(&t, h->ev[pairs[i][0]], h->ev[pairs[i][1]]) != cudaSuccess) {
+        cudaGetLastError();
+        t = -1.f;
+      }
       h->times[i] = t;
     }
   }
@@ -357,6 +374,79 @@ int finish_eval(hsma_ctx* h, double* energy) {
   if (r.flags & FLAG_TIMEOUT) return fail(h, HSMA_ERR_TIMEOUT, "device wait timed out");
   if (energy) *energy = r.energy;
   return HSMA_OK;
+}
+
+// Process-wide cache of tuned near/check launches: (dims, precision, N bucket,
+// check-point bucket) -> (kernel variant, source chunks).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+// Time the near/check launch for each candidate (kernel variant x chunk
+// count) on the real input and keep the fastest.  Inputs are in d_x, d_q.
+static int tune_near(hsma_ctx* h, int64_t N) {
+  const Geometry& g = h->geo;
+  const int prec = h->precision;
+  const auto key = std::make_tuple(g.par.dims, prec, (int)std::lround(4.0 * std::log2((double)N)),
+                                   (int)std::lround(4.0 * std::log2((double)g.n_check + 1.0)));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (prec) h->tpt = it->second.first;
+      h->tuned_chunks = std::max(1, it->second.second);
+      h->tuned_N = N;
+      h->plan_N = -1;
+      return ensure_plan(h, N);
+    }
+  }
+  std::vector<int> tpts = prec ? std::vector<int>{12, 14} : std::vector<int>{1};
+  struct Cand { int tpt, chunks; float ms; };
+  std::vector<Cand> cands;
+  int maxc = 1;
+  for (int tpt : tpts) {
+    const int tile = pair_tile_targets(prec, tpt);
+    const int tiles = (h->n_tgt1 + tile - 1) / tile;
+    const int s0 = choose_chunks(tiles, pair_slots(prec, tpt), h->ns_est, prec == 0 ? 512 : 1024);
+    for (int c : {s0, std::max(1, s0 / 2), 2 * s0}) {
+      bool dup = false;
+      for (const Cand& k : cands) dup |= (k.tpt == tpt && k.chunks == c);
+      if (!dup) cands.push_back({tpt, c, 0.f});
+      maxc = std::max(maxc, c);
+    }
+  }
+  h->part_chunks_min = maxc;
+  h->plan_N = -1;
+  int rc = ensure_plan(h, N);
+  if (rc) return rc;
+  rc = stage_prep(h, N);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  for (size_t ci = 0; ci <= cands.size(); ++ci) {
+    Cand& c = cands[ci == 0 ? 0 : ci - 1];       // the first launch is an untimed warm-up
+    PairArgs a = near_args(h, N);
+    const int tile = pair_tile_targets(prec, c.tpt);
+    a.n_tiles = (h->n_tgt1 + tile - 1) / tile;
+    a.n_chunks = c.chunks;
+    const int grid = (int)std::min<long>((long)a.n_tiles * a.n_chunks, pair_slots(prec, c.tpt));
+    cudaEventRecord(h->ev[0], s);
+    cudaError_t e = launch_pair(prec, prec ? c.tpt : 1, a, grid, s);
+    cudaEventRecord(h->ev[1], s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev[1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    if (ci > 0) cudaEventElapsedTime(&c.ms, h->ev[0], h->ev[1]);
+  }
+  const Cand* best = &cands[0];
+  for (const Cand& c : cands)
+    if (c.ms < best->ms) best = &c;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {best->tpt, best->chunks};
+  }
+  if (prec) h->tpt = best->tpt;
+  h->tuned_chunks = best->chunks;
+  h->tuned_N = N;
+  h->plan_N = -1;
+  return ensure_plan(h, N);
 }
 
 static int eval_impl(hsma_ctx* h, const double* x, const double* q, int64_t N, double* energy,
@@ -373,16 +463,48 @@ static int eval_impl(hsma_ctx* h, const double* x, const double* q, int64_t N, d
   cudaError_t e = cudaMemcpyAsync(h->d_x.p, x, (size_t)N * 24, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q.p, q, (size_t)N * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
+  if (h->autotune && h->chunks_opt == 0 && h->tuned_N != N) {
+    rc = tune_near(h, N);
+    if (rc) return rc;
+  }
   const bool fdev = forces && is_device_ptr(forces);
   const bool pdev = potential && is_device_ptr(potential);
-  rc = enqueue_eval(h, N, fdev ? forces : (double*)h->d_forces.p, pdev ? potential : (double*)h->d_pot.p);
-  if (rc) return rc;
-  if (forces && !fdev) {
-    e = cudaMemcpyAsync(forces, h->d_forces.p, (size_t)N * 24, cudaMemcpyDeviceToHost, s);
+  // per-phase timing records events between the launches, so it runs unrolled
+  const bool graph = h->use_graphs != 0 && h->timing == 0;
+  double* fout = (graph || !fdev) ? (double*)h->d_forces.p : forces;
+  double* pout = (graph || !pdev) ? (double*)h->d_pot.p : potential;
+  if (graph) {
+    if (!h->gexec || h->graph_N != N) {
+      drop_graph(h);
+      cudaGraph_t gr = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+      rc = enqueue_eval(h, N, fout, pout);
+      e = cudaStreamEndCapture(s, &gr);
+      if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (e != cudaSuccess) {
+        h->gexec = nullptr;
+        return cuda_fail(h, e, "graph instantiate");
+      }
+      h->graph_N = N;
+    }
+    e = cudaGraphLaunch(h->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+  } else {
+    rc = enqueue_eval(h, N, fout, pout);
+    if (rc) return rc;
+  }
+  if (forces && fout != forces) {
+    e = cudaMemcpyAsync(forces, fout, (size_t)N * 24, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "force copy");
   }
-  if (potential && !pdev) {
-    e = cudaMemcpyAsync(potential, h->d_pot.p, (size_t)N * 8, cudaMemcpyDeviceToHost, s);
+  if (potential && pout != potential) {
+    e = cudaMemcpyAsync(potential, pout, (size_t)N * 8, cudaMemcpyDefault, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "potential copy");
   }
   e = cudaStreamSynchronize(s);
@@ -438,6 +560,8 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "precision") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "precision must be 0 or 1");
     h->precision = (int)v;
+    h->tuned_N = -1;
+    h->tuned_chunks = 0;
     h->plan_N = -1;
   } else if (k == "dtn_grid") {
     if (!(v >= 4) || v > 1024) return fail(h, HSMA_ERR_ARG, "dtn_grid must be in [4, 1024]");
@@ -446,16 +570,31 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "coulomb_prefactor") {
     if (!std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "prefactor must be finite");
     h->pref = v;
+    drop_graph(h);
   } else if (k == "timing") {
     h->timing = (v != 0);
+    drop_graph(h);
+  } else if (k == "graphs") {
+    h->use_graphs = (v != 0);
+    drop_graph(h);
+  } else if (k == "autotune") {
+    h->autotune = (v != 0);
+    h->tuned_N = -1;
+    h->tuned_chunks = 0;
+    h->plan_N = -1;
   } else if (k == "chunks") {
     if (!(v >= 0) || v > 4096) return fail(h, HSMA_ERR_ARG, "chunks must be in [0, 4096]");
     h->chunks_opt = (int)v;
+    h->tuned_N = -1;
+    h->tuned_chunks = 0;
     h->plan_N = -1;
   } else if (k == "targets_per_thread") {
     if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14)
       return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2, 4 (scalar) or 12, 14 (packed)");
     h->tpt = (int)v;
+    h->autotune = 0;          // an explicit kernel choice turns tuning off
+    h->tuned_N = -1;
+    h->tuned_chunks = 0;
     h->plan_N = -1;
   } else {
     return fail(h, HSMA_ERR_ARG, "unknown option " + k);
@@ -507,6 +646,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "t_far_ms") *value = h->times[4];
   else if (k == "t_assemble_ms") *value = h->times[5];
   else if (k == "chunks") *value = h->chunks1;
+  else if (k == "kernel") *value = h->precision ? h->tpt : 0;
   else if (k == "far_chunks") *value = h->chunks2;
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;

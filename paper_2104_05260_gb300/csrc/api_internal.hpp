@@ -64,6 +64,16 @@ struct hsma_ctx {
   const double* ext_Y = nullptr;
   const double* ext_C = nullptr;
   double gscale = 1.0;
+  // CUDA graph of the per-evaluation pipeline (prep .. assembly), valid for
+  // graph_N particles under the current plan and options
+  int use_graphs = 1;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_N = -1;
+  // autotuning of the near/check launch (kernel variant, source chunks)
+  int autotune = 1;
+  int64_t tuned_N = -1;
+  int tuned_chunks = 0;
+  int part_chunks_min = 0;   // d_part holds at least this many chunks
   ~hsma_ctx();
 };
 
@@ -76,6 +86,6 @@ hsma::PairArgs near_args(hsma_ctx* h, int64_t N);
 int stage_fit(hsma_ctx* h, int64_t N);
 hsma::PairArgs far_args(hsma_ctx* h, int64_t N);
 int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev);
-int plan_for(hsma_ctx* h, int64_t N);
+void drop_graph(hsma_ctx* h);
 int finish_eval(hsma_ctx* h, double* energy);
 void server_shutdown(hsma_ctx* h);

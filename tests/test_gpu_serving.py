@@ -50,12 +50,15 @@ def test_served_results_match_eval_and_oracle(P, prec):
     server = P.hsma_server_create(8, 4e9, prec)
     out = serve_all(P, server, reqs)
     P.hsma_destroy(server)
+    # the server uses the fixed launch plan and a scaled unit-box geometry;
+    # hsma_eval may autotune its chunking: equal up to summation order
+    tol = {0: (1e-12, 1e-11), 1: (1e-6, 1e-5)}[prec]
     for (c, x, q), (E, F) in zip(reqs, out):
         h = P.HSMA(c.box, 3, c.p, c.M, precision=prec)
         E0, F0, _ = h.eval(x, q)
         h.close()
-        assert abs(E - E0) <= 1e-9 * abs(E0)
-        assert frms(F, F0) <= 1e-8
+        assert abs(E - E0) <= tol[0] * abs(E0)
+        assert frms(F, F0) <= tol[1]
     c, x, q = reqs[0]
     ref = O.evaluate(O.make_setup(c.box, 3, c.p, c.M), x, q)
     tol = 1e-6 if prec == 0 else 1e-5
@@ -91,7 +94,7 @@ def test_admission_by_budget(P):
         h = P.HSMA(c.box, 3, c.p, c.M)
         E0, _, _ = h.eval(x, q)
         h.close()
-        assert abs(E - E0) <= 1e-9 * abs(E0)
+        assert abs(E - E0) <= 1e-6 * abs(E0)
 
 
 def test_submit_rejects_bad_requests(P):
