@@ -108,7 +108,7 @@ hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
-                    &d_blke, &d_sc, &d_ioff, &d_self})
+                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -179,6 +179,8 @@ void drop_graph(hsma_ctx* h) {
   h->graph_N = -1;
 }
 
+int mask_words(const Geometry& g) { return std::max<int>(1, ((int)g.shifts.size() - 1 + 31) / 32); }
+
 // Launch plan and buffers for N particles.
 int ensure_plan(hsma_ctx* h, int64_t N) {
   if (h->plan_N == N) return HSMA_OK;
@@ -191,16 +193,17 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   h->tiles1 = (h->n_tgt1 + tile - 1) / tile;
   h->ns_est = estimate_images(g, N);
   h->chunks1 = h->chunks_opt > 0 ? h->chunks_opt
-                                  : choose_chunks(h->tiles1, slots, h->ns_est, prec == 0 ? 512 : 1024);
+                                  : choose_chunks(h->tiles1, slots, h->ns_est, prec == 0 ? 128 : 256);
   if (h->tuned_chunks > 0 && h->tuned_N == N) h->chunks1 = h->tuned_chunks;
   h->grid1 = (int)std::min<long>((long)h->tiles1 * h->chunks1, slots);
   h->tiles2 = ((int)N + tile - 1) / tile;
-  h->chunks2 = choose_chunks(h->tiles2, slots, g.par.M, 256);
+  h->chunks2 = choose_chunks(h->tiles2, slots, g.par.M, 128);
   h->grid2 = (int)std::min<long>((long)h->tiles2 * h->chunks2, slots);
   h->slots = slots;
   const size_t n = (size_t)N, nt = (size_t)h->n_tgt1;
-  const size_t nblk = (n + 255) / 256;
+  const size_t nblk = (size_t)prep_blocks((int)n, g.n_check) + (n + 255) / 256;
   const size_t simg = n * g.shifts.size();  // upper bound on images in B
+  if (h->d_mask.ensure(n * 4 * (size_t)mask_words(g))) return fail(h, HSMA_ERR_NOMEM, "mask buffer");
   bool bad = h->d_x.ensure(n * 24) || h->d_q.ensure(n * 8) || h->d_xc.ensure(n * 24) ||
              h->d_cnt.ensure(n * 4) || h->d_blk.ensure(nblk * 4) || h->d_blkq.ensure(nblk * 8) ||
              h->d_blkaq.ensure(nblk * 8) || h->d_forces.ensure(n * 24) || h->d_pot.ensure(n * 8) ||
@@ -255,11 +258,13 @@ int stage_prep(hsma_ctx* h, int64_t N) {
   a.src64 = prec ? nullptr : (double4_32a*)h->d_src64.p;
   a.tgt64 = prec ? nullptr : (double4_32a*)h->d_tgt64.p;
   a.ioff = prec ? (int*)h->d_ioff.p : nullptr;
+  a.mask = (unsigned*)h->d_mask.p;
+  a.mwords = mask_words(g);
+  // FP32 path: each ion's own shifted images are summed in FP64 by the prep
+  // kernels and skipped by the FP32 pair kernel
+  a.self = prec ? (double*)h->d_self.p : nullptr;
   const int nblk = (int)((N + 255) / 256);
   cudaError_t e = launch_prep(a, nblk, s);
-  // FP32 path: each ion's own shifted images are summed in FP64 here and
-  // skipped by the FP32 pair kernel
-  if (e == cudaSuccess && prec) e = launch_self_images(a, (double*)h->d_self.p, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "prep launch");
   return HSMA_OK;
 }
@@ -399,15 +404,15 @@ static int tune_near(hsma_ctx* h, int64_t N) {
       return ensure_plan(h, N);
     }
   }
-  std::vector<int> tpts = prec ? std::vector<int>{12, 14} : std::vector<int>{1};
+  std::vector<int> tpts = prec ? std::vector<int>{12, 14, 1} : std::vector<int>{1};
   struct Cand { int tpt, chunks; float ms; };
   std::vector<Cand> cands;
   int maxc = 1;
   for (int tpt : tpts) {
     const int tile = pair_tile_targets(prec, tpt);
     const int tiles = (h->n_tgt1 + tile - 1) / tile;
-    const int s0 = choose_chunks(tiles, pair_slots(prec, tpt), h->ns_est, prec == 0 ? 512 : 1024);
-    for (int c : {s0, std::max(1, s0 / 2), 2 * s0}) {
+    const int s0 = choose_chunks(tiles, pair_slots(prec, tpt), h->ns_est, prec == 0 ? 128 : 256);
+    for (int c : {s0, std::max(1, s0 / 2), 2 * s0, 4 * s0}) {
       bool dup = false;
       for (const Cand& k : cands) dup |= (k.tpt == tpt && k.chunks == c);
       if (!dup) cands.push_back({tpt, c, 0.f});

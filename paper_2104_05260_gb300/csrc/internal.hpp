@@ -42,6 +42,9 @@ struct PrepArgs {
   float4* tgt32;         // targets: N particles then n_check check points
   double4_32a* tgt64;
   int* ioff;             // N: first section-1 image of each ion, or NULL
+  unsigned* mask;        // N x mwords: bit s-1 set when shift s puts the ion's image in B
+  int mwords;            // ceil((n_shift - 1) / 32)
+  double* self;          // 4 x N: FP64 sums over each ion's own images, or NULL
 };
 
 // One generic pair-sum launch: targets x sources -> per-chunk partial sums of
@@ -72,6 +75,7 @@ struct PairPlan {
 // Plans and launches; all return cudaError_t of the launch.
 int pair_tile_targets(int precision, int tpt);
 cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s);
+int prep_blocks(int N, int n_check);   // blocks of the prep kernels (8 ions each)
 cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s);
 int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
 // One launch over several packed-FP32 pair sums (descs and start in device
@@ -88,7 +92,6 @@ cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const doub
                             int f_chunks, int fld, const double* self, const double* q, int N,
                             double pref, DevScalars* sc, double* forces, double* pot, double* grad,
                             double* blk_e, cudaStream_t s);
-// FP64 sum of every ion's own shifted images in B: self[c*N + i], c = phi, grad.
-cudaError_t launch_self_images(const PrepArgs& a, double* self, cudaStream_t s);
+
 
 }  // namespace hsma

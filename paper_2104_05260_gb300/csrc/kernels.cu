@@ -65,48 +65,92 @@ __device__ __forceinline__ int block_excl_scan_i(int v, int* sh, int* total) {
 }
 
 // ------------------------------------------------------------------ prep
+// One warp per ion, one lane per image shift: every FP64 sphere test is its
+// own short chain (FP64 latency is long on this part), and a warp ballot
+// compacts the images of an ion in shift order.
 constexpr int kPrepThreads = 256;
+constexpr int kIonsPerBlock = kPrepThreads / 32;
+
+int prep_blocks(int N, int n_check) {
+  const int a = (N + kIonsPerBlock - 1) / kIonsPerBlock;
+  const int b = (n_check + kPrepThreads - 1) / kPrepThreads;
+  return a > b ? a : b;
+}
+
+// Image of the box-centred source (xc, yc, zc) under shift s, and whether it
+// lies inside B: |p|^2 < R_s^2 with every operation rounded separately.
+__device__ __forceinline__ bool image_in_B(const PrepArgs& a, int s, double xc, double yc, double zc,
+                                           double* px, double* py, double* pz) {
+  const double* sh = a.shifts + 5 * s;
+  *px = __dadd_rn(xc, sh[0]);
+  *py = __dadd_rn(yc, sh[1]);
+  *pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(*px, *px), __dmul_rn(*py, *py)), __dmul_rn(*pz, *pz));
+  return r2 < a.Rs2;
+}
+
+// Box-centred FP64 position of ion j for the whole warp: lane d < 3 wraps
+// coordinate d (one FP64 division each) and the warp shares the results.
+__device__ __forceinline__ void centre_ion(const PrepArgs& a, int j, double* xc, double* yc, double* zc) {
+  const int lane = threadIdx.x & 31;
+  double v = 0.0;
+  if (lane < 3) {
+    const double u = a.x[3 * (size_t)j + lane];
+    if (lane < 2 || a.dims == 3) {
+      v = wrap_centre(u, a.L[lane]);
+    } else {
+      if (!(u > 0.0 && u < a.L[2])) atomicOr(&a.sc->flags, FLAG_OUT_OF_SLAB);
+      v = __dsub_rn(u, 0.5 * a.L[2]);
+    }
+  }
+  *xc = __shfl_sync(0xffffffffu, v, 0);
+  *yc = __shfl_sync(0xffffffffu, v, 1);
+  *zc = __shfl_sync(0xffffffffu, v, 2);
+}
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_count(PrepArgs a) {
-  __shared__ double shd[kPrepThreads];
-  __shared__ int shi[kPrepThreads];
-  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
+  __shared__ int sc_cnt[kIonsPerBlock];
+  __shared__ double sc_q[kIonsPerBlock], sc_aq[kIonsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * kIonsPerBlock + w;
   int c = 0;
-  double qj = 0.0, aq = 0.0;
+  double qj = 0.0;
   if (j < a.N) {
-    const double x = a.x[3 * (size_t)j], y = a.x[3 * (size_t)j + 1], z = a.x[3 * (size_t)j + 2];
-    const double xc = wrap_centre(x, a.L[0]);
-    const double yc = wrap_centre(y, a.L[1]);
-    double zc;
-    if (a.dims == 3) {
-      zc = wrap_centre(z, a.L[2]);
-    } else {
-      if (!(z > 0.0 && z < a.L[2])) atomicOr(&a.sc->flags, FLAG_OUT_OF_SLAB);
-      zc = __dsub_rn(z, 0.5 * a.L[2]);
+    double xc, yc, zc;
+    centre_ion(a, j, &xc, &yc, &zc);
+    if (lane == 0) {
+      a.xc[3 * (size_t)j] = xc;
+      a.xc[3 * (size_t)j + 1] = yc;
+      a.xc[3 * (size_t)j + 2] = zc;
     }
-    a.xc[3 * (size_t)j] = xc;
-    a.xc[3 * (size_t)j + 1] = yc;
-    a.xc[3 * (size_t)j + 2] = zc;
-    for (int s = 1; s < a.n_shift; ++s) {
-      const double* sh = a.shifts + 5 * s;
-      const double px = __dadd_rn(xc, sh[0]);
-      const double py = __dadd_rn(yc, sh[1]);
-      const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
-      c += (r2 < a.Rs2) ? 1 : 0;
+    for (int s0 = 1, g = 0; s0 < a.n_shift; s0 += 32, ++g) {
+      const int s = s0 + lane;
+      double px, py, pz;
+      const bool in = s < a.n_shift && image_in_B(a, s, xc, yc, zc, &px, &py, &pz);
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (lane == 0) a.mask[(size_t)j * a.mwords + g] = m;
+      c += __popc(m);
     }
-    a.cnt[j] = c;
+    if (lane == 0) a.cnt[j] = c;
     qj = a.q[j];
-    aq = fabs(qj);
   }
-  int tot;
-  block_excl_scan_i<kPrepThreads>(c, shi, &tot);
-  const double bq = block_sum_d<kPrepThreads>(qj, shd);
-  const double baq = block_sum_d<kPrepThreads>(aq, shd);
+  if (lane == 0) {
+    sc_cnt[w] = c;
+    sc_q[w] = qj;
+    sc_aq[w] = fabs(qj);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    a.blk[blockIdx.x] = tot;
-    a.blk_q[blockIdx.x] = bq;
-    a.blk_aq[blockIdx.x] = baq;
+    int tc = 0;
+    double tq = 0.0, taq = 0.0;
+    for (int k = 0; k < kIonsPerBlock; ++k) {   // fixed order
+      tc += sc_cnt[k];
+      tq += sc_q[k];
+      taq += sc_aq[k];
+    }
+    a.blk[blockIdx.x] = tc;
+    a.blk_q[blockIdx.x] = tq;
+    a.blk_aq[blockIdx.x] = taq;
   }
 }
 
@@ -144,51 +188,91 @@ __global__ void __launch_bounds__(kScanThreads) k_prep_scan(PrepArgs a, int nblk
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
-  __shared__ int shi[kPrepThreads];
-  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
-  const int c = (j < a.N) ? a.cnt[j] : 0;
-  int tot;
-  const int local = block_excl_scan_i<kPrepThreads>(c, shi, &tot);
+  __shared__ int sh_off[kIonsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * kIonsPerBlock + w;
+  if (threadIdx.x == 0) {
+    int o = a.blk[blockIdx.x];
+    for (int k = 0; k < kIonsPerBlock; ++k) {   // exclusive prefix over the block's ions
+      const int jj = blockIdx.x * kIonsPerBlock + k;
+      sh_off[k] = o;
+      o += (jj < a.N) ? a.cnt[jj] : 0;
+    }
+  }
+  __syncthreads();
   if (j < a.N) {
-    int o = a.N + a.blk[blockIdx.x] + local;
-    if (a.ioff) a.ioff[j] = o;
+    int o = a.N + sh_off[w];
+    if (a.ioff && lane == 0) a.ioff[j] = o;
     const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
     const double qj = a.q[j] - a.sc->qcorr;
-    if (a.src32) {
-      a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
-      a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
+    if (lane == 0) {
+      if (a.src32) {
+        a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
+        a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
+      }
+      if (a.src64) {
+        a.src64[j] = make_double4_32a(xc, yc, zc, qj);
+        a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
+      }
     }
-    if (a.src64) {
-      a.src64[j] = make_double4_32a(xc, yc, zc, qj);
-      a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
-    }
-    for (int s = 1; s < a.n_shift; ++s) {
-      const double* sh = a.shifts + 5 * s;
-      const double px = __dadd_rn(xc, sh[0]);
-      const double py = __dadd_rn(yc, sh[1]);
-      const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
-      if (r2 < a.Rs2) {
+    // own-image sums in FP64 (FP32 path): the ion's interaction with its own
+    // shifted images, which the FP32 pair kernel skips
+    double sp = 0.0, sgx = 0.0, sgy = 0.0, sgz = 0.0;
+    for (int s0 = 1, g = 0; s0 < a.n_shift; s0 += 32, ++g) {
+      const int s = s0 + lane;
+      const unsigned m = a.mask[(size_t)j * a.mwords + g];   // decided in FP64 by k_prep_count
+      if ((m >> lane) & 1u) {
+        const double* sh = a.shifts + 5 * s;
+        const double px = __dadd_rn(xc, sh[0]);
+        const double py = __dadd_rn(yc, sh[1]);
+        const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
+        const int k = o + __popc(m & ((1u << lane) - 1u));
         const double qs = sh[4] * qj;
-        if (a.src32) a.src32[o] = make_float4((float)px, (float)py, (float)pz, (float)qs);
-        if (a.src64) a.src64[o] = make_double4_32a(px, py, pz, qs);
-        ++o;
+        if (a.src32) a.src32[k] = make_float4((float)px, (float)py, (float)pz, (float)qs);
+        if (a.src64) a.src64[k] = make_double4_32a(px, py, pz, qs);
+        if (a.self) {
+          const double dx = px - xc, dy = py - yc, dz = pz - zc;
+          const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
+          const double qi = qs * inv;
+          const double q3 = qi * inv * inv;
+          sp += qi;
+          sgx += q3 * dx;
+          sgy += q3 * dy;
+          sgz += q3 * dz;
+        }
+      }
+      o += __popc(m);
+    }
+    if (a.self) {
+      for (int off = 16; off > 0; off >>= 1) {   // fixed-order warp sum
+        sp += __shfl_xor_sync(0xffffffffu, sp, off);
+        sgx += __shfl_xor_sync(0xffffffffu, sgx, off);
+        sgy += __shfl_xor_sync(0xffffffffu, sgy, off);
+        sgz += __shfl_xor_sync(0xffffffffu, sgz, off);
+      }
+      if (lane == 0) {
+        a.self[j] = sp;
+        a.self[(size_t)a.N + j] = sgx;
+        a.self[2 * (size_t)a.N + j] = sgy;
+        a.self[3 * (size_t)a.N + j] = sgz;
       }
     }
   }
-  if (j < a.n_check) {
-    const double* cp = a.check_pts + 3 * (size_t)j;
+  const int t = blockIdx.x * kPrepThreads + threadIdx.x;
+  if (t < a.n_check) {
+    const double* cp = a.check_pts + 3 * (size_t)t;
     const double c0 = a.cscale * cp[0], c1 = a.cscale * cp[1], c2 = a.cscale * cp[2];
-    if (a.tgt32) a.tgt32[a.N + j] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
-    if (a.tgt64) a.tgt64[a.N + j] = make_double4_32a(c0, c1, c2, 0.0);
+    if (a.tgt32) a.tgt32[a.N + t] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
+    if (a.tgt64) a.tgt64[a.N + t] = make_double4_32a(c0, c1, c2, 0.0);
   }
 }
 
 cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
-  k_prep_count<<<nblk, kPrepThreads, 0, s>>>(a);
-  k_prep_scan<<<1, kScanThreads, 0, s>>>(a, nblk);
-  const int n = a.N > a.n_check ? a.N : a.n_check;
-  k_prep_emit<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a);
+  (void)nblk;
+  const int nb = (a.N + kIonsPerBlock - 1) / kIonsPerBlock;
+  k_prep_count<<<nb, kPrepThreads, 0, s>>>(a);
+  k_prep_scan<<<1, kScanThreads, 0, s>>>(a, nb);
+  k_prep_emit<<<prep_blocks(a.N, a.n_check), kPrepThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -701,42 +785,5 @@ cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const doub
   return cudaGetLastError();
 }
 
-// Every ion's interaction with its own shifted images inside B, in FP64 from
-// the FP64 positions (an ion near a dielectric wall sits very close to its own
-// reflection; FP32 box-centred coordinates cannot resolve that distance).
-// The membership test repeats the prep kernels' FP64 arithmetic exactly.
-__global__ void __launch_bounds__(kPrepThreads) k_self_images(PrepArgs a, double* self) {
-  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
-  if (j >= a.N) return;
-  const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
-  const double qj = a.q[j] - a.sc->qcorr;
-  double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-  for (int s = 1; s < a.n_shift; ++s) {
-    const double* sh = a.shifts + 5 * s;
-    const double px = __dadd_rn(xc, sh[0]);
-    const double py = __dadd_rn(yc, sh[1]);
-    const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
-    if (r2 < a.Rs2) {
-      const double dx = px - xc, dy = py - yc, dz = pz - zc;
-      const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
-      const double qi = sh[4] * qj * inv;
-      const double q3 = qi * inv * inv;
-      p += qi;
-      gx += q3 * dx;
-      gy += q3 * dy;
-      gz += q3 * dz;
-    }
-  }
-  self[j] = p;
-  self[(size_t)a.N + j] = gx;
-  self[2 * (size_t)a.N + j] = gy;
-  self[3 * (size_t)a.N + j] = gz;
-}
-
-cudaError_t launch_self_images(const PrepArgs& a, double* self, cudaStream_t s) {
-  k_self_images<<<(a.N + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a, self);
-  return cudaGetLastError();
-}
 
 }  // namespace hsma

@@ -102,7 +102,7 @@ extern "C" int hsma_pair_sum_static(const double* targets, int64_t n_tgt, const 
   const int tile = pair_tile_targets(precision, tpt);
   const int slots = pair_slots(precision, tpt);
   const int tiles = (int)((n_tgt + tile - 1) / tile);
-  int chunks = choose_chunks(tiles, slots, (double)n_src, precision ? 1024 : 512);
+  int chunks = choose_chunks(tiles, slots, (double)n_src, precision ? 256 : 128);
   const int max_chunks = (int)((kStaticScratchBytes - fixed) / per_chunk);
   if (chunks > max_chunks) chunks = max_chunks;
   unsigned char* p = (unsigned char*)base;
