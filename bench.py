@@ -412,7 +412,8 @@ def main():
     energy = float(ebuf[0])
     Ns = int(P.hsma_get_info(h.h, "Ns"))
     n_check = int(P.hsma_get_info(h.h, "n_check"))
-    kern = {12: "k_pair_f32x2<1>", 14: "k_pair_f32x2<2>", 1: "k_pair_f32<1>", 2: "k_pair_f32<2>",
+    kern = {12: "k_pair_f32x2<1>", 14: "k_pair_f32x2<2>", 24: "k_pair_f32x2s<2>", 1: "k_pair_f32<1>",
+            2: "k_pair_f32<2>",
             4: "k_pair_f32<4>"}.get(int(P.hsma_get_info(h.h, "kernel")), "k_pair_f32")
     plan = {"kernel": kern, "chunks": int(P.hsma_get_info(h.h, "chunks")),
             "grid": int(P.hsma_get_info(h.h, "grid")), "tile_targets": int(P.hsma_get_info(h.h, "tile_targets"))}

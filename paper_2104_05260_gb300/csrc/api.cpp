@@ -404,7 +404,7 @@ static int tune_near(hsma_ctx* h, int64_t N) {
       return ensure_plan(h, N);
     }
   }
-  std::vector<int> tpts = prec ? std::vector<int>{12, 14, 1} : std::vector<int>{1};
+  std::vector<int> tpts = prec ? std::vector<int>{12, 14, 24, 1} : std::vector<int>{1};
   struct Cand { int tpt, chunks; float ms; };
   std::vector<Cand> cands;
   int maxc = 1;
@@ -594,8 +594,8 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->tuned_chunks = 0;
     h->plan_N = -1;
   } else if (k == "targets_per_thread") {
-    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14)
-      return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2, 4 (scalar) or 12, 14 (packed)");
+    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14 && v != 24)
+      return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2, 4 (scalar), 12, 14 or 24 (packed)");
     h->tpt = (int)v;
     h->autotune = 0;          // an explicit kernel choice turns tuning off
     h->tuned_N = -1;

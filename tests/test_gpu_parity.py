@@ -251,3 +251,26 @@ def test_cfg3_2d_20k_stagewise(P, gam):
     Fr = -qc[ti, None] * (ngrad + fgrad)
     assert frms(F[ti], Fr) <= F_TOL[1]
     h.close()
+
+
+def test_kernel_variants_graphs_and_tuning_agree(P):
+    # every FP32 kernel variant sums the same pair terms in the same source
+    # order, so with a fixed chunk count they agree bitwise; CUDA-graph replay
+    # changes nothing; autotuned chunking only changes FP64 combine order
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    ref = None
+    for tpt in (1, 2, 4, 12, 14, 24):
+        for graphs in (0, 1):
+            h = P.HSMA(c.box, 3, c.p, c.M, targets_per_thread=tpt, chunks=8, graphs=graphs)
+            E, F, pot = h.eval(x, q, potential=True)
+            E2, F2, _ = h.eval(x, q)
+            h.close()
+            assert E == E2 and np.array_equal(F, F2)
+            if ref is None:
+                ref = (E, F, pot)
+            assert E == ref[0] and np.array_equal(F, ref[1]) and np.array_equal(pot, ref[2]), (tpt, graphs)
+    h = P.HSMA(c.box, 3, c.p, c.M)            # autotune on (default)
+    E, F, _ = h.eval(x, q)
+    h.close()
+    assert rel(E, ref[0]) <= 1e-12 and frms(F, ref[1]) <= 1e-12
