@@ -483,7 +483,8 @@ def main():
             import hashlib
             rec = json.load(open(tr))
             src = open(os.path.join(ROOT, "paper_2104_05260_gb300", "csrc", "kernels.cu"), "rb").read()
-            if rec.get("kernels_sha1") == hashlib.sha1(src).hexdigest():
+            if (rec.get("kernels_sha1") == hashlib.sha1(src).hexdigest()
+                    and rec.get("chunks") == plan["chunks"] and rec.get("kernel", "").startswith(plan["kernel"])):
                 roof["traffic"] = rec.get("bytes_per_launch")
         except Exception:
             pass

@@ -83,6 +83,7 @@ int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
 cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
                                cudaStream_t s);
 int pair_ragged_slots();
+int pair_ragged_variant();   // kernel code the ragged launch runs (plan tiles with it)
 // scale multiplies W and ysurf (a geometry built for the box divided by scale)
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
                        const double* P, int nA, int nv, const double* W, int M,

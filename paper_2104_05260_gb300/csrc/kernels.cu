@@ -283,6 +283,7 @@ cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
 constexpr int kUnroll = HSMA_PAIR_UNROLL;
 constexpr int kPairThreads = 256;
 constexpr int kTile32 = 256;   // images per shared-memory tile (FP32 path)
+constexpr int kAccBytes2 = 8 * 4 * kPairThreads * 4;   // (hi, lo) x 4 components x 4 targets
 constexpr int kTile64 = 128;   // images per tile (FP64 path)
 constexpr float kFar = 1.0e18f;
 
@@ -704,24 +705,29 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
 // loop): item i belongs to the descriptor d with start[d] <= i < start[d+1].
 // Each item writes only its own descriptor's partials, so every request's
 // result is the same whatever else shares the launch.
-template <int NP>
+// Ragged launches run the packed kernel with 2 targets per thread (code 12):
+// its 512-target tiles give small requests more items than the 4-target
+// variants, which keeps served latency down.  Descriptors must be planned
+// with that tile size.
 __global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged(const PairArgs* __restrict__ descs,
-                                                             const int* __restrict__ start,
-                                                             int n_desc) {
+                                                                const int* __restrict__ start,
+                                                                int n_desc) {
   __shared__ float4 sh[2 * kTile32];
   const int total = start[n_desc];
   for (int item = blockIdx.x; item < total; item += gridDim.x) {
     int d = 0;
     while (d + 1 < n_desc && start[d + 1] <= item) ++d;
     const PairArgs a = descs[d];
-    pair_item_f32x2<NP>(a, item - start[d], sh);
+    pair_item_f32x2<1>(a, item - start[d], sh);
   }
 }
+
+int pair_ragged_variant() { return 12; }
 
 cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
                                cudaStream_t s) {
   if (grid < 1) grid = 1;
-  k_pair_ragged<1><<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
+  k_pair_ragged<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
   return cudaGetLastError();
 }
 
@@ -729,7 +735,7 @@ int pair_ragged_slots() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged<1>, kPairThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged, kPairThreads, 0);
   return sms * (per < 1 ? 1 : per);
 }
 
@@ -782,7 +788,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
 // Kernel variants of the FP32 path, by code: 1, 2, 4 = scalar FP32 with that
 // many targets per thread; 12, 14 = packed FP32x2 with 2 or 4 targets;
 // 24 = packed, 4 targets, compensated sums in shared memory.
-constexpr int kAccBytes2 = 8 * 4 * kPairThreads * 4;
 int pair_tile_targets(int precision, int tpt) {
   if (precision == 0) return kPairThreads;
   return kPairThreads * (tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);

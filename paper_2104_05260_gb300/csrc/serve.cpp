@@ -367,6 +367,8 @@ int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* ou
     if (rc != HSMA_OK) break;
     sl.ctx = new hsma_ctx();
     sl.ctx->precision = precision;
+    sl.ctx->autotune = 0;                      // a request's plan depends only on the request
+    if (precision) sl.ctx->tpt = pair_ragged_variant();
     rc = hsma_ctx_init(sl.ctx);
     if (rc == HSMA_OK) {
       cudaStreamDestroy(sl.ctx->stream);
