@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
             r2 = fmaf(dy, dy, r2);
             r2 = fmaf(dz, dz, r2);
             // an ion (t < n_diag) skips its identity image and, on the FP32
-            // path, its own shifted images (added in FP64 by k_self_images)
+            // path, its own shifted images (added in FP64 by k_prep_emit)
             const bool own = (sidx == t && t < a.n_diag) || (unsigned)(sidx - so[k]) < (unsigned)sc[k];
             const float inv = own ? 0.f : rsqrtf(r2);
             const float qi = s.w * inv;
