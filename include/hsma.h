@@ -108,6 +108,10 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       (packed FP32x2, 2 or 4 targets); turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
+ * On a server handle (hsma_server_create) the only key is
+ *   "inject_fail_ticket" fault injection for tests: the request with this
+ *                       ticket fails with HSMA_ERR_CUDA when it is admitted,
+ *                       without touching the GPU; 0 = off.
  * Errors: HSMA_ERR_ARG (unknown key or value out of range).
  */
 int hsma_set_option(hsma_t h, const char* key, double value);

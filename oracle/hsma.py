@@ -352,22 +352,25 @@ def check_raw(st, cphi, cgrad):
     return np.concatenate([cphi, cgrad[:, 2]])
 
 
-def evaluate(st, x, q, targets=None):
+def evaluate(st, x, q, targets=None, Q=None):
     """One HSMA evaluation.
 
     Returns a dict with energy (None when ``targets`` selects a subset),
     phi, grad, forces (at the selected targets, prefactor applied to energy
     and forces only), the check-point values, the coefficients A (scaled
-    basis, n >= 1), the surface charges Q and N_s.
+    basis, n >= 1), the surface charges Q and N_s.  Passing the surface
+    charges Q of an earlier call on the same input skips steps 3 and 4.
     """
     xc, qc = prepare_inputs(st, x, q)
     n = len(qc)
     ipos, iq, isrc, isid = near_set(st, xc, qc)
-    # step 3: Phi_B at the check points, then the fit
-    cphi, cgrad = pair_field(st.check_pts, ipos, iq)
-    A = st.P @ check_raw(st, cphi, cgrad)
-    # step 4: surface charges
-    Q = st.W @ A
+    cphi = cgrad = A = None
+    if Q is None:
+        # step 3: Phi_B at the check points, then the fit
+        cphi, cgrad = pair_field(st.check_pts, ipos, iq)
+        A = st.P @ check_raw(st, cphi, cgrad)
+        # step 4: surface charges
+        Q = st.W @ A
     # step 5: near + far at the particles (self copy excluded, R1)
     sel = np.arange(n) if targets is None else np.asarray(targets)
     s0 = self_shift(st)

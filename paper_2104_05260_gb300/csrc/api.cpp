@@ -553,6 +553,7 @@ int hsma_create(const double box[3], int dims, int p, int M, double gamma_top, d
 int hsma_set_option(hsma_t h, const char* key, double v) {
   if (!h || !key) return HSMA_ERR_ARG;
   const std::string k(key);
+  if (h->is_server) return server_set_option(h, k, v);
   if (k == "lambda") {
     if (!(v > 1.0) || !std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "lambda must be > 1");
     h->gp.lam = v;

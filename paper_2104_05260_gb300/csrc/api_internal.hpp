@@ -90,3 +90,4 @@ void drop_graph(hsma_ctx* h);
 int mask_words(const hsma::Geometry& g);
 int finish_eval(hsma_ctx* h, double* energy);
 void server_shutdown(hsma_ctx* h);
+int server_set_option(hsma_ctx* h, const std::string& key, double v);

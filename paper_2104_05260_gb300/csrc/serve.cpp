@@ -88,6 +88,9 @@ struct Server {
   std::map<std::tuple<double, double, int, int>, std::unique_ptr<UnitGeo>> geos;
   BatchBuf bufs[kBatchBufs];
   std::string err;
+  // host-side fault injection (tests): the request with this ticket fails as
+  // if a CUDA call had failed while it was being bound to a slot
+  uint64_t inject_fail_ticket = 0;
 };
 
 static void free_request(Request* r) {
@@ -287,6 +290,10 @@ static int step(Server* s) {
       std::string err;
       Slot& sl = s->slots[free_slot];
       int rc = bind_request(s, sl, r, &err);
+      if (rc == HSMA_OK && r->ticket == s->inject_fail_ticket) {
+        rc = HSMA_ERR_CUDA;
+        err = "injected failure";
+      }
       if (rc != HSMA_OK) {
         r->status = rc;
         s->err = err;
@@ -320,6 +327,16 @@ static int step(Server* s) {
 }  // namespace hsma
 
 using namespace hsma;
+
+int server_set_option(hsma_ctx* h, const std::string& key, double v) {
+  if (!h->srv) return HSMA_ERR_ARG;
+  if (key == "inject_fail_ticket" && v >= 0) {
+    h->srv->inject_fail_ticket = (uint64_t)v;
+    return HSMA_OK;
+  }
+  h->err = "unknown server option " + key;
+  return HSMA_ERR_ARG;
+}
 
 void server_shutdown(hsma_ctx* h) {
   if (!h->srv) return;

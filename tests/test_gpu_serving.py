@@ -110,3 +110,35 @@ def test_submit_rejects_bad_requests(P):
     with pytest.raises(P.HSMAError):
         P.hsma_poll(server, 12345, 100)
     P.hsma_destroy(server)
+
+
+def test_failed_request_does_not_disturb_the_others(P):
+    # host-side fault injection: one request fails when it is admitted; the
+    # loop reports that request's error and completes every other request
+    reqs = [request(N, 6, s) for N, s in ((1000, 41), (1200, 42), (900, 43), (1500, 44))]
+    server = P.hsma_server_create(4, 4e9, 1)
+    P.hsma_set_option(server, "inject_fail_ticket", 2)    # the second submission
+    tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
+    assert tickets[1] == 2
+    results = {}
+    for _ in range(100000):
+        for i, t in enumerate(tickets):
+            if i in results:
+                continue
+            try:
+                r = P.hsma_poll(server, t, reqs[i][0].N)
+            except P.HSMAError as e:
+                results[i] = e.code
+                continue
+            if r is not None:
+                results[i] = r
+        if len(results) == len(tickets):
+            break
+    P.hsma_destroy(server)
+    assert results[1] == -7
+    for i in (0, 2, 3):
+        c, x, q = reqs[i]
+        h = P.HSMA(c.box, 3, c.p, c.M)
+        E0, _, _ = h.eval(x, q)
+        h.close()
+        assert abs(results[i][0] - E0) <= 1e-6 * abs(E0)
