@@ -111,3 +111,56 @@ def solid_dz(nmax, xyz, scale):
             c = math.sqrt((2 * n + 1) / (2 * n - 1) * (n - am) * (n + am))
             out[..., idx(n, m)] = (c / scale) * S[..., idx(n - 1, m)]
     return out
+
+
+def solid_cart(nmax, xyz, scale):
+    """The same scaled solid harmonics as ``solid``, written as polynomials in
+    Cartesian coordinates so the input may be complex (for complex-step
+    derivatives).
+
+    (x + iy)^m = C_m + i S_m is carried as the real pair (C_m, S_m); the
+    polar factor r^n P_n^m(cos t) / sin^m t is the polynomial V_n^m(z, r^2)
+    with V_m^m = (2m-1)!!, V_{m+1}^m = (2m+1) z V_m^m and
+    (n-m) V_n^m = (2n-1) z V_{n-1}^m - (n+m-1) r^2 V_{n-2}^m.
+    """
+    xyz = np.asarray(xyz) / scale
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    r2 = x * x + y * y + z * z
+    out = np.zeros(xyz.shape[:-1] + (nbasis(nmax),), dtype=np.result_type(xyz, float))
+    C = np.ones_like(x)
+    S = np.zeros_like(x)
+    for m in range(nmax + 1):
+        dfact = 1.0
+        for k in range(2 * m - 1, 1, -2):
+            dfact *= k
+        V = [None] * (nmax + 1)
+        V[m] = dfact * np.ones_like(x)
+        if m + 1 <= nmax:
+            V[m + 1] = (2 * m + 1) * z * V[m]
+        for n in range(m + 2, nmax + 1):
+            V[n] = ((2 * n - 1) * z * V[n - 1] - (n + m - 1) * r2 * V[n - 2]) / (n - m)
+        for n in range(m, nmax + 1):
+            c = math.sqrt((2 * n + 1) / (4.0 * math.pi)
+                          * math.factorial(n - m) / math.factorial(n + m))
+            if m == 0:
+                out[..., idx(n, 0)] = c * V[n]
+            else:
+                out[..., idx(n, m)] = math.sqrt(2.0) * c * V[n] * C
+                out[..., idx(n, -m)] = math.sqrt(2.0) * c * V[n] * S
+        C, S = x * C - y * S, x * S + y * C
+    return out
+
+
+def series_field(nmax, xyz, scale, coeffs):
+    """phi = sum_k coeffs[k] S_k(xyz) over the basis without k = 0 (the
+    constant), and its gradient by complex-step differentiation (exact to
+    rounding for these polynomials)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    phi = solid_cart(nmax, xyz, scale)[..., 1:] @ coeffs
+    h = 1e-30
+    grad = np.empty(xyz.shape)
+    for d in range(3):
+        z = xyz.astype(np.complex128)
+        z[..., d] += 1j * h
+        grad[..., d] = (solid_cart(nmax, z, scale)[..., 1:] @ coeffs).imag / h
+    return phi, grad

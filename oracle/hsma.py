@@ -352,7 +352,7 @@ def check_raw(st, cphi, cgrad):
     return np.concatenate([cphi, cgrad[:, 2]])
 
 
-def evaluate(st, x, q, targets=None, Q=None):
+def evaluate(st, x, q, targets=None, Q=None, far="surface"):
     """One HSMA evaluation.
 
     Returns a dict with energy (None when ``targets`` selects a subset),
@@ -360,6 +360,8 @@ def evaluate(st, x, q, targets=None, Q=None):
     and forces only), the check-point values, the coefficients A (scaled
     basis, n >= 1), the surface charges Q and N_s.  Passing the surface
     charges Q of an earlier call on the same input skips steps 3 and 4.
+    far="series" evaluates the fitted series of Eq. 5 directly at the ions
+    instead of the surface charges (the survey's next-step variant).
     """
     xc, qc = prepare_inputs(st, x, q)
     n = len(qc)
@@ -378,7 +380,13 @@ def evaluate(st, x, q, targets=None, Q=None):
     m0 = isid == s0
     self_idx[isrc[m0]] = np.nonzero(m0)[0]
     nphi, ngrad = pair_field(xc[sel], ipos, iq, exclude=self_idx[sel])
-    fphi, fgrad = pair_field(xc[sel], st.ysurf, Q)
+    if far == "series":
+        # the truncated series of Sec. 2.2, Eq. 5 itself (no surface charges)
+        if A is None:
+            raise OracleError("the series far field needs the fitted coefficients")
+        fphi, fgrad = H.series_field(st.p, xc[sel], st.Rc, A)
+    else:
+        fphi, fgrad = pair_field(xc[sel], st.ysurf, Q)
     phi = nphi + fphi
     grad = ngrad + fgrad
     out = dict(phi=phi, grad=grad, forces=-st.prefactor * qc[sel, None] * grad,

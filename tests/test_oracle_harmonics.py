@@ -76,3 +76,27 @@ def test_against_scipy_when_available():
                 # |real combination| agrees with sqrt(2)|Re|, sqrt(2)|Im|
                 assert np.allclose(np.abs(Y[:, H.idx(n, m)]), math.sqrt(2) * np.abs(c.real), atol=1e-12)
                 assert np.allclose(np.abs(Y[:, H.idx(n, -m)]), math.sqrt(2) * np.abs(c.imag), atol=1e-12)
+
+
+def test_cartesian_form_matches_angular_form():
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-2, 2, (40, 3))
+    for p in (1, 6, 10):
+        a = H.solid(p, x, 1.7)
+        b = H.solid_cart(p, x, 1.7)
+        assert np.abs(a - b).max() < 1e-12 * max(1.0, np.abs(a).max())
+
+
+def test_series_gradient_matches_finite_differences_and_dz_identity():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, (20, 3))
+    p, s = 8, 1.3
+    coeffs = rng.normal(size=H.nbasis(p) - 1)
+    phi, grad = H.series_field(p, x, s, coeffs)
+    h = 1e-6
+    for d in range(3):
+        e = np.zeros(3); e[d] = h
+        fd = (H.series_field(p, x + e, s, coeffs)[0] - H.series_field(p, x - e, s, coeffs)[0]) / (2 * h)
+        assert np.abs(fd - grad[:, d]).max() < 1e-7 * max(1.0, np.abs(grad).max())
+    dz = H.solid_dz(p, x, s)[:, 1:] @ coeffs        # the independent z-derivative
+    assert np.abs(dz - grad[:, 2]).max() < 1e-12 * max(1.0, np.abs(dz).max())

@@ -254,3 +254,20 @@ def test_pins_detect_planted_mistakes():
     Lv = np.array([L, L, L])
     wrong = mon - Lv * np.floor(mon / Lv)            # floor instead of nearest
     assert not np.allclose(wrong, st.check_pts[st.n_monitor:])
+
+
+def test_series_far_field_agrees_with_surface_charges():
+    # the surface charges are a quadrature of the series (Sec. 2.2, third
+    # step): the two far fields differ by the quadrature error plus a constant
+    L = 10.0 * (0.3) ** (1 / 3)
+    x, q = system3d(300, L, 21)
+    Ee, Fe = ewald_of(x, q, L)
+    st = hsma.make_setup([L, L, L], 3, 8, 2000)
+    a = hsma.evaluate(st, x, q)
+    b = hsma.evaluate(st, x, q, far="series")
+    assert rel_force_err(a["forces"], b["forces"]) < 1e-4
+    d = a["phi"] - b["phi"]
+    assert np.std(d) < 1e-4 * np.sqrt(np.mean(a["phi"] ** 2))
+    assert abs(a["energy"] - b["energy"]) < 1e-4 * abs(a["energy"])
+    # and the series is no worse against Ewald
+    assert rel_force_err(b["forces"], Fe) < 1.05 * rel_force_err(a["forces"], Fe)
