@@ -151,16 +151,24 @@ def solid_cart(nmax, xyz, scale):
     return out
 
 
-def series_field(nmax, xyz, scale, coeffs):
-    """phi = sum_k coeffs[k] S_k(xyz) over the basis without k = 0 (the
-    constant), and its gradient by complex-step differentiation (exact to
-    rounding for these polynomials)."""
+def solid_grad(nmax, xyz, scale):
+    """Gradient of the scaled solid harmonics at the points xyz, shape
+    xyz.shape[:-1] + ((nmax+1)^2, 3), by complex-step differentiation of the
+    polynomial form (exact to rounding: no subtraction)."""
     xyz = np.asarray(xyz, dtype=np.float64)
-    phi = solid_cart(nmax, xyz, scale)[..., 1:] @ coeffs
     h = 1e-30
-    grad = np.empty(xyz.shape)
+    out = np.empty(xyz.shape[:-1] + (nbasis(nmax), 3))
     for d in range(3):
         z = xyz.astype(np.complex128)
         z[..., d] += 1j * h
-        grad[..., d] = (solid_cart(nmax, z, scale)[..., 1:] @ coeffs).imag / h
+        out[..., d] = solid_cart(nmax, z, scale).imag / h
+    return out
+
+
+def series_field(nmax, xyz, scale, coeffs):
+    """phi = sum_k coeffs[k] S_k(xyz) over the basis without k = 0 (the
+    constant), and its gradient."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    phi = solid_cart(nmax, xyz, scale)[..., 1:] @ coeffs
+    grad = np.einsum("...kd,k->...d", solid_grad(nmax, xyz, scale)[..., 1:, :], coeffs)
     return phi, grad

@@ -48,6 +48,14 @@ notes of the repository):
     first upper image reflects across the top interface).  See ``ewald``.
  R8 Neutrality: |sum q| > 1e-10 sum |q| is an error; otherwise the residual is
     removed as q_i -= sum q / N.
+ R9 Gradient-periodicity rows (optional, off by default; not in the paper's
+    fit): for every periodic row of R4/R5 three more rows, one per Cartesian
+    component d, require the field to be periodic as well:
+        w_g sum A [d_d b(r_c) - d_d b(w(r_c))] = w_g [d_d Phi_B(w(r_c)) - d_d Phi_B(r_c)]
+    with weight w_g = grad_weight * R_c (length units, so these rows are in
+    potential units like those of R4).  They are appended after all other rows;
+    the raw check vector gains d_x, d_y, d_z Phi_B at the 2 N_m monitoring
+    points and wraps.
 
 Coordinates at the API: 3D box [0,Lx)x[0,Ly)x[0,Lz) (positions are wrapped);
 2D slab [0,Lx)x[0,Ly)x(0,Lz) (x, y wrapped; z must be inside).  Internally
@@ -64,6 +72,7 @@ from .ewald import image_factor
 GOLDEN = (1.0 + math.sqrt(5.0)) / 2.0
 NEUTRAL_TOL = 1e-10
 SVD_RCOND = 1e-13
+GRAD_WEIGHT = 0.1        # R9: w_g / R_c
 
 
 class OracleError(ValueError):
@@ -111,6 +120,8 @@ class Setup:
     ysurf: np.ndarray = field(default=None)    # (M, 3) surface points
     rank: int = 0
     sing: np.ndarray = field(default=None)
+    grad_rows: bool = False                    # R9
+    grad_weight: float = 0.0
 
 
 def shift_table(dims, box, Rs, gamma_top=0.0, gamma_bot=0.0):
@@ -167,8 +178,10 @@ def face_grid(box, G):
 
 
 def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
-               n_monitor=None, dtn_grid=80, prefactor=1.0):
-    """Geometry-only preparation: sphere, shifts, check points, fit, map."""
+               n_monitor=None, dtn_grid=80, prefactor=1.0, grad_rows=False,
+               grad_weight=GRAD_WEIGHT):
+    """Geometry-only preparation: sphere, shifts, check points, fit, map.
+    grad_rows adds the gradient-periodicity rows of R9."""
     box = tuple(float(b) for b in box)
     if dims not in (2, 3):
         raise OracleError("dims must be 2 or 3")
@@ -185,6 +198,8 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
     Lx, Ly, Lz = box
     st = Setup(dims, box, p, M, float(lam), int(n_monitor), float(gamma_top),
                float(gamma_bot), int(dtn_grid), float(prefactor))
+    st.grad_rows = bool(grad_rows)
+    st.grad_weight = float(grad_weight)
     st.Rc = 0.5 * math.sqrt((Lx * Lx + Ly * Ly) + Lz * Lz)
     st.Rs = st.lam * st.Rc
     st.Rs2 = st.Rs * st.Rs
@@ -223,6 +238,13 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
                            for c in range(nb - 1)], axis=1)
             blocks.append(wd * ((1.0 + g) * sn * dB + (1.0 - g) * LB))
         D = np.vstack(blocks)
+    n_base_rows = D.shape[0]
+    if st.grad_rows:
+        # R9: one row per kept monitoring point and component, component-major
+        wg = st.grad_weight * st.Rc
+        Gm = H.solid_grad(p, mon, st.Rc)[:, 1:, :]
+        Gw = H.solid_grad(p, wrap, st.Rc)[:, 1:, :]
+        D = np.vstack([D] + [wg * (Gm[:, :, d] - Gw[:, :, d])[keep] for d in range(3)])
     U, sv, Vt = np.linalg.svd(D, full_matrices=False)
     cut = SVD_RCOND * sv[0]
     inv = np.where(sv > cut, 1.0 / np.where(sv > cut, sv, 1.0), 0.0)
@@ -256,6 +278,17 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
             off = 2 * nm + f * G * G
             P[:, off:off + G * G] += -wd * (1.0 - g) * LPf
             P[:, ncheck + off:ncheck + off + G * G] += -wd * (1.0 + g) * sn * Pf
+    if st.grad_rows:
+        # raw vector gains [d_x Phi_B ; d_y Phi_B ; d_z Phi_B] at [mon ; wrap]
+        nv0 = P.shape[1]
+        Pg = np.zeros((nb - 1, 6 * nm))
+        nk = len(kidx)
+        for d in range(3):
+            Pd = wg * pinv[:, n_base_rows + d * nk: n_base_rows + (d + 1) * nk]
+            Pg[:, 2 * nm * d + kidx] -= Pd
+            Pg[:, 2 * nm * d + nm + kidx] += Pd
+        P = np.hstack([P, Pg])
+        assert P.shape[1] == nv0 + 6 * nm
     st.P = P
 
     # surface map (R6): Q_m = sum_nm A_nm (2n+1) R_s^(n+1) / M Y_nm(yhat_m)
@@ -347,9 +380,11 @@ def pair_field(tgt, src, qs, exclude=None, budget=4_000_000):
 
 def check_raw(st, cphi, cgrad):
     """Raw check-point vector v in the layout ``P`` expects."""
-    if st.dims == 3:
-        return cphi
-    return np.concatenate([cphi, cgrad[:, 2]])
+    v = cphi if st.dims == 3 else np.concatenate([cphi, cgrad[:, 2]])
+    if st.grad_rows:
+        nm2 = 2 * st.n_mon
+        v = np.concatenate([v, cgrad[:nm2, 0], cgrad[:nm2, 1], cgrad[:nm2, 2]])
+    return v
 
 
 def evaluate(st, x, q, targets=None, Q=None, far="surface"):
@@ -361,7 +396,7 @@ def evaluate(st, x, q, targets=None, Q=None, far="surface"):
     basis, n >= 1), the surface charges Q and N_s.  Passing the surface
     charges Q of an earlier call on the same input skips steps 3 and 4.
     far="series" evaluates the fitted series of Eq. 5 directly at the ions
-    instead of the surface charges (the survey's next-step variant).
+    instead of the surface charges (a cheaper alternative at small p).
     """
     xc, qc = prepare_inputs(st, x, q)
     n = len(qc)

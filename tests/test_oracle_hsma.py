@@ -271,3 +271,52 @@ def test_series_far_field_agrees_with_surface_charges():
     assert abs(a["energy"] - b["energy"]) < 1e-4 * abs(a["energy"])
     # and the series is no worse against Ewald
     assert rel_force_err(b["forces"], Fe) < 1.05 * rel_force_err(a["forces"], Fe)
+
+
+def _fd_grad(p, pts, scale, A, h=1e-5):
+    # central differences of the angular form: independent of the polynomial
+    # form and of the complex-step gradients the fit operator uses
+    g = np.empty(pts.shape)
+    for d in range(3):
+        e = np.zeros(3); e[d] = h * scale
+        g[:, d] = ((H.solid(p, pts + e, scale) - H.solid(p, pts - e, scale))[:, 1:] @ A) / (2 * h * scale)
+    return g
+
+
+@pytest.mark.parametrize("dims,grad_rows", [(3, False), (3, True), (2, False), (2, True)])
+def test_fit_recovers_the_series_of_a_periodic_field(dims, grad_rows):
+    # If Phi_B is minus a harmonic polynomial sum A b (so that Phi_B plus the
+    # series is zero: periodic, and in 2D meeting the dielectric condition for
+    # any gamma), every row of the fit is met exactly by A, and the least-squares
+    # solution must return A to rounding.  Checks the row signs, the column
+    # layout of P and the raw-vector layout, with and without the gradient rows.
+    box = [10.0, 10.0, 10.0] if dims == 3 else [20.0, 20.0, 10.0]
+    p = 6
+    st = hsma.make_setup(box, dims, p, 600, 0.6, -0.3, dtn_grid=24, grad_rows=grad_rows)
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=H.nbasis(p) - 1) / np.arange(1, H.nbasis(p)) ** 0.5
+    cphi = -(H.solid(p, st.check_pts, st.Rc)[:, 1:] @ A)
+    cgrad = -_fd_grad(p, st.check_pts, st.Rc, A)
+    got = st.P @ hsma.check_raw(st, cphi, cgrad)
+    assert np.abs(got - A).max() < 1e-7 * np.abs(A).max()
+    if grad_rows:
+        # a wrong sign of the gradient block is seen
+        bad = st.P @ hsma.check_raw(st, cphi, -cgrad)
+        assert np.abs(bad - A).max() > 1e-3 * np.abs(A).max()
+
+
+def test_gradient_rows_keep_rank_and_accuracy():
+    # the gradient-periodicity rows (R9) add information: full rank, a better
+    # conditioned fit, and an Ewald error no worse than the value rows alone
+    L = 10.0 * (0.3) ** (1 / 3)
+    x, q = system3d(300, L, 21)
+    Ee, Fe = ewald_of(x, q, L)
+    errs, conds = [], []
+    for gr in (False, True):
+        st = hsma.make_setup([L, L, L], 3, 8, 2000, grad_rows=gr)
+        assert st.rank == H.nbasis(8) - 1
+        assert st.P.shape[1] == 2 * st.n_mon * (4 if gr else 1)
+        conds.append(st.sing[0] / st.sing[-1])
+        errs.append(rel_force_err(hsma.evaluate(st, x, q)["forces"], Fe))
+    assert conds[1] < conds[0]
+    assert errs[1] < 1.02 * errs[0]
