@@ -306,6 +306,37 @@ def other_cases(P, torch, dev, stream):
     return out
 
 
+def far_series_compare(P, torch, stream, c, xd, qd, fd, h_surface, n=10):
+    """The main workload with the far field taken from the fitted series
+    (far_field = 1) instead of the M surface charges: evaluations/s, the far
+    stage's time in both forms and their energy / force difference."""
+    N = c.N
+    h = P.HSMA(c.box, c.dims, c.p, c.M, precision=1, timing=1, far_field=1)
+    P.hsma_set_stream(h.h, stream.cuda_stream)
+    e = np.zeros(1)
+    f = torch.empty_like(fd)
+    for _ in range(2):
+        P.hsma_eval_into(h.h, xd, qd, N, e, f)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    far_ms = []
+    a.record(stream)
+    for _ in range(n):
+        P.hsma_eval_into(h.h, xd, qd, N, e, f)
+        far_ms.append(P.hsma_get_info(h.h, "t_far_ms"))
+    b.record(stream)
+    torch.cuda.synchronize()
+    e0 = np.zeros(1)
+    P.hsma_eval_into(h_surface.h, xd, qd, N, e0, fd)
+    torch.cuda.synchronize()
+    rec = {"evals_per_s": 1e3 * n / a.elapsed_time(b), "far_ms_series": float(np.mean(far_ms)),
+           "far_ms_surface": P.hsma_get_info(h_surface.h, "t_far_ms"),
+           "rel_energy_vs_surface": abs(float(e[0]) - float(e0[0])) / abs(float(e0[0])),
+           "rel_force_rms_vs_surface": float(torch.sqrt(((f - fd) ** 2).sum() / (fd ** 2).sum()))}
+    h.close()
+    return rec
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -351,6 +382,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other-cases", action="store_true")
     ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
+    ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
+                    help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     c = workloads.case(args.case)
@@ -373,7 +406,7 @@ def main():
 
     x, q = workloads.electrolyte(c, seed=c.seed + 1000 * rank)
     N = c.N
-    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, timing=1)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, timing=1, far_field=args.far_field)
     stream = torch.cuda.current_stream(dev)
     P.hsma_set_stream(h.h, stream.cuda_stream)
     xd = torch.from_numpy(x).to(dev)
@@ -418,7 +451,7 @@ def main():
     plan = {"kernel": kern, "chunks": int(P.hsma_get_info(h.h, "chunks")),
             "grid": int(P.hsma_get_info(h.h, "grid")), "tile_targets": int(P.hsma_get_info(h.h, "tile_targets"))}
     pairs_near = (N + n_check) * Ns
-    pairs_far = N * c.M
+    pairs_far = 0 if args.far_field else N * c.M     # the series has no pair sum
     pairs = pairs_near + pairs_far
     value = ws / (ms_step / 1e3)
 
@@ -484,8 +517,9 @@ def main():
         try:
             import hashlib
             rec = json.load(open(tr))
-            src = open(os.path.join(ROOT, "paper_2104_05260_gb300", "csrc", "kernels.cu"), "rb").read()
-            if (rec.get("kernels_sha1") == hashlib.sha1(src).hexdigest()
+            csrc = os.path.join(ROOT, "paper_2104_05260_gb300", "csrc")
+            src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("pair.cu", "internal.hpp"))
+            if (rec.get("pair_sources_sha1") == hashlib.sha1(src).hexdigest()
                     and rec.get("chunks") == plan["chunks"] and rec.get("kernel", "").startswith(plan["kernel"])):
                 roof["traffic"] = rec.get("bytes_per_launch")
         except Exception:
@@ -498,6 +532,7 @@ def main():
             "config": {"workload": c.name, "N": N, "p": c.p, "M": c.M, "lambda": c.lam,
                        "N_s": Ns, "n_check": n_check, "precision": "fp32-compute/fp64-accumulate",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
+                       "far_field": "series (Eq. 5)" if args.far_field else "surface charges (Eq. 8)",
                        "plan": plan},
             "pair_ints_per_s": pairs * ws / (ms_step / 1e3), "pairs_per_eval": pairs,
             "energy": energy, "roofline": roof,
@@ -520,6 +555,8 @@ def main():
     if not args.no_serve:
         line["serve"] = serve_bench(P)
     if not args.no_other_cases:
+        if not args.far_field:
+            line["far_field_series"] = far_series_compare(P, torch, stream, c, xd, qd, fd, h)
         line["other_cases"] = other_cases(P, torch, dev, stream)
     print(json.dumps(line), flush=True)
     if dist:

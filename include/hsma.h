@@ -108,6 +108,18 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       (packed FP32x2, 2 or 4 targets); turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
+ *   "grad_rows"         1 = append gradient-periodicity rows to the fit: for
+ *                       every periodicity row of Eq. 6 three more that ask
+ *                       the field (each Cartesian component) to be periodic
+ *                       too, weighted by grad_weight * R_c.  Not in the
+ *                       paper's fit; 0 (default) = the paper's rows only.
+ *   "grad_weight"       weight of those rows in units of R_c (> 0; 0.1).
+ *   "far_field"         0 (default) = the far field from the M surface charges
+ *                       (Eq. 8, the paper's choice); 1 = the fitted series of
+ *                       Eq. 5 itself, sum over n >= 1 of A_nm (r/R_c)^n Y_nm,
+ *                       and its gradient, per particle (cost N (p+1)^2 instead
+ *                       of N M).  The two agree to the surface quadrature's
+ *                       error; the series skips that quadrature.
  * On a server handle (hsma_server_create) the only key is
  *   "inject_fail_ticket" fault injection for tests: the request with this
  *                       ticket fails with HSMA_ERR_CUDA when it is admitted,
@@ -147,7 +159,7 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * Keys: "Rc", "Rs", "n_shifts", "n_check", "rank", "Ns" (images in B at the
  * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
- * "far_chunks", "grid", "slots", "kernel", "tile_targets".
+ * "far_chunks", "far_field", "grid", "slots", "kernel", "tile_targets".
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);
@@ -172,17 +184,21 @@ int hsma_get_array(hsma_t h, const char* name, double* out, int64_t n);
  *   "T"              M x nv  the composite map from the raw check vector v
  *                    (3D: Phi_B at [monitoring points; wraps]; 2D: [Phi_B;
  *                    dPhi_B/dz] at [monitoring points; wraps; top face;
- *                    bottom face]) to the surface charges, row-major.  It is
- *                    the fit of Sec. 2.2, Eq. 6 followed by the surface map.
+ *                    bottom face]; with gradient rows followed by
+ *                    [dx; dy; dz Phi_B] at [monitoring points; wraps]) to the
+ *                    surface charges, row-major.  It is the fit of Sec. 2.2,
+ *                    Eq. 6 followed by the surface map.
  *   "check_points"   n_check*3, "surface_points" M*3,
  *   "shifts"         n_shift*5 (sx, sy, zs, zo, factor), identity first,
  *   "sizes"          [n_check, nv, nA, rank, n_shift, Rc, Rs, Rs2].
- * lam <= 0, n_monitor <= 0 or G <= 0 select the defaults.  n is the capacity
- * of out in doubles.  Errors: HSMA_ERR_ARG, HSMA_ERR_NUMERIC.
+ * lam <= 0, n_monitor <= 0 or G <= 0 select the defaults; grad_weight > 0
+ * adds the gradient-periodicity rows with that weight (option grad_rows),
+ * <= 0 leaves them out.  n is the capacity of out in doubles.
+ * Errors: HSMA_ERR_ARG, HSMA_ERR_NUMERIC.
  */
 int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
                         double gamma_bot, double lam, int n_monitor, int G,
-                        const char* name, double* out, int64_t n);
+                        double grad_weight, const char* name, double* out, int64_t n);
 
 /*
  * hsma_pair_sum_static -- the direct pair sum (the kernel behind the near

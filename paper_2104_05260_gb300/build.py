@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsma.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["kernels.cu", "noalloc.cu"]
+CU = ["pair.cu", "kernels.cu", "noalloc.cu"]
 CPP = ["geometry.cpp", "api.cpp", "serve.cpp"]
 HEADERS = ["geometry.hpp", "internal.hpp", "api_internal.hpp"]
 

@@ -108,7 +108,7 @@ hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
-                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask})
+                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -146,8 +146,23 @@ int ensure_geometry(hsma_ctx* h) {
     sh[5 * i + 3] = g.shifts[i].zo;
     sh[5 * i + 4] = g.shifts[i].f;
   }
+  // normalisation table of the direct series far field (k_far_series)
+  const int p = g.par.p;
+  std::vector<double> norm((size_t)(p + 1) * (p + 1), 0.0);
+  for (int n = 0; n <= p; ++n)
+    for (int m = 0; m <= n; ++m) {
+      double ratio = 1.0;  // (n-m)!/(n+m)!
+      for (int k = n - m + 1; k <= n + m; ++k) ratio /= k;
+      double c = std::sqrt((2 * n + 1) / (4.0 * 3.14159265358979323846) * ratio);
+      if (m > 0) {
+        c *= std::sqrt(2.0);
+        for (int k = 2 * m - 1; k > 1; k -= 2) c *= k;
+      }
+      norm[(size_t)n * (p + 1) + m] = c;
+    }
   struct Up { DevBuf* b; const void* src; size_t bytes; };
   const Up ups[] = {
+      {&h->d_norm, norm.data(), norm.size() * 8},
       {&h->d_shifts, sh.data(), sh.size() * 8},
       {&h->d_check, g.check_pts.data(), g.check_pts.size() * 8},
       {&h->d_P, g.P.data(), g.P.size() * 8},
@@ -294,7 +309,7 @@ int stage_fit(hsma_ctx* h, int64_t N) {
   const Geometry& g = h->geo;
   const int prec = h->precision;
   cudaError_t e = launch_fit(g.par.dims, (const double*)h->d_part.p, h->chunks1, h->n_tgt1, (int)N,
-                             g.n_check, geo_P(h), g.nA, g.nv, geo_W(h), g.par.M, geo_Y(h), h->gscale,
+                             g.n_check, g.par.grad_rows ? 2 * g.n_mon : 0, geo_P(h), g.nA, g.nv, geo_W(h), g.par.M, geo_Y(h), h->gscale,
                              (double*)h->d_v.p, (double*)h->d_A.p, (double*)h->d_cphi.p,
                              (double*)h->d_cdz.p, (double*)h->d_Q.p,
                              prec ? (float4*)h->d_s32.p : nullptr,
@@ -324,7 +339,7 @@ PairArgs far_args(hsma_ctx* h, int64_t N) {
 int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   const int prec = h->precision;
   cudaError_t e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1,
-                                  (const double*)h->d_fpart.p, h->chunks2, (int)N,
+                                  (const double*)h->d_fpart.p, h->far_series ? 1 : h->chunks2, (int)N,
                                   prec ? (const double*)h->d_self.p : nullptr,
                                   (const double*)h->d_q.p, (int)N, h->pref, (DevScalars*)h->d_sc.p,
                                   forces_dev, pot_dev, (double*)h->d_grad.p, (double*)h->d_blke.p,
@@ -351,7 +366,12 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   rc = stage_fit(h, N);
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[3], s);
-  e = launch_pair(prec, tpt, far_args(h, N), h->grid2, s);
+  if (h->far_series)
+    e = launch_far_series(prec, prec ? (const void*)h->d_tgt32.p : (const void*)h->d_tgt64.p, (int)N,
+                          (const double*)h->d_A.p, (const double*)h->d_norm.p, h->geo.par.p,
+                          1.0 / (h->geo.Rc * h->gscale), (double*)h->d_fpart.p, s);
+  else
+    e = launch_pair(prec, tpt, far_args(h, N), h->grid2, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "far launch");
   if (tm) cudaEventRecord(h->ev[4], s);
   rc = stage_assemble(h, N, forces_dev, pot_dev);
@@ -580,6 +600,18 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "timing") {
     h->timing = (v != 0);
     drop_graph(h);
+  } else if (k == "grad_rows") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "grad_rows must be 0 or 1");
+    h->gp.grad_rows = (int)v;
+    h->geo_dirty = true;
+  } else if (k == "grad_weight") {
+    if (!(v > 0) || !std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "grad_weight must be > 0");
+    h->gp.grad_weight = v;
+    h->geo_dirty = true;
+  } else if (k == "far_field") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "far_field must be 0 (surface charges) or 1 (series)");
+    h->far_series = (int)v;
+    drop_graph(h);
   } else if (k == "graphs") {
     h->use_graphs = (v != 0);
     drop_graph(h);
@@ -653,7 +685,8 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "t_assemble_ms") *value = h->times[5];
   else if (k == "chunks") *value = h->chunks1;
   else if (k == "kernel") *value = h->precision ? h->tpt : 0;
-  else if (k == "far_chunks") *value = h->chunks2;
+  else if (k == "far_chunks") *value = h->far_series ? 1 : h->chunks2;
+  else if (k == "far_field") *value = h->far_series;
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;
   else if (k == "tile_targets") *value = pair_tile_targets(h->precision, h->precision ? h->tpt : 1);
@@ -703,7 +736,7 @@ const char* hsma_last_error(hsma_t h) {
 
 extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
                                    double gamma_bot, double lam, int n_monitor, int G,
-                                   const char* name, double* out, int64_t n) {
+                                   double grad_weight, const char* name, double* out, int64_t n) {
   if (!box || !name || !out) return HSMA_ERR_ARG;
   if (dims != 2 && dims != 3) return HSMA_ERR_ARG;
   GeoParams gp;
@@ -716,6 +749,8 @@ extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, 
   gp.gtop = dims == 2 ? gamma_top : 0.0;
   gp.gbot = dims == 2 ? gamma_bot : 0.0;
   gp.G = G > 0 ? G : 80;
+  gp.grad_rows = grad_weight > 0 ? 1 : 0;
+  if (grad_weight > 0) gp.grad_weight = grad_weight;
   Geometry g;
   std::string err;
   const int rc = build_geometry(gp, &g, &err);

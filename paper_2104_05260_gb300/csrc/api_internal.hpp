@@ -42,7 +42,7 @@ struct hsma_ctx {
   bool own_stream = false;
   std::string err;
   // geometry-sized device buffers
-  hsma::DevBuf d_shifts, d_check, d_P, d_W, d_ysurf, d_v, d_A, d_cphi, d_cdz, d_Q, d_s32, d_s64;
+  hsma::DevBuf d_shifts, d_check, d_P, d_W, d_ysurf, d_v, d_A, d_cphi, d_cdz, d_Q, d_s32, d_s64, d_norm;
   // N-sized device buffers
   hsma::DevBuf d_x, d_q, d_xc, d_cnt, d_blk, d_blkq, d_blkaq, d_src32, d_src64, d_tgt32, d_tgt64,
       d_part, d_fpart, d_forces, d_pot, d_grad, d_blke, d_sc, d_ioff, d_self, d_mask;
@@ -67,6 +67,7 @@ struct hsma_ctx {
   // CUDA graph of the per-evaluation pipeline (prep .. assembly), valid for
   // graph_N particles under the current plan and options
   int use_graphs = 1;
+  int far_series = 0;  // far field: 0 surface charges (Eq. 8), 1 the fitted series (Eq. 5)
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_N = -1;
   // autotuning of the near/check launch (kernel variant, source chunks)

@@ -306,6 +306,65 @@ struct DtN {
   }
 };
 
+// Polynomial form: (x + iy)^m = C_m + i S_m, and V_n^m(z, r^2), the polar
+// factor r^n P_n^m(cos t) / sin^m t, by the three-term recursion in n.  The
+// gradient follows from dV/dz at fixed r^2, dV/d(r^2) and the x, y derivatives
+// of C_m, S_m, each carried along its own recursion.
+void solid_basis_grad(int p, double x, double y, double z, double s, double* val, double* grad) {
+  const int nb = (p + 1) * (p + 1);
+  x /= s; y /= s; z /= s;
+  const double r2 = x * x + y * y + z * z;
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  double C = 1, S = 0, Cx = 0, Cy = 0, Sx = 0, Sy = 0;
+  for (int m = 0; m <= p; ++m) {
+    double dfact = 1.0;
+    for (int k = 2 * m - 1; k > 1; k -= 2) dfact *= k;
+    double v1 = dfact, z1 = 0, q1 = 0, v2 = 0, z2 = 0, q2 = 0;  // V, dV/dz, dV/dr2
+    for (int n = m; n <= p; ++n) {
+      double v = v1, vz = z1, vq = q1;
+      if (n == m + 1) {
+        v = (2 * m + 1) * z * v1;
+        vz = (2 * m + 1) * (v1 + z * z1);
+        vq = (2 * m + 1) * z * q1;
+      } else if (n > m + 1) {
+        const double a = 2 * n - 1, b = n + m - 1;
+        v = (a * z * v1 - b * r2 * v2) / (n - m);
+        vz = (a * (v1 + z * z1) - b * r2 * z2) / (n - m);
+        vq = (a * z * q1 - b * (v2 + r2 * q2)) / (n - m);
+      }
+      if (n > m) {
+        v2 = v1; z2 = z1; q2 = q1;
+        v1 = v; z1 = vz; q1 = vq;
+      }
+      double ratio = 1.0;  // (n-m)!/(n+m)!
+      for (int k = n - m + 1; k <= n + m; ++k) ratio /= k;
+      double c = std::sqrt((2 * n + 1) * inv4pi * ratio);
+      const double Vx = 2 * x * vq, Vy = 2 * y * vq, Vz = vz + 2 * z * vq;
+      const int base = n * n + n;
+      if (m == 0) {
+        val[base] = c * v;
+        grad[base] = c * Vx / s;
+        grad[nb + base] = c * Vy / s;
+        grad[2 * nb + base] = c * Vz / s;
+      } else {
+        c *= std::sqrt(2.0);
+        val[base + m] = c * v * C;
+        val[base - m] = c * v * S;
+        grad[base + m] = c * (Vx * C + v * Cx) / s;
+        grad[base - m] = c * (Vx * S + v * Sx) / s;
+        grad[nb + base + m] = c * (Vy * C + v * Cy) / s;
+        grad[nb + base - m] = c * (Vy * S + v * Sy) / s;
+        grad[2 * nb + base + m] = c * Vz * C / s;
+        grad[2 * nb + base - m] = c * Vz * S / s;
+      }
+    }
+    const double nC = x * C - y * S, nS = x * S + y * C;
+    const double nCx = C + x * Cx - y * Sx, nSx = S + x * Sx + y * Cx;
+    const double nCy = x * Cy - S - y * Sy, nSy = x * Sy + C + y * Cy;
+    C = nC; S = nS; Cx = nCx; Sx = nSx; Cy = nCy; Sy = nSy;
+  }
+}
+
 int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
   const int p = gp.p, M = gp.M;
   const int nb = (p + 1) * (p + 1), nA = nb - 1;
@@ -319,6 +378,9 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
     *err = "|gamma| must be <= 1"; return HSMA_ERR_ARG;
   }
   if (gp.dims == 2 && gp.G < 4) { *err = "dtn_grid must be >= 4"; return HSMA_ERR_ARG; }
+  if (gp.grad_rows && !(gp.grad_weight > 0.0 && std::isfinite(gp.grad_weight))) {
+    *err = "grad_weight must be > 0"; return HSMA_ERR_ARG;
+  }
   g->par = gp;
   sphere_radius(gp.box, gp.lam, &g->Rc, &g->Rs, &g->Rs2);
   build_shifts(gp, g->Rs, &g->shifts);
@@ -363,7 +425,8 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
   std::vector<int> prow;  // monitoring index of each periodic row
   for (int c = 0; c < nm; ++c) if (keep[c]) prow.push_back(c);
   const int nper = (int)prow.size();
-  const int rows = nper + 2 * nface;
+  const int rows0 = nper + 2 * nface;                       // value and DtN rows
+  const int rows = rows0 + (gp.grad_rows ? 3 * nper : 0);  // + gradient rows
   std::vector<double> D((size_t)rows * nA);
   std::vector<double> bm(nb), bw(nb), dzb(nb);
   for (int r = 0; r < nper; ++r) {
@@ -394,6 +457,19 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
       }
     }
   }
+  // gradient-periodicity rows: component-major after all other rows
+  const double wg = gp.grad_weight * Rc;
+  if (gp.grad_rows) {
+    std::vector<double> vm(nb), vw(nb), gm(3 * (size_t)nb), gw(3 * (size_t)nb);
+    for (int r = 0; r < nper; ++r) {
+      const int c = prow[r];
+      solid_basis_grad(p, mon[3 * c], mon[3 * c + 1], mon[3 * c + 2], Rc, vm.data(), gm.data());
+      solid_basis_grad(p, wrap[3 * c], wrap[3 * c + 1], wrap[3 * c + 2], Rc, vw.data(), gw.data());
+      for (int d = 0; d < 3; ++d)
+        for (int k = 1; k < nb; ++k)
+          D[(size_t)(rows0 + d * nper + r) * nA + k - 1] = wg * (gm[(size_t)d * nb + k] - gw[(size_t)d * nb + k]);
+    }
+  }
   std::vector<double> pinv;
   g->rank = pseudo_inverse(D, rows, nA, 1e-13, &pinv, &g->smax, &g->smin);
   if (g->rank < nA) {
@@ -402,7 +478,8 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
   }
   // P = pinv * S, S mapping the raw check vector v to the right-hand sides.
   g->nA = nA;
-  g->nv = (gp.dims == 3) ? g->n_check : 2 * g->n_check;
+  const int nv0 = (gp.dims == 3) ? g->n_check : 2 * g->n_check;
+  g->nv = nv0 + (gp.grad_rows ? 6 * nm : 0);
   g->P.assign((size_t)nA * g->nv, 0.0);
   for (int r = 0; r < nper; ++r) {
     const int c = prow[r];
@@ -427,6 +504,18 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
         }
       }
     }
+  }
+  if (gp.grad_rows) {
+    // v gains [d_x Phi_B ; d_y Phi_B ; d_z Phi_B] at [monitoring points ; wraps]
+    for (int d = 0; d < 3; ++d)
+      for (int r = 0; r < nper; ++r) {
+        const int c = prow[r];
+        for (int k = 0; k < nA; ++k) {
+          const double v = wg * pinv[(size_t)k * rows + rows0 + d * nper + r];
+          g->P[(size_t)k * g->nv + nv0 + 2 * nm * d + c] -= v;
+          g->P[(size_t)k * g->nv + nv0 + 2 * nm * d + nm + c] += v;
+        }
+      }
   }
   // surface points and W
   fibonacci_sphere(M, Rs, &g->ysurf);

@@ -26,6 +26,8 @@ struct GeoParams {
   int n_monitor = 98;
   double gtop = 0, gbot = 0;
   int G = 80;
+  int grad_rows = 0;         // gradient-periodicity rows appended to the fit
+  double grad_weight = 0.1;  // their weight, in units of R_c
 };
 
 struct Geometry {
@@ -57,6 +59,10 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err);
 // Real orthonormal solid harmonics (r/s)^n Y_nm at (x, y, z)/s, n <= p,
 // entry n*n + n + m; dz (nullable) receives d/dz of each (unscaled z).
 void solid_basis(int p, double x, double y, double z, double s, double* val, double* dz);
+
+// The same harmonics and their full gradient (unscaled coordinates):
+// grad[d*(p+1)^2 + k], d = x, y, z.
+void solid_basis_grad(int p, double x, double y, double z, double s, double* val, double* grad);
 
 // Pseudo-inverse of the m x n (m >= n) row-major matrix D with relative
 // singular-value cut-off rcond; pinv is n x m row-major.  Returns the rank.

@@ -84,9 +84,16 @@ cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_de
                                cudaStream_t s);
 int pair_ragged_slots();
 int pair_ragged_variant();   // kernel code the ragged launch runs (plan tiles with it)
+// Far field as the fitted series itself (no surface charges): out[c*N + i],
+// c = phi, grad; norm[n*(p+1) + m] = c_n0 (m = 0), sqrt(2) c_nm (2m-1)!! (m > 0)
+// with c_nm the orthonormal harmonic normalisation; A as the fit writes it.
+cudaError_t launch_far_series(int precision, const void* tgt, int N, const double* A, const double* norm,
+                              int p, double inv_rc, double* out, cudaStream_t s);
 // scale multiplies W and ysurf (a geometry built for the box divided by scale)
+// n_grad: check points (2 N_m, monitoring points then wraps) whose gradients
+// also enter v for the gradient-periodicity rows; 0 without them.
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
-                       const double* P, int nA, int nv, const double* W, int M,
+                       int n_grad, const double* P, int nA, int nv, const double* W, int M,
                        const double* ysurf, double scale, double* v, double* A, double* cphi,
                        double* cdz, double* Q, float4* s32, double4_32a* s64, cudaStream_t s);
 cudaError_t launch_assemble(const double* part, int n_chunks, int ld, const double* fpart,

@@ -6,17 +6,10 @@
 //         neutrality sums, and a deterministic compaction of the images in B
 //         into one list: section 0 holds the identity image of every source
 //         in source order, section 1 the other images, source-major.
-//  pair   generic direct sum targets x sources -> phi and grad phi.  The near
-//         field (Sec. 2.2, first and last steps), the check-point sums
-//         (Sec. 2.2, Eq. 6) and the far field of the surface charges all run
-//         through it.  FP32 pair arithmetic (rsqrt on the MUFU pipe) with
-//         TwoSum-compensated float-float accumulation per target, or an FP64
-//         twin.  Sources are staged through shared memory and broadcast to
-//         every thread; each CTA walks (target tile, source chunk) items of a
-//         static schedule, and every item writes its own FP64 partial, so the
-//         result does not depend on which CTA ran it.
+//  pair   the direct pair sums live in pair.cu.
 //  fit    FP64: combine the check-point partials in fixed order, A = P v,
 //         Q = W A (the least-squares solve and the surface map of Sec. 2.2).
+//  series the far field as the fitted series itself (optional; Eq. 5).
 //  assemble  Phi_i, F_i = -q_i grad Phi_i, E = 1/2 sum q_i Phi_i (Sec. 3.1),
 //         with fixed-order tree reductions (no floating-point atomics).
 #include <cuda_runtime.h>
@@ -276,562 +269,14 @@ cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ pair sums
-#ifndef HSMA_PAIR_UNROLL
-#define HSMA_PAIR_UNROLL 8     // images per unrolled step of the FP32 inner loops
-#endif
-constexpr int kUnroll = HSMA_PAIR_UNROLL;
-constexpr int kPairThreads = 256;
-constexpr int kTile32 = 256;   // images per shared-memory tile (FP32 path)
-constexpr int kAccBytes2 = 8 * 4 * kPairThreads * 4;   // (hi, lo) x 4 components x 4 targets
-constexpr int kTile64 = 128;   // images per tile (FP64 path)
-constexpr float kFar = 1.0e18f;
-
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
-  // Knuth TwoSum: hi + v = s + err exactly; err is carried in lo
-  const float s = hi + v;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (v - bb);
-  hi = s;
-  lo += err;
-}
-
-// Section-1 index range holding the own images of the ions in the target
-// tile [t0, t0 + tt) (images are emitted source-major, so it is contiguous).
-__device__ __forceinline__ void own_range(const PairArgs& a, int t0, int tt, int* lo, int* hi) {
-  *lo = 0;
-  *hi = 0;
-  if (!a.ioff || t0 >= a.n_diag) return;
-  const int tl = min(t0 + tt, a.n_diag) - 1;
-  *lo = a.ioff[t0];
-  *hi = a.ioff[tl] + a.icnt[tl];
-}
-
-template <int TPT>
-__global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
-  __shared__ float4 sh[kTile32];
-  const float4* __restrict__ tgt = (const float4*)a.tgt;
-  const float4* __restrict__ src = (const float4*)a.src;
-  const int ns = a.sc ? a.sc->Ns : a.n_src;
-  int per = (ns + a.n_chunks - 1) / a.n_chunks;
-  per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-    const int t0 = tile * kPairThreads * TPT;
-    float tx[TPT], ty[TPT], tz[TPT];
-    float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-      const int t = t0 + threadIdx.x + k * kPairThreads;
-      const float4 v = (t < a.n_tgt) ? tgt[t] : make_float4(kFar, kFar, kFar, 0.f);
-      tx[k] = v.x; ty[k] = v.y; tz[k] = v.z;
-      hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
-    }
-    int so[TPT], sc[TPT];   // own section-1 image range of each ion target
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-      const int t = t0 + threadIdx.x + k * kPairThreads;
-      const bool ion = a.ioff && t < a.n_diag;
-      so[k] = ion ? a.ioff[t] : 0;
-      sc[k] = ion ? a.icnt[t] : 0;
-    }
-    int lo1 = 0, hi1 = 0;
-    own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
-    const int s0 = chunk * per;
-    const int s1 = min(ns, s0 + per);
-    for (int sb = s0; sb < s1; sb += kTile32) {
-      const int n = min(kTile32, s1 - sb);
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
-      __syncthreads();
-      float p[TPT], gx[TPT], gy[TPT], gz[TPT];
-#pragma unroll
-      for (int k = 0; k < TPT; ++k) p[k] = gx[k] = gy[k] = gz[k] = 0.f;
-      const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
-                        (sb < hi1 && lo1 < sb + n);
-      if (!diag) {
-#pragma unroll kUnroll
-        for (int i = 0; i < n; ++i) {
-          const float4 s = sh[i];
-#pragma unroll
-          for (int k = 0; k < TPT; ++k) {
-            const float dx = s.x - tx[k], dy = s.y - ty[k], dz = s.z - tz[k];
-            float r2 = dx * dx;
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            const float inv = rsqrtf(r2);
-            const float qi = s.w * inv;
-            p[k] += qi;
-            const float q3 = qi * (inv * inv);
-            gx[k] = fmaf(q3, dx, gx[k]);
-            gy[k] = fmaf(q3, dy, gy[k]);
-            gz[k] = fmaf(q3, dz, gz[k]);
-          }
-        }
-      } else {
-        for (int i = 0; i < n; ++i) {
-          const float4 s = sh[i];
-          const int sidx = sb + i;
-#pragma unroll
-          for (int k = 0; k < TPT; ++k) {
-            const int t = t0 + threadIdx.x + k * kPairThreads;
-            const float dx = s.x - tx[k], dy = s.y - ty[k], dz = s.z - tz[k];
-            float r2 = dx * dx;
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            // an ion (t < n_diag) skips its identity image and, on the FP32
-            // path, its own shifted images (added in FP64 by k_prep_emit)
-            const bool own = (sidx == t && t < a.n_diag) || (unsigned)(sidx - so[k]) < (unsigned)sc[k];
-            const float inv = own ? 0.f : rsqrtf(r2);
-            const float qi = s.w * inv;
-            p[k] += qi;
-            const float q3 = qi * (inv * inv);
-            gx[k] = fmaf(q3, dx, gx[k]);
-            gy[k] = fmaf(q3, dy, gy[k]);
-            gz[k] = fmaf(q3, dz, gz[k]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < TPT; ++k) {
-        two_sum_add(hp[k], lp[k], p[k]);
-        two_sum_add(hx[k], lx[k], gx[k]);
-        two_sum_add(hy[k], ly[k], gy[k]);
-        two_sum_add(hz[k], lz[k], gz[k]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-      const int t = t0 + threadIdx.x + k * kPairThreads;
-      if (t < a.n_tgt) {
-        double* o = a.part + (size_t)chunk * 4 * a.ld + t;
-        o[0] = (double)hp[k] + (double)lp[k];
-        o[(size_t)a.ld] = (double)hx[k] + (double)lx[k];
-        o[2 * (size_t)a.ld] = (double)hy[k] + (double)ly[k];
-        o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
-      }
-    }
-  }
-}
-
-// Packed FP32x2 variant: the same per-pair arithmetic on two targets at once
-// with Blackwell's paired FP32 instructions (FADD2/FMUL2/FFMA2), so one issued
-// instruction does the work of two.  Each thread holds 2*NP targets as NP
-// pairs; a shared-memory image is stored twice over, (x, x, y, y) and
-// (z, z, q, q), so every operand is already a pair.
-template <int NP>
-__device__ __forceinline__ void pair_item_f32x2(const PairArgs& a, int item, float4* sh) {
-  const float4* __restrict__ tgt = (const float4*)a.tgt;
-  const float4* __restrict__ src = (const float4*)a.src;
-  constexpr int TPT = 2 * NP;
-  const int ns = a.sc ? a.sc->Ns : a.n_src;
-  int per = (ns + a.n_chunks - 1) / a.n_chunks;
-  per = (per + kTile32 - 1) / kTile32 * kTile32;
-  {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-    const int t0 = tile * kPairThreads * TPT;
-    // pair k holds targets t0 + tid + (2k)*256 and t0 + tid + (2k+1)*256, negated
-    float2 nx[NP], ny[NP], nz[NP];
-    float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
-      const int tb = ta + kPairThreads;
-      const float4 va = (ta < a.n_tgt) ? tgt[ta] : make_float4(kFar, kFar, kFar, 0.f);
-      const float4 vb = (tb < a.n_tgt) ? tgt[tb] : make_float4(kFar, kFar, kFar, 0.f);
-      nx[k] = make_float2(-va.x, -vb.x);
-      ny[k] = make_float2(-va.y, -vb.y);
-      nz[k] = make_float2(-va.z, -vb.z);
-    }
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
-    int so[TPT], sc[TPT];   // own section-1 image range of each ion target
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-      const int t = t0 + threadIdx.x + k * kPairThreads;
-      const bool ion = a.ioff && t < a.n_diag;
-      so[k] = ion ? a.ioff[t] : 0;
-      sc[k] = ion ? a.icnt[t] : 0;
-    }
-    int lo1 = 0, hi1 = 0;
-    own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
-    const int s0 = chunk * per;
-    const int s1 = min(ns, s0 + per);
-    for (int sb = s0; sb < s1; sb += kTile32) {
-      const int n = min(kTile32, s1 - sb);
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kPairThreads) {
-        const float4 v = src[sb + i];
-        sh[2 * i] = make_float4(v.x, v.x, v.y, v.y);
-        sh[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
-      }
-      __syncthreads();
-      float2 p[NP], gx[NP], gy[NP], gz[NP];
-#pragma unroll
-      for (int k = 0; k < NP; ++k) p[k] = gx[k] = gy[k] = gz[k] = make_float2(0.f, 0.f);
-      const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
-                        (sb < hi1 && lo1 < sb + n);
-      if (!diag) {
-#pragma unroll kUnroll
-        for (int i = 0; i < n; ++i) {
-          const float4 A = sh[2 * i], B = sh[2 * i + 1];
-          const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
-          const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
-#pragma unroll
-          for (int k = 0; k < NP; ++k) {
-            const float2 dx = __fadd2_rn(sx, nx[k]);
-            const float2 dy = __fadd2_rn(sy, ny[k]);
-            const float2 dz = __fadd2_rn(sz, nz[k]);
-            float2 r2 = __fmul2_rn(dx, dx);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-            const float2 qi = __fmul2_rn(sq, inv);
-            p[k] = __fadd2_rn(p[k], qi);
-            const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
-            gx[k] = __ffma2_rn(q3, dx, gx[k]);
-            gy[k] = __ffma2_rn(q3, dy, gy[k]);
-            gz[k] = __ffma2_rn(q3, dz, gz[k]);
-          }
-        }
-      } else {
-        for (int i = 0; i < n; ++i) {
-          const float4 A = sh[2 * i], B = sh[2 * i + 1];
-          const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
-          const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
-          const int sidx = sb + i;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) {
-            const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
-            const int tb = ta + kPairThreads;
-            const float2 dx = __fadd2_rn(sx, nx[k]);
-            const float2 dy = __fadd2_rn(sy, ny[k]);
-            const float2 dz = __fadd2_rn(sz, nz[k]);
-            float2 r2 = __fmul2_rn(dx, dx);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            // an ion skips its identity image and its own shifted images
-            const bool owna = (sidx == ta && ta < a.n_diag) || (unsigned)(sidx - so[2 * k]) < (unsigned)sc[2 * k];
-            const bool ownb = (sidx == tb && tb < a.n_diag) || (unsigned)(sidx - so[2 * k + 1]) < (unsigned)sc[2 * k + 1];
-            const float2 inv = make_float2(owna ? 0.f : rsqrtf(r2.x), ownb ? 0.f : rsqrtf(r2.y));
-            const float2 qi = __fmul2_rn(sq, inv);
-            p[k] = __fadd2_rn(p[k], qi);
-            const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
-            gx[k] = __ffma2_rn(q3, dx, gx[k]);
-            gy[k] = __ffma2_rn(q3, dy, gy[k]);
-            gz[k] = __ffma2_rn(q3, dz, gz[k]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        two_sum_add(hp[2 * k], lp[2 * k], p[k].x);
-        two_sum_add(hp[2 * k + 1], lp[2 * k + 1], p[k].y);
-        two_sum_add(hx[2 * k], lx[2 * k], gx[k].x);
-        two_sum_add(hx[2 * k + 1], lx[2 * k + 1], gx[k].y);
-        two_sum_add(hy[2 * k], ly[2 * k], gy[k].x);
-        two_sum_add(hy[2 * k + 1], ly[2 * k + 1], gy[k].y);
-        two_sum_add(hz[2 * k], lz[2 * k], gz[k].x);
-        two_sum_add(hz[2 * k + 1], lz[2 * k + 1], gz[k].y);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < TPT; ++k) {
-      const int t = t0 + threadIdx.x + k * kPairThreads;
-      if (t < a.n_tgt) {
-        double* o = a.part + (size_t)chunk * 4 * a.ld + t;
-        o[0] = (double)hp[k] + (double)lp[k];
-        o[(size_t)a.ld] = (double)hx[k] + (double)lx[k];
-        o[2 * (size_t)a.ld] = (double)hy[k] + (double)ly[k];
-        o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
-      }
-    }
-  }
-}
-
-// Low-register variant of the packed kernel: the compensated (hi, lo) sums
-// of every target live in shared memory (one column per thread, so the
-// accesses are conflict-free) and the own-image ranges are read only in the
-// rare guarded tiles, which lets more CTAs share an SM.
-// TwoSum of v into the (hi, lo) pair of target slot `slot`, component comp.
-__device__ __forceinline__ void smem_two_sum(float* acc, int slot, int comp, float v) {
-  float* hp = acc + ((8 * slot + 2 * comp) * kPairThreads + threadIdx.x);
-  float hi = hp[0], lo = hp[kPairThreads];
-  two_sum_add(hi, lo, v);
-  hp[0] = hi;
-  hp[kPairThreads] = lo;
-}
-
-template <int NP>
-__device__ __forceinline__ void pair_item_f32x2s(const PairArgs& a, int item, float4* sh, float* acc) {
-  const float4* __restrict__ tgt = (const float4*)a.tgt;
-  const float4* __restrict__ src = (const float4*)a.src;
-  constexpr int TPT = 2 * NP;
-  const int ns = a.sc ? a.sc->Ns : a.n_src;
-  int per = (ns + a.n_chunks - 1) / a.n_chunks;
-  per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-  const int t0 = tile * kPairThreads * TPT;
-  float2 nx[NP], ny[NP], nz[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
-    const int tb = ta + kPairThreads;
-    const float4 va = (ta < a.n_tgt) ? tgt[ta] : make_float4(kFar, kFar, kFar, 0.f);
-    const float4 vb = (tb < a.n_tgt) ? tgt[tb] : make_float4(kFar, kFar, kFar, 0.f);
-    nx[k] = make_float2(-va.x, -vb.x);
-    ny[k] = make_float2(-va.y, -vb.y);
-    nz[k] = make_float2(-va.z, -vb.z);
-  }
-  // acc[(8*k + c) * kPairThreads + tid]: c = 2*component + (0 hi, 1 lo), target slot k
-#pragma unroll
-  for (int r = 0; r < 8 * TPT; ++r) acc[r * kPairThreads + threadIdx.x] = 0.f;
-  int lo1 = 0, hi1 = 0;
-  own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
-  const int s0 = chunk * per;
-  const int s1 = min(ns, s0 + per);
-  for (int sb = s0; sb < s1; sb += kTile32) {
-    const int n = min(kTile32, s1 - sb);
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kPairThreads) {
-      const float4 v = src[sb + i];
-      sh[2 * i] = make_float4(v.x, v.x, v.y, v.y);
-      sh[2 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
-    }
-    __syncthreads();
-    float2 p[NP], gx[NP], gy[NP], gz[NP];
-#pragma unroll
-    for (int k = 0; k < NP; ++k) p[k] = gx[k] = gy[k] = gz[k] = make_float2(0.f, 0.f);
-    const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
-                      (sb < hi1 && lo1 < sb + n);
-    if (!diag) {
-#pragma unroll kUnroll
-      for (int i = 0; i < n; ++i) {
-        const float4 A = sh[2 * i], B = sh[2 * i + 1];
-        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
-        const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const float2 dx = __fadd2_rn(sx, nx[k]);
-          const float2 dy = __fadd2_rn(sy, ny[k]);
-          const float2 dz = __fadd2_rn(sz, nz[k]);
-          float2 r2 = __fmul2_rn(dx, dx);
-          r2 = __ffma2_rn(dy, dy, r2);
-          r2 = __ffma2_rn(dz, dz, r2);
-          const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-          const float2 qi = __fmul2_rn(sq, inv);
-          p[k] = __fadd2_rn(p[k], qi);
-          const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
-          gx[k] = __ffma2_rn(q3, dx, gx[k]);
-          gy[k] = __ffma2_rn(q3, dy, gy[k]);
-          gz[k] = __ffma2_rn(q3, dz, gz[k]);
-        }
-      }
-    } else {
-      for (int i = 0; i < n; ++i) {
-        const float4 A = sh[2 * i], B = sh[2 * i + 1];
-        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
-        const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
-        const int sidx = sb + i;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
-          const int tb = ta + kPairThreads;
-          const bool ia = a.ioff && ta < a.n_diag, ib = a.ioff && tb < a.n_diag;
-          const int soa = ia ? a.ioff[ta] : 0, sca = ia ? a.icnt[ta] : 0;
-          const int sob = ib ? a.ioff[tb] : 0, scb = ib ? a.icnt[tb] : 0;
-          const float2 dx = __fadd2_rn(sx, nx[k]);
-          const float2 dy = __fadd2_rn(sy, ny[k]);
-          const float2 dz = __fadd2_rn(sz, nz[k]);
-          float2 r2 = __fmul2_rn(dx, dx);
-          r2 = __ffma2_rn(dy, dy, r2);
-          r2 = __ffma2_rn(dz, dz, r2);
-          // an ion skips its identity image and its own shifted images
-          const bool owna = (sidx == ta && ta < a.n_diag) || (unsigned)(sidx - soa) < (unsigned)sca;
-          const bool ownb = (sidx == tb && tb < a.n_diag) || (unsigned)(sidx - sob) < (unsigned)scb;
-          const float2 inv = make_float2(owna ? 0.f : rsqrtf(r2.x), ownb ? 0.f : rsqrtf(r2.y));
-          const float2 qi = __fmul2_rn(sq, inv);
-          p[k] = __fadd2_rn(p[k], qi);
-          const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
-          gx[k] = __ffma2_rn(q3, dx, gx[k]);
-          gy[k] = __ffma2_rn(q3, dy, gy[k]);
-          gz[k] = __ffma2_rn(q3, dz, gz[k]);
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      smem_two_sum(acc, 2 * k, 0, p[k].x);
-      smem_two_sum(acc, 2 * k + 1, 0, p[k].y);
-      smem_two_sum(acc, 2 * k, 1, gx[k].x);
-      smem_two_sum(acc, 2 * k + 1, 1, gx[k].y);
-      smem_two_sum(acc, 2 * k, 2, gy[k].x);
-      smem_two_sum(acc, 2 * k + 1, 2, gy[k].y);
-      smem_two_sum(acc, 2 * k, 3, gz[k].x);
-      smem_two_sum(acc, 2 * k + 1, 3, gz[k].y);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < TPT; ++k) {
-    const int t = t0 + threadIdx.x + k * kPairThreads;
-    if (t < a.n_tgt) {
-      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
-#pragma unroll
-      for (int comp = 0; comp < 4; ++comp) {
-        const float* hp = acc + ((8 * k + 2 * comp) * kPairThreads + threadIdx.x);
-        o[comp * (size_t)a.ld] = (double)hp[0] + (double)hp[kPairThreads];
-      }
-    }
-  }
-}
-
-template <int NP>
-__global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2s(PairArgs a) {
-  __shared__ float4 sh[2 * kTile32];
-  extern __shared__ float acc[];   // 8 * 2NP * kPairThreads floats
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2s<NP>(a, item, sh, acc);
-}
-
-template <int NP>
-__global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
-  __shared__ float4 sh[2 * kTile32];
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2<NP>(a, item, sh);
-}
-
-// Ragged launch over several independent pair sums (requests of the serving
-// loop): item i belongs to the descriptor d with start[d] <= i < start[d+1].
-// Each item writes only its own descriptor's partials, so every request's
-// result is the same whatever else shares the launch.
-// Ragged launches run the packed kernel with 2 targets per thread (code 12):
-// its 512-target tiles give small requests more items than the 4-target
-// variants, which keeps served latency down.  Descriptors must be planned
-// with that tile size.
-__global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged(const PairArgs* __restrict__ descs,
-                                                                const int* __restrict__ start,
-                                                                int n_desc) {
-  __shared__ float4 sh[2 * kTile32];
-  const int total = start[n_desc];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int d = 0;
-    while (d + 1 < n_desc && start[d + 1] <= item) ++d;
-    const PairArgs a = descs[d];
-    pair_item_f32x2<1>(a, item - start[d], sh);
-  }
-}
-
-int pair_ragged_variant() { return 12; }
-
-cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
-                               cudaStream_t s) {
-  if (grid < 1) grid = 1;
-  k_pair_ragged<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
-  return cudaGetLastError();
-}
-
-int pair_ragged_slots() {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged, kPairThreads, 0);
-  return sms * (per < 1 ? 1 : per);
-}
-
-__global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
-  __shared__ double4_32a sh[kTile64];
-  const double4_32a* __restrict__ tgt = (const double4_32a*)a.tgt;
-  const double4_32a* __restrict__ src = (const double4_32a*)a.src;
-  const int ns = a.sc ? a.sc->Ns : a.n_src;
-  int per = (ns + a.n_chunks - 1) / a.n_chunks;
-  per = (per + kTile64 - 1) / kTile64 * kTile64;
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-    const int t = tile * kPairThreads + threadIdx.x;
-    const double4_32a tv = (t < a.n_tgt) ? tgt[t] : make_double4_32a(1e18, 1e18, 1e18, 0.0);
-    double p = 0, gx = 0, gy = 0, gz = 0;
-    const int s0 = chunk * per;
-    const int s1 = min(ns, s0 + per);
-    const int t0 = tile * kPairThreads;
-    for (int sb = s0; sb < s1; sb += kTile64) {
-      const int n = min(kTile64, s1 - sb);
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
-      __syncthreads();
-      const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads) && (t0 < sb + n);
-      for (int i = 0; i < n; ++i) {
-        const double4_32a s = sh[i];
-        const double dx = s.x - tv.x, dy = s.y - tv.y, dz = s.z - tv.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        double inv = rsqrt(r2);
-        if (diag && sb + i == t && t < a.n_diag) inv = 0.0;
-        const double qi = s.w * inv;
-        p += qi;
-        const double q3 = qi * inv * inv;
-        gx += q3 * dx;
-        gy += q3 * dy;
-        gz += q3 * dz;
-      }
-    }
-    if (t < a.n_tgt) {
-      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
-      o[0] = p;
-      o[(size_t)a.ld] = gx;
-      o[2 * (size_t)a.ld] = gy;
-      o[3 * (size_t)a.ld] = gz;
-    }
-  }
-}
-
-// Kernel variants of the FP32 path, by code: 1, 2, 4 = scalar FP32 with that
-// many targets per thread; 12, 14 = packed FP32x2 with 2 or 4 targets;
-// 24 = packed, 4 targets, compensated sums in shared memory.
-int pair_tile_targets(int precision, int tpt) {
-  if (precision == 0) return kPairThreads;
-  return kPairThreads * (tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);
-}
-
-static const void* pair_fn(int precision, int tpt) {
-  if (precision == 0) return (const void*)k_pair_f64;
-  switch (tpt) {
-    case 1: return (const void*)k_pair_f32<1>;
-    case 2: return (const void*)k_pair_f32<2>;
-    case 12: return (const void*)k_pair_f32x2<1>;
-    case 14: return (const void*)k_pair_f32x2<2>;
-    case 24: return (const void*)k_pair_f32x2s<2>;
-    default: return (const void*)k_pair_f32<4>;
-  }
-}
-
-int pair_slots(int precision, int tpt) {
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fn(precision, tpt), kPairThreads,
-                                                tpt == 24 ? kAccBytes2 : 0);
-  if (per < 1) per = 1;
-  return sms * per;
-}
-
-cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s) {
-  if (grid < 1) grid = 1;
-  if (precision == 0) k_pair_f64<<<grid, kPairThreads, 0, s>>>(a);
-  else if (tpt == 1) k_pair_f32<1><<<grid, kPairThreads, 0, s>>>(a);
-  else if (tpt == 2) k_pair_f32<2><<<grid, kPairThreads, 0, s>>>(a);
-  else if (tpt == 12) k_pair_f32x2<1><<<grid, kPairThreads, 0, s>>>(a);
-  else if (tpt == 14) k_pair_f32x2<2><<<grid, kPairThreads, 0, s>>>(a);
-  else if (tpt == 24) k_pair_f32x2s<2><<<grid, kPairThreads, kAccBytes2, s>>>(a);
-  else k_pair_f32<4><<<grid, kPairThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ fit + map
 constexpr int kFitThreads = 256;
 
+// v = [Phi_B at the check points ; (2D) dPhi_B/dz there ; (gradient rows)
+// dx, dy, dz Phi_B at the first n_grad check points (monitoring points and
+// their wraps), component-major].
 __global__ void k_check_combine(const double* part, int n_chunks, int ld, int N, int n_check,
-                                int dims, double* v, double* cphi, double* cdz) {
+                                int dims, int n_grad, double* v, double* cphi, double* cdz) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_check) return;
   double p = 0.0, d = 0.0;
@@ -843,6 +288,17 @@ __global__ void k_check_combine(const double* part, int n_chunks, int ld, int N,
   if (dims == 2) v[n_check + c] = d;
   cphi[c] = p;
   cdz[c] = d;
+  if (c < n_grad) {
+    double gx = 0.0, gy = 0.0;
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      gx += part[((size_t)ch * 4 + 1) * ld + N + c];
+      gy += part[((size_t)ch * 4 + 2) * ld + N + c];
+    }
+    double* vg = v + (dims == 2 ? 2 * n_check : n_check);
+    vg[c] = gx;
+    vg[n_grad + c] = gy;
+    vg[2 * n_grad + c] = d;
+  }
 }
 
 __global__ void __launch_bounds__(kFitThreads) k_gemv_rows(const double* P, int nv, const double* v, double* A) {
@@ -869,12 +325,116 @@ __global__ void k_surface(const double* W, int M, int nA, const double* A, const
 }
 
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,
-                       const double* P, int nA, int nv, const double* W, int M,
+                       int n_grad, const double* P, int nA, int nv, const double* W, int M,
                        const double* ysurf, double scale, double* v, double* A, double* cphi,
                        double* cdz, double* Q, float4* s32, double4_32a* s64, cudaStream_t s) {
-  k_check_combine<<<(n_check + 255) / 256, 256, 0, s>>>(part, n_chunks, ld, N, n_check, dims, v, cphi, cdz);
+  k_check_combine<<<(n_check + 255) / 256, 256, 0, s>>>(part, n_chunks, ld, N, n_check, dims, n_grad, v,
+                                                        cphi, cdz);
   k_gemv_rows<<<nA, kFitThreads, 0, s>>>(P, nv, v, A);
   k_surface<<<(M + 127) / 128, 128, 0, s>>>(W, M, nA, A, ysurf, scale, Q, s32, s64);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ far field as a series
+// The fitted truncated series of Sec. 2.2, Eq. 5 evaluated directly at each
+// ion (an alternative to the surface charges): phi = sum_{n>=1} A_nm S_nm,
+// S_nm the real orthonormal solid harmonics in coordinates scaled by 1/R_c,
+// written as polynomials: (x + iy)^m = C_m + i S_m and
+// V_n^m(z, r^2) = r^(n-m) d^m P_n/dt^m (t = z/r) from the three-term
+// recursion.  The gradient carries dV/dz at fixed r^2, dV/d(r^2) and the x, y
+// derivatives of C_m, S_m along the same recursions.  norm[n*(p+1) + m] holds
+// c_n0 for m = 0 and sqrt(2) c_nm (2m-1)!! for m > 0.
+template <typename T, typename TV>
+__global__ void __launch_bounds__(256) k_far_series(const TV* __restrict__ tgt, int N, const double* __restrict__ A,
+                                                    const double* __restrict__ norm, int p, double inv_rc,
+                                                    double* __restrict__ out) {
+  // per block: the coefficient pairs (A_n,m c, A_n,-m c) for 0 <= m <= n <= p in
+  // the working precision, then 1/k for k = 1..p (the recursion's divisor)
+  extern __shared__ __align__(16) unsigned char far_smem[];
+  T* coef = reinterpret_cast<T*>(far_smem);
+  const int P1 = p + 1;
+  T* recip = coef + 2 * P1 * P1;
+  for (int e = threadIdx.x; e < P1 * P1; e += blockDim.x) {
+    const int n = e / P1, m = e - n * P1;
+    T ac = 0, as = 0;
+    if (n >= 1 && m <= n) {
+      const int base = n * n + n - 1;           // coefficient index of (n, 0)
+      const double c = norm[e];
+      ac = (T)(A[base + m] * c);
+      as = m ? (T)(A[base - m] * c) : (T)0;
+    }
+    coef[2 * e] = ac;
+    coef[2 * e + 1] = as;
+  }
+  for (int k = threadIdx.x; k <= p; k += blockDim.x) recip[k] = k ? (T)1 / (T)k : (T)0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const TV t = tgt[i];
+  const T s = (T)inv_rc;
+  const T x = (T)t.x * s, y = (T)t.y * s, z = (T)t.z * s;
+  const T r2 = x * x + y * y + z * z;
+  T phi = 0, gx = 0, gy = 0, gz = 0;
+  T C = 1, S = 0, Cx = 0, Cy = 0, Sx = 0, Sy = 0;
+  for (int m = 0; m <= p; ++m) {
+    // V_n^m / (2m-1)!!: the recursion is linear, so the double factorial
+    // lives in the host-side table (keeps FP32 in range for large p)
+    T v1 = 1, vz1 = 0, vr1 = 0;       // V_{n-1}
+    T v2 = 0, vz2 = 0, vr2 = 0;       // V_{n-2}
+    for (int n = m; n <= p; ++n) {
+      T v, vz, vr;
+      if (n == m) {
+        v = v1; vz = vz1; vr = vr1;
+      } else {
+        if (n == m + 1) {
+          const T a = (T)(2 * m + 1);
+          v = a * z * v1;
+          vz = a * (v1 + z * vz1);
+          vr = a * z * vr1;
+        } else {
+          const T a = (T)(2 * n - 1), b = (T)(n + m - 1), inv = recip[n - m];
+          v = (a * z * v1 - b * r2 * v2) * inv;
+          vz = (a * (v1 + z * vz1) - b * r2 * vz2) * inv;
+          vr = (a * z * vr1 - b * (v2 + r2 * vr2)) * inv;
+        }
+        v2 = v1; vz2 = vz1; vr2 = vr1;
+        v1 = v; vz1 = vz; vr1 = vr;
+      }
+      if (n >= 1) {
+        // grad V = (2x dV/dr2, 2y dV/dr2, dV/dz + 2z dV/dr2)
+        const T Vx = 2 * x * vr, Vy = 2 * y * vr, Vz = vz + 2 * z * vr;
+        const T ac = coef[2 * (n * P1 + m)], as = coef[2 * (n * P1 + m) + 1];
+        const T w = ac * C + as * S;                // combined azimuthal factor
+        const T wx = ac * Cx + as * Sx, wy = ac * Cy + as * Sy;
+        phi += v * w;
+        gx += Vx * w + v * wx;
+        gy += Vy * w + v * wy;
+        gz += Vz * w;
+      }
+    }
+    // (x + iy)^(m+1) and its x, y derivatives
+    const T nC = x * C - y * S, nS = x * S + y * C;
+    const T nCx = C + x * Cx - y * Sx, nSx = S + x * Sx + y * Cx;
+    const T nCy = x * Cy - S - y * Sy, nSy = x * Sy + C + y * Cy;
+    C = nC; S = nS; Cx = nCx; Sx = nSx; Cy = nCy; Sy = nSy;
+  }
+  out[i] = (double)phi;
+  out[(size_t)N + i] = (double)gx * inv_rc;
+  out[2 * (size_t)N + i] = (double)gy * inv_rc;
+  out[3 * (size_t)N + i] = (double)gz * inv_rc;
+}
+
+cudaError_t launch_far_series(int precision, const void* tgt, int N, const double* A, const double* norm,
+                              int p, double inv_rc, double* out, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int grid = (N + 255) / 256;
+  const size_t P1 = (size_t)p + 1;
+  const size_t smem = (2 * P1 * P1 + P1) * (precision ? sizeof(float) : sizeof(double));
+  if (precision)
+    k_far_series<float, float4><<<grid, 256, smem, s>>>((const float4*)tgt, N, A, norm, p, inv_rc, out);
+  else
+    k_far_series<double, double4_32a><<<grid, 256, smem, s>>>((const double4_32a*)tgt, N, A, norm, p, inv_rc,
+                                                              out);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,25 @@ def test_geometry_2d_matches_oracle(P, gam):
     assert np.abs(T - To).max() < 1e-8 * np.abs(To).max()
 
 
+@pytest.mark.parametrize("dims", [3, 2])
+def test_geometry_gradient_rows_match_oracle(P, dims):
+    # the gradient-periodicity rows: the host builds their basis gradients by
+    # an analytic recursion, the oracle by complex steps of the polynomial form
+    from oracle import hsma
+    box = (10.0, 10.0, 10.0) if dims == 3 else (20.0, 20.0, 10.0)
+    p, M, G, w = 6, 600, 16, 0.1
+    st = hsma.make_setup(box, dims, p, M, 0.4, -0.2, dtn_grid=G, grad_rows=True, grad_weight=w)
+    kw = dict(gamma_top=0.4, gamma_bot=-0.2, G=G, grad_weight=w)
+    sz = sizes(P, box, dims, p, M, **kw)
+    assert sz["rank"] == (p + 1) ** 2 - 1
+    assert sz["nv"] == st.P.shape[1] == sizes(P, box, dims, p, M, G=G)["nv"] + 6 * st.n_mon
+    T = P.hsma_geometry_array(box, dims, p, M, "T", M * sz["nv"], **kw).reshape(M, sz["nv"])
+    To = st.W @ st.P
+    assert np.abs(T - To).max() < 1e-8 * np.abs(To).max()
+    # the rows change the map (the gradient block is not empty)
+    assert np.abs(To[:, -6 * st.n_mon:]).max() > 1e-3 * np.abs(To).max()
+
+
 def test_geometry_rejects_bad_arguments(P):
     with pytest.raises(P.HSMAError):
         P.hsma_geometry_array((10, 10, 10), 3, 6, 10, "sizes", 8)       # M < (p+1)^2

@@ -1,0 +1,97 @@
+"""GPU parity of the fit with gradient-periodicity rows (option grad_rows)
+against the oracle's make_setup(grad_rows=True): the check-point gradients
+enter the raw vector of the fit (Sec. 2.2, Eq. 6, extended), everything else
+is the default path.  Tolerances: energy error <= 1e-6 of |E| (FP64) and
+<= 1e-5 of the energy scale 1/2 sum |q_i Phi_i| (FP32); forces by relative RMS.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import hsma as O
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = {0: 1e-6, 1: 1e-5}
+F_TOL = {0: 1e-6, 1: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def frms(F, Fr):
+    return math.sqrt(np.mean(np.sum((F - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1)))
+
+
+def check(P, c, x, q, prec, far="surface", **opt):
+    st = O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
+                      dtn_grid=c.dtn_grid, grad_rows=True)
+    ref = O.evaluate(st, x, q, far=far)
+    h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=prec, grad_rows=1,
+               far_field=1 if far == "series" else 0, **opt)
+    E, F, pot = h.eval(x, q, potential=True)
+    assert int(h.info("Ns")) == ref["Ns"]
+    # FP32 rounding scales with the energy scale 1/2 sum |q_i Phi_i|, not with
+    # the (possibly nearly cancelling) total, so the FP32 path is judged there
+    scale = abs(ref["energy"]) if prec == 0 else 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
+    assert abs(E - ref["energy"]) <= E_TOL[prec] * scale, (E, ref["energy"], scale)
+    assert frms(F, ref["forces"]) <= F_TOL[prec]
+    if prec == 0:
+        A = h.array("coeffs", len(ref["A"]))
+        assert np.abs(A - ref["A"]).max() <= 1e-9 * np.abs(ref["A"]).max()
+    h.close()
+    return E
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grad_rows_cfg1(P, prec):
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    check(P, c, x, q, prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grad_rows_with_series_far_field(P, prec):
+    c = workloads.small_case(1001, dims=3, box=(10.0, 10.0, 10.0), p=8, M=1200,
+                             valences=(2, -1), seed=7)
+    x, q = workloads.electrolyte(c)
+    check(P, c, x, q, prec, far="series")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.5, -0.3)])
+def test_grad_rows_2d(P, prec, gam):
+    c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam,
+                             G=24, seed=13)
+    x, q = workloads.electrolyte(c)
+    check(P, c, x, q, prec, dtn_grid=24)
+
+
+def test_grad_rows_option_rebuilds_geometry(P):
+    # switching the rows on and off rebuilds the fit; off again reproduces the
+    # default result bit for bit
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=0)
+    E0, F0, _ = h.eval(x, q, potential=True)
+    nv0 = h.array("coeffs", (c.p + 1) ** 2 - 1)
+    h.set_option("grad_rows", 1)
+    E1, F1, _ = h.eval(x, q, potential=True)
+    h.set_option("grad_rows", 0)
+    E2, F2, _ = h.eval(x, q, potential=True)
+    assert np.array_equal(h.array("coeffs", (c.p + 1) ** 2 - 1), nv0)
+    h.close()
+    assert E2 == E0 and np.array_equal(F2, F0)
+    assert E1 != E0 and rel(E1, E0) < 5e-3
