@@ -48,6 +48,11 @@ notes of the repository):
     first upper image reflects across the top interface).  See ``ewald``.
  R8 Neutrality: |sum q| > 1e-10 sum |q| is an error; otherwise the residual is
     removed as q_i -= sum q / N.
+ R2b Unmasked near set (optional): every image of every shift of the table is
+    near, whether inside B or not (3D: the full 27 cells at lambda <= sqrt 3).
+    The far sources then start at 1.5 cells from the centre, so the series of
+    Eq. 5 converges faster inside the circumsphere, at about 4.5 times the
+    near-field cost.  The fit and the surface map are unchanged.
  R9 Gradient-periodicity rows (optional, off by default; not in the paper's
     fit): for every periodic row of R4/R5 three more rows, one per Cartesian
     component d, require the field to be periodic as well:
@@ -122,6 +127,7 @@ class Setup:
     sing: np.ndarray = field(default=None)
     grad_rows: bool = False                    # R9
     grad_weight: float = 0.0
+    sphere_mask: bool = True                   # R2 (False: R2b)
 
 
 def shift_table(dims, box, Rs, gamma_top=0.0, gamma_bot=0.0):
@@ -179,9 +185,10 @@ def face_grid(box, G):
 
 def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
                n_monitor=None, dtn_grid=80, prefactor=1.0, grad_rows=False,
-               grad_weight=GRAD_WEIGHT):
+               grad_weight=GRAD_WEIGHT, sphere_mask=True):
     """Geometry-only preparation: sphere, shifts, check points, fit, map.
-    grad_rows adds the gradient-periodicity rows of R9."""
+    grad_rows adds the gradient-periodicity rows of R9; sphere_mask=False
+    takes the unmasked near set of R2b."""
     box = tuple(float(b) for b in box)
     if dims not in (2, 3):
         raise OracleError("dims must be 2 or 3")
@@ -200,6 +207,7 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
                float(gamma_bot), int(dtn_grid), float(prefactor))
     st.grad_rows = bool(grad_rows)
     st.grad_weight = float(grad_weight)
+    st.sphere_mask = bool(sphere_mask)
     st.Rc = 0.5 * math.sqrt((Lx * Lx + Ly * Ly) + Lz * Lz)
     st.Rs = st.lam * st.Rc
     st.Rs2 = st.Rs * st.Rs
@@ -327,14 +335,15 @@ def prepare_inputs(st, x, q):
 
 
 def near_set(st, xc, q):
-    """Images inside B (step 1, R2): positions, charges, source index, shift index."""
+    """Images inside B (step 1, R2), or every image of the table (R2b):
+    positions, charges, source index, shift index."""
     pos, chg, src, sid = [], [], [], []
     for s, (sx, sy, zs, zo, f) in enumerate(st.shifts):
         px = xc[:, 0] + sx
         py = xc[:, 1] + sy
         pz = zs * xc[:, 2] + zo
         r2 = (px * px + py * py) + pz * pz
-        inside = r2 < st.Rs2
+        inside = (r2 < st.Rs2) if st.sphere_mask else np.ones(len(px), dtype=bool)
         j = np.nonzero(inside)[0]
         pos.append(np.stack([px[j], py[j], pz[j]], -1))
         chg.append(f * q[j])

@@ -320,3 +320,32 @@ def test_gradient_rows_keep_rank_and_accuracy():
         errs.append(rel_force_err(hsma.evaluate(st, x, q)["forces"], Fe))
     assert conds[1] < conds[0]
     assert errs[1] < 1.02 * errs[0]
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_unmasked_near_set_counts_and_is_more_accurate(dims):
+    # R2b: every image of the shift table is near, so N_s = N x (table rows);
+    # the far sources start further out and the series converges faster, so
+    # the error against the plain sums drops at equal p
+    if dims == 3:
+        L = 10.0 * (0.3) ** (1 / 3)
+        x, q = system3d(300, L, 21)
+        Ee, Fe = ewald_of(x, q, L)
+        mk = lambda m: hsma.make_setup([L, L, L], 3, 6, 800, sphere_mask=m)
+    else:
+        c = workloads.small_case(40, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=(0.5, 0.5),
+                                 seed=9)
+        x, q = workloads.electrolyte(c, margin=0.5)
+        xc = x - np.array([10.0, 10.0, 5.0])
+        Ee, _, ge, _ = slab_ewald(xc, q, *c.box, 0.5, 0.5, tol=1e-12)
+        Fe = -q[:, None] * ge
+        mk = lambda m: hsma.make_setup(c.box, 2, 6, 600, 0.5, 0.5, dtn_grid=32, sphere_mask=m)
+    res = {}
+    for m in (True, False):
+        st = mk(m)
+        out = hsma.evaluate(st, x, q)
+        if not m:
+            assert out["Ns"] == len(x) * len(st.shifts)
+        res[m] = (abs(out["energy"] - Ee) / abs(Ee), rel_force_err(out["forces"], Fe), out["Ns"])
+    assert res[False][2] > 2 * res[True][2]
+    assert res[False][1] < 0.5 * res[True][1]
