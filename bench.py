@@ -337,6 +337,60 @@ def far_series_compare(P, torch, stream, c, xd, qd, fd, h_surface, n=10):
     return rec
 
 
+def option_variant(P, torch, stream, c, xd, qd, fd, e_default, n=3, **opt):
+    """The main workload with one option changed: evaluations/s, N_s and the
+    energy / force difference from the default configuration (fd, e_default)."""
+    h = P.HSMA(c.box, c.dims, c.p, c.M, precision=1, **opt)
+    P.hsma_set_stream(h.h, stream.cuda_stream)
+    e = np.zeros(1)
+    f = torch.empty_like(fd)
+    P.hsma_eval_into(h.h, xd, qd, c.N, e, f)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n):
+        P.hsma_eval_into(h.h, xd, qd, c.N, e, f)
+    b.record(stream)
+    torch.cuda.synchronize()
+    rec = {"options": opt, "evals_per_s": 1e3 * n / a.elapsed_time(b), "N_s": int(P.hsma_get_info(h.h, "Ns")),
+           "rel_energy_vs_default": abs(float(e[0]) - e_default) / abs(e_default),
+           "rel_force_rms_vs_default": float(torch.sqrt(((f - fd) ** 2).sum() / (fd ** 2).sum()))}
+    h.close()
+    return rec
+
+
+def paper_like(P, torch, dev, stream, n32=5):
+    """The main workload shape with ions kept >= 0.8 apart (the soft cores of
+    the paper's LJ electrolytes): FP32 evaluations/s and the FP32-vs-FP64
+    energy and force errors, which close pairs dominate in the uniform case."""
+    c = workloads.case(2)
+    x, q = workloads.electrolyte(c, min_dist=0.8)
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q).to(dev)
+    out = {"workload": c.name + "_mindist0.8", "N": c.N}
+    res = {}
+    for prec, n in ((1, n32), (0, 1)):
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=prec, autotune=1 if prec else 0)
+        P.hsma_set_stream(h.h, stream.cuda_stream)
+        e = np.zeros(1)
+        f = torch.empty((c.N, 3), dtype=torch.float64, device=dev)
+        P.hsma_eval_into(h.h, xd, qd, c.N, e, f)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            P.hsma_eval_into(h.h, xd, qd, c.N, e, f)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[("fp32" if prec else "fp64") + "_evals_per_s"] = 1e3 * n / a.elapsed_time(b)
+        res[prec] = (float(e[0]), f)
+        h.close()
+    (e32, f32), (e64, f64) = res[1], res[0]
+    out["fp32_vs_fp64_rel_energy"] = abs(e32 - e64) / abs(e64)
+    out["fp32_vs_fp64_rel_force_rms"] = float(torch.sqrt(((f32 - f64) ** 2).sum() / (f64 ** 2).sum()))
+    return out
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -557,7 +611,14 @@ def main():
     if not args.no_other_cases:
         if not args.far_field:
             line["far_field_series"] = far_series_compare(P, torch, stream, c, xd, qd, fd, h)
+            e0 = np.zeros(1)
+            P.hsma_eval_into(h.h, xd, qd, N, e0, fd)
+            torch.cuda.synchronize()
+            line["option_variants"] = [
+                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), sphere_mask=0),
+                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), grad_rows=1)]
         line["other_cases"] = other_cases(P, torch, dev, stream)
+        line["paper_like"] = paper_like(P, torch, dev, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

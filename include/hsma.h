@@ -108,6 +108,12 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       (packed FP32x2, 2 or 4 targets); turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
+ *   "sphere_mask"       1 (default) = the near set is the images inside the
+ *                       sphere B (Sec. 2.2, first step); 0 = every image of
+ *                       the enumerated cells (3D: all 27 at lambda <= sqrt 3),
+ *                       inside B or not.  The far sources then start 1.5
+ *                       cells out and the series converges faster: more
+ *                       accurate at equal p, about 4.5 x the near-field cost.
  *   "grad_rows"         1 = append gradient-periodicity rows to the fit: for
  *                       every periodicity row of Eq. 6 three more that ask
  *                       the field (each Cartesian component) to be periodic

@@ -58,6 +58,7 @@ bool is_device_ptr(const void* ptr) {
 double estimate_images(const Geometry& g, int64_t N) {
   const double* L = g.par.box;
   const double kPi = 3.14159265358979323846;
+  if (!g.par.sphere_mask) return (double)N * (double)g.shifts.size();
   if (g.par.dims == 3) {
     const double r = 4.0 * kPi / 3.0 * g.Rs * g.Rs * g.Rs / (L[0] * L[1] * L[2]);
     return (double)N * std::min<double>((double)g.shifts.size(), std::max(1.0, r));
@@ -256,7 +257,8 @@ int stage_prep(hsma_ctx* h, int64_t N) {
   a.N = (int)N;
   a.dims = g.par.dims;
   for (int d = 0; d < 3; ++d) a.L[d] = g.par.box[d];
-  a.Rs2 = g.Rs2;
+  // unmasked near set: every image of the table passes r2 < +inf
+  a.Rs2 = g.par.sphere_mask ? g.Rs2 : HUGE_VAL;
   a.shifts = (const double*)h->d_shifts.p;
   a.n_shift = (int)g.shifts.size();
   a.check_pts = geo_C(h);
@@ -404,15 +406,18 @@ int finish_eval(hsma_ctx* h, double* energy) {
 // Process-wide cache of tuned near/check launches: (dims, precision, N bucket,
 // check-point bucket) -> (kernel variant, source chunks).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune;
 
 // Time the near/check launch for each candidate (kernel variant x chunk
 // count) on the real input and keep the fastest.  Inputs are in d_x, d_q.
 static int tune_near(hsma_ctx* h, int64_t N) {
   const Geometry& g = h->geo;
   const int prec = h->precision;
+  // keyed by N, the check-point count and the expected images per target
+  // (which the sphere radius and the mask set), each in quarter-octave buckets
   const auto key = std::make_tuple(g.par.dims, prec, (int)std::lround(4.0 * std::log2((double)N)),
-                                   (int)std::lround(4.0 * std::log2((double)g.n_check + 1.0)));
+                                   (int)std::lround(4.0 * std::log2((double)g.n_check + 1.0)),
+                                   (int)std::lround(4.0 * std::log2(h->ns_est / (double)N + 1.0)));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -600,6 +605,10 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "timing") {
     h->timing = (v != 0);
     drop_graph(h);
+  } else if (k == "sphere_mask") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "sphere_mask must be 0 or 1");
+    h->gp.sphere_mask = (int)v;
+    h->geo_dirty = true;
   } else if (k == "grad_rows") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "grad_rows must be 0 or 1");
     h->gp.grad_rows = (int)v;

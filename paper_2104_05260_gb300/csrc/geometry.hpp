@@ -26,6 +26,7 @@ struct GeoParams {
   int n_monitor = 98;
   double gtop = 0, gbot = 0;
   int G = 80;
+  int sphere_mask = 1;       // 0: every image of the shift table is near
   int grad_rows = 0;         // gradient-periodicity rows appended to the fit
   double grad_weight = 0.1;  // their weight, in units of R_c
 };

@@ -133,6 +133,25 @@ def test_2d_small(P, prec, gam):
     check_full(P, c, x, q, prec, dtn_grid=24)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_unmasked_near_set_3d(P, prec):
+    # every image of the 27 cells is near (option sphere_mask = 0)
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    st = O.make_setup(c.box, 3, c.p, c.M, lam=c.lam, sphere_mask=False)
+    assert len(st.shifts) == 27
+    check_full(P, c, x, q, prec, st=st, sphere_mask=0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_unmasked_near_set_2d(P, prec):
+    c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=(0.5, -0.3),
+                             G=24, seed=17)
+    x, q = workloads.electrolyte(c, margin=1e-3)
+    st = O.make_setup(c.box, 2, c.p, c.M, 0.5, -0.3, lam=c.lam, dtn_grid=24, sphere_mask=False)
+    check_full(P, c, x, q, prec, st=st, dtn_grid=24, sphere_mask=0)
+
+
 def test_errors_are_reported(P):
     c = workloads.small_case(20, dims=2, box=(20.0, 20.0, 10.0), p=4, M=200, G=8)
     x, q = workloads.electrolyte(c)

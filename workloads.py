@@ -59,22 +59,76 @@ def case(n, gamma=0.95):
     raise KeyError(n)
 
 
-def electrolyte(c, margin=0.0, seed=None):
-    """Positions (N, 3) in the API box and charges (N,) for a case."""
+def electrolyte(c, margin=0.0, seed=None, min_dist=0.0):
+    """Positions (N, 3) in the API box and charges (N,) for a case.
+
+    min_dist > 0 gives the "paper-like" variant: candidates drawn in the same
+    way are rejected while closer than min_dist (periodic minimum image in the
+    periodic directions) to an accepted ion, mimicking the soft cores of the
+    paper's Lennard-Jones electrolytes (Sec. 4.1: sigma-sized ions)."""
     rng = np.random.Generator(np.random.PCG64(c.seed if seed is None else seed))
     N = c.N
     Lx, Ly, Lz = c.box
-    x = np.empty((N, 3))
-    x[:, 0] = rng.uniform(0.0, Lx, N)
-    x[:, 1] = rng.uniform(0.0, Ly, N)
-    if c.dims == 3:
-        x[:, 2] = rng.uniform(0.0, Lz, N)
+    lo = max(margin, 1e-9 * Lz)
+
+    def draw(n):
+        y = np.empty((n, 3))
+        y[:, 0] = rng.uniform(0.0, Lx, n)
+        y[:, 1] = rng.uniform(0.0, Ly, n)
+        y[:, 2] = rng.uniform(0.0, Lz, n) if c.dims == 3 else rng.uniform(lo, Lz - lo, n)
+        return y
+
+    if min_dist <= 0.0:
+        x = draw(N)
     else:
-        lo = max(margin, 1e-9 * Lz)
-        x[:, 2] = rng.uniform(lo, Lz - lo, N)
+        x = _hard_core(draw, N, c.box, c.dims, min_dist)
     q = np.concatenate([np.full(k, float(v)) for v, k in sorted(c.counts.items())])
     q = q[rng.permutation(N)]
     return x, q
+
+
+def _hard_core(draw, N, box, dims, dmin, max_tries=200):
+    """Sequential rejection sampling on a cell grid (cells >= dmin wide)."""
+    L = np.asarray(box, dtype=np.float64)
+    nc = np.maximum(1, np.floor(L / dmin).astype(int))
+    cell = L / nc
+    per = (True, True, dims == 3)
+    grid = {}
+    out = np.empty((N, 3))
+    n = 0
+    d2 = dmin * dmin
+    for _ in range(max_tries):
+        for y in draw(2 * (N - n) + 64):
+            ci = np.minimum((y / cell).astype(int), nc - 1)
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        k = [ci[0] + dx, ci[1] + dy, ci[2] + dz]
+                        for a in range(3):
+                            if per[a]:
+                                k[a] %= nc[a]
+                        for j in grid.get(tuple(k), ()):
+                            dv = out[j] - y
+                            for a in range(3):
+                                if per[a]:
+                                    dv[a] -= L[a] * round(dv[a] / L[a])
+                            if dv @ dv < d2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                out[n] = y
+                grid.setdefault(tuple(ci), []).append(n)
+                n += 1
+                if n == N:
+                    return out
+    raise RuntimeError("hard-core sampling did not place every ion")
 
 
 def small_case(N, dims=3, box=None, p=6, M=800, lam=None, gammas=(0.0, 0.0), seed=11,
