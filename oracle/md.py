@@ -1,0 +1,170 @@
+"""Molecular dynamics of a primitive-model electrolyte (TEST INFRASTRUCTURE).
+
+The validation workload of Sec. 4.1: ions are soft spheres of diameter sigma
+that repel through the shifted-truncated Lennard-Jones potential (cut at its
+minimum 2^(1/6) sigma, energy coupling eps = kT), and interact through
+Coulomb's law with Bjerrum length l_B (energy l_B kT q_i q_j / r, the
+electrostatic solver's prefactor).  Canonical ensemble with a Nose-Hoover
+thermostat; velocity-Verlet integration.
+
+One step of length dt, in this order (a symmetric Trotter splitting of the
+Nose-Hoover equations of motion, thermostat chain of length one):
+
+  thermostat half step:  G = (2K - g kT) / Q;  xi += G dt/4
+                         v *= exp(-xi dt/2);  eta += xi dt/2
+                         G = (2K - g kT) / Q;  xi += G dt/4   (K after scaling)
+  kick:                  v += (dt/2) F / m
+  drift:                 x += dt v, wrapped into the box (image counters kept)
+  forces:                F = F_LJ(x) + F_coulomb(x)
+  kick:                  v += (dt/2) F / m
+  thermostat half step   (as above)
+
+with Q = g kT tdamp^2 and g = 3N - 3 degrees of freedom (the centre-of-mass
+momentum is conserved).  The extended energy H = K + U + Q xi^2/2 + g kT eta
+is conserved by the flow.  Readings: the paper states the damping time of its
+thermostat but not its chain length or the degrees of freedom; a single
+thermostat and g = 3N - 3 are taken here.  With the thermostat off the step
+is plain velocity Verlet (NVE).
+
+Everything is FP64 NumPy; the Coulomb forces come from a callable (the
+oracle's HSMA or Ewald sum).
+"""
+import math
+
+import numpy as np
+
+WCA_CUT = 2.0 ** (1.0 / 6.0)
+
+
+def wca(x, box, sigma=1.0, eps=1.0):
+    """Energy and forces of the shifted-truncated LJ repulsion, minimum image
+    in every periodic direction (3D), all pairs i < j."""
+    x = np.asarray(x, dtype=np.float64)
+    L = np.asarray(box, dtype=np.float64)
+    n = len(x)
+    F = np.zeros_like(x)
+    U = 0.0
+    rc2 = (WCA_CUT * sigma) ** 2
+    for i in range(n - 1):
+        d = x[i + 1:] - x[i]
+        d -= L * np.round(d / L)
+        r2 = np.sum(d * d, axis=1)
+        m = r2 < rc2
+        if not np.any(m):
+            continue
+        s2 = sigma * sigma / r2[m]
+        s6 = s2 * s2 * s2
+        U += float(np.sum(4.0 * eps * (s6 * s6 - s6) + eps))
+        # force on j (the partner) along d: 24 eps (2 s12 - s6) / r^2 * d
+        f = (24.0 * eps * (2.0 * s6 * s6 - s6) / r2[m])[:, None] * d[m]
+        F[i + 1:][m] += f
+        F[i] -= f.sum(axis=0)
+    return U, F
+
+
+class State:
+    """Positions (wrapped into [0, L)), image counters, velocities, thermostat."""
+
+    def __init__(self, x, v, q, box, mass=1.0):
+        self.box = np.asarray(box, dtype=np.float64)
+        self.x = np.array(x, dtype=np.float64)
+        self.img = np.zeros(self.x.shape, dtype=np.int64)
+        self.wrap()
+        self.v = np.array(v, dtype=np.float64)
+        self.q = np.array(q, dtype=np.float64)
+        self.m = float(mass)
+        self.xi = 0.0
+        self.eta = 0.0
+        self.F = None
+        self.U = None
+
+    def wrap(self):
+        k = np.floor(self.x / self.box)
+        self.x -= k * self.box
+        self.img += k.astype(np.int64)
+
+    def kinetic(self):
+        return 0.5 * self.m * float(np.sum(self.v * self.v))
+
+    def unwrapped(self):
+        return self.x + self.img * self.box
+
+
+class Integrator:
+    """Velocity Verlet with an optional Nose-Hoover thermostat (see header).
+
+    coulomb(x, q) -> (energy, forces) is the electrostatic solver; None leaves
+    Coulomb out.  tdamp None means NVE."""
+
+    def __init__(self, coulomb, dt, kT=1.0, tdamp=None, sigma=1.0, eps=1.0):
+        self.coulomb = coulomb
+        self.dt = float(dt)
+        self.kT = float(kT)
+        self.tdamp = tdamp
+        self.sigma = sigma
+        self.eps = eps
+
+    def forces(self, s):
+        U, F = wca(s.x, s.box, self.sigma, self.eps)
+        Uc = 0.0
+        if self.coulomb is not None:
+            Uc, Fc = self.coulomb(s.x, s.q)
+            F = F + Fc
+        s.U_lj, s.U_c = U, Uc
+        s.U = U + Uc
+        s.F = F
+
+    def _thermostat_half(self, s):
+        g = 3 * len(s.x) - 3
+        Q = g * self.kT * self.tdamp ** 2
+        h = 0.5 * self.dt
+        K = s.kinetic()
+        s.xi += (2.0 * K - g * self.kT) / Q * (h / 2)
+        f = math.exp(-s.xi * h)
+        s.v *= f
+        s.eta += s.xi * h
+        K = s.kinetic()
+        s.xi += (2.0 * K - g * self.kT) / Q * (h / 2)
+
+    def step(self, s):
+        if s.F is None:
+            self.forces(s)
+        if self.tdamp is not None:
+            self._thermostat_half(s)
+        s.v += (0.5 * self.dt / s.m) * s.F
+        s.x += self.dt * s.v
+        s.wrap()
+        self.forces(s)
+        s.v += (0.5 * self.dt / s.m) * s.F
+        if self.tdamp is not None:
+            self._thermostat_half(s)
+
+    def extended_energy(self, s):
+        H = s.kinetic() + s.U
+        if self.tdamp is not None:
+            g = 3 * len(s.x) - 3
+            Q = g * self.kT * self.tdamp ** 2
+            H += 0.5 * Q * s.xi ** 2 + g * self.kT * s.eta
+        return H
+
+
+def rdf_counts(x, box, mask_a, mask_b, rmax, nbins):
+    """Pair counts of species a around species b in nbins shells of width
+    rmax/nbins (minimum image), the histogram g(r) is built from."""
+    L = np.asarray(box, dtype=np.float64)
+    xa, xb = x[mask_a], x[mask_b]
+    h = np.zeros(nbins, dtype=np.int64)
+    for p in xb:
+        d = xa - p
+        d -= L * np.round(d / L)
+        r = np.sqrt(np.sum(d * d, axis=1))
+        r = r[(r > 0) & (r < rmax)]
+        h += np.bincount((r * (nbins / rmax)).astype(np.int64), minlength=nbins)[:nbins]
+    return h
+
+
+def maxwell_velocities(n, kT, mass, rng):
+    """Gaussian velocities at temperature kT with zero total momentum."""
+    v = rng.normal(0.0, math.sqrt(kT / mass), (n, 3))
+    v -= v.mean(axis=0)
+    return v

@@ -1,0 +1,150 @@
+"""Pins of the oracle's MD loop (the validation workload of Sec. 4.1) to facts
+it does not itself compute: the WCA closed form and F = -grad U by finite
+differences, time reversibility and second-order energy conservation of
+velocity Verlet, the Nose-Hoover thermostat against an independent RK4
+solution of its scalar equations for an ideal gas, conservation of the
+extended energy, and the RDF counts against a brute-force double loop."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import md
+from oracle.ewald import ewald3d
+
+
+def lattice(n_side, L, jitter, rng):
+    g = (np.arange(n_side) + 0.5) * (L / n_side)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    return x + rng.uniform(-jitter, jitter, x.shape)
+
+
+def ewald_coulomb(box, lb):
+    def f(x, q):
+        L = np.asarray(box)
+        xc = (x - L * np.floor(x / L)) - 0.5 * L
+        E, _, g = ewald3d(xc, q, box, tol=1e-14)
+        return lb * E, -lb * q[:, None] * g
+    return f
+
+
+def test_wca_closed_form_and_gradient():
+    box = [10.0, 10.0, 10.0]
+    for r in (0.9, 1.0, 1.1, md.WCA_CUT - 1e-9, 1.2):
+        x = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+        U, F = md.wca(x, box)
+        ref = 4 * (r ** -12 - r ** -6) + 1 if r < md.WCA_CUT else 0.0
+        assert abs(U - ref) < 1e-12 * max(1.0, abs(ref))
+        assert np.allclose(F[0], -F[1], atol=0)
+    assert md.wca(np.array([[1.0, 1, 1], [1.0 + md.WCA_CUT - 1e-9, 1, 1]]), box)[0] < 1e-7
+    rng = np.random.default_rng(0)
+    x = lattice(3, 3.3, 0.15, rng)
+    U, F = md.wca(x, [3.3] * 3)
+    assert U > 0
+    h = 1e-6
+    for i, d in ((0, 0), (5, 1), (13, 2)):
+        e = np.zeros_like(x); e[i, d] = h
+        fd = -(md.wca(x + e, [3.3] * 3)[0] - md.wca(x - e, [3.3] * 3)[0]) / (2 * h)
+        assert abs(fd - F[i, d]) < 1e-6 * max(1.0, np.abs(F).max())
+
+
+def small_system(seed=1, n_side=3, L=4.0):
+    rng = np.random.default_rng(seed)
+    x = lattice(n_side, L, 0.2, rng)
+    n = len(x)
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    if n % 2:
+        q[-1] = 0.0
+    v = md.maxwell_velocities(n, 1.0, 1.0, rng)
+    return x, v, q, [L, L, L]
+
+
+def test_velocity_verlet_is_time_reversible():
+    x, v, q, box = small_system()
+    it = md.Integrator(ewald_coulomb(box, 1.0), dt=0.005)
+    s = md.State(x, v, q, box)
+    x0 = s.unwrapped().copy()
+    for _ in range(25):
+        it.step(s)
+    s.v = -s.v
+    for _ in range(25):
+        it.step(s)
+    assert np.abs(s.unwrapped() - x0).max() < 1e-9
+    assert np.abs(s.v + v).max() < 1e-9
+
+
+def test_nve_energy_error_is_second_order():
+    x, v, q, box = small_system(seed=2)
+    devs = []
+    for dt in (0.004, 0.002):
+        it = md.Integrator(ewald_coulomb(box, 1.0), dt=dt)
+        s = md.State(x, v, q, box)
+        it.forces(s)
+        H0 = it.extended_energy(s)
+        dev = 0.0
+        for _ in range(int(round(0.08 / dt))):
+            it.step(s)
+            dev = max(dev, abs(it.extended_energy(s) - H0))
+        devs.append(dev)
+    assert 3.0 < devs[0] / devs[1] < 5.0
+
+
+def test_nose_hoover_matches_rk4_for_an_ideal_gas():
+    # no forces: only K and xi evolve, dK/dt = -2 xi K, dxi/dt = (2K - g kT)/Q
+    rng = np.random.default_rng(3)
+    n, kT, tdamp, dt, steps = 20, 1.0, 0.2, 0.01, 200
+    v = md.maxwell_velocities(n, 2.5, 1.0, rng)       # start hot
+    s = md.State(rng.uniform(0, 5, (n, 3)), v, np.zeros(n), [5.0] * 3)
+    it = md.Integrator(None, dt=dt, kT=kT, tdamp=tdamp, sigma=1e-9)   # WCA range ~0
+    K0 = s.kinetic()
+    for _ in range(steps):
+        it.step(s)
+    g = 3 * n - 3
+    Q = g * kT * tdamp ** 2
+
+    def rhs(y):
+        K, xi = y
+        return np.array([-2 * xi * K, (2 * K - g * kT) / Q])
+    y = np.array([K0, 0.0])
+    h = dt / 20
+    for _ in range(steps * 20):
+        k1 = rhs(y); k2 = rhs(y + h / 2 * k1); k3 = rhs(y + h / 2 * k2); k4 = rhs(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    assert abs(s.kinetic() - y[0]) < 1e-3 * K0
+    assert abs(s.xi - y[1]) < 1e-3 * max(1.0, abs(y[1]))
+
+
+def test_nose_hoover_conserves_the_extended_energy_and_thermalises():
+    rng = np.random.default_rng(4)
+    x = lattice(4, 5.0, 0.2, rng)
+    n = len(x)
+    v = md.maxwell_velocities(n, 2.0, 1.0, rng)
+    s = md.State(x, v, np.zeros(n), [5.0] * 3)
+    it = md.Integrator(None, dt=0.002, kT=1.0, tdamp=0.1)
+    it.forces(s)
+    H0 = it.extended_energy(s)
+    temps, drift = [], 0.0
+    for k in range(3000):
+        it.step(s)
+        drift = max(drift, abs(it.extended_energy(s) - H0))
+        if k >= 1000:
+            temps.append(2 * s.kinetic() / (3 * n - 3))
+    assert drift < 2e-3 * abs(H0)
+    assert abs(np.mean(temps) - 1.0) < 0.06
+
+
+def test_rdf_counts_match_brute_force():
+    rng = np.random.default_rng(5)
+    box = [6.0, 6.0, 6.0]
+    x = rng.uniform(0, 6.0, (40, 3))
+    a = np.arange(40) % 2 == 0
+    h = md.rdf_counts(x, box, a, ~a, 3.0, 12)
+    ref = np.zeros(12, dtype=np.int64)
+    for i in np.nonzero(~a)[0]:
+        for j in np.nonzero(a)[0]:
+            d = x[j] - x[i]
+            d -= 6.0 * np.round(d / 6.0)
+            r = math.sqrt(d @ d)
+            if r < 3.0:
+                ref[int(r / 0.25)] += 1
+    assert np.array_equal(h, ref)
