@@ -391,6 +391,70 @@ def paper_like(P, torch, dev, stream, n32=5):
     return out
 
 
+PAPER_E1 = {"monovalent": (0.3561, 1.2132e-3), "divalent": (-1.4840, 2.3875e-3),
+            "trivalent": (-3.2741, 3.8337e-3)}     # Sec. 4.1, table: HSMA3D mean, variance
+
+
+def md_e1(P, valence=1, steps_eq=20000, steps_prod=200000, rdf_every=100, seed=11, tdamp=0.01):
+    """The primitive electrolyte of Sec. 4.1 under the library's MD loop:
+    L = 25 sigma, 3000 ions (valence z:1, so 1500/1000/750 cations), WCA
+    soft spheres with eps = kT, Bjerrum length 3.5 sigma, dt = 0.01 tau,
+    Nose-Hoover with damping time 0.01 tau.  Electrostatics: HSMA3D with
+    p = 10, N_m = 200 (the paper's parameter line), M = 2000, the unmasked
+    near set (force error 3e-6 against Ewald at p = 10), FP32 pairs.
+    Start: hard-core random positions 1.0 sigma apart, Maxwell velocities.
+    Reports the total energy per ion (mean, variance; block standard error
+    of the mean over 20 blocks) beside the paper's, the cation-anion g(r)
+    peak and steps/s."""
+    L, N = 25.0, 3000
+    n_cat = {1: 1500, 2: 1000, 3: 750}[valence]
+    c = workloads.Case(f"e1_z{valence}", 3, (L, L, L), {valence: n_cat, -1: N - n_cat}, p=10, M=2000,
+                       lam=1.3, seed=seed)
+    x, q = workloads.electrolyte(c, min_dist=1.0)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    v = rng.normal(0.0, 1.0, (N, 3))
+    v -= v.mean(axis=0)
+    h = P.HSMA(c.box, 3, 10, 2000, precision=1, coulomb_prefactor=3.5, n_monitor=200, sphere_mask=0)
+    md = P.MD(h, x, v, q, mass=1.0, dt=0.01, kT=1.0, tdamp=tdamp, lj_sigma=1.0, lj_eps=1.0)
+    t0 = time.perf_counter()
+    md.run(steps_eq)
+    t_eq = time.perf_counter() - t0
+    bins, rmax = 100, 5.0
+    md.set_option("rdf_bins", bins)
+    md.set_option("rdf_rmax", rmax)
+    md.set_option("rdf_every", rdf_every)
+    t0 = time.perf_counter()
+    th = md.run(steps_prod)
+    t_prod = time.perf_counter() - t0
+    e = (th[:, 0] + th[:, 1] + th[:, 2]) / N
+    blocks = np.array_split(e, 20)
+    sem = float(np.std([b.mean() for b in blocks], ddof=1) / math.sqrt(len(blocks)))
+    counts = md.get("rdf").reshape(3, bins)
+    samples = md.get("state")[4]
+    r = (np.arange(bins) + 0.5) * (rmax / bins)
+    shell = 4.0 / 3.0 * math.pi * ((r + rmax / bins / 2) ** 3 - (r - rmax / bins / 2) ** 3)
+    n_a = int(np.sum(q < 0))
+    g_ca = counts[0] / (samples * n_cat * n_a / L ** 3 * shell)
+    k = int(np.argmax(g_ca))
+    T = 2 * th[:, 0] / (3 * N - 3)
+    name = {1: "monovalent", 2: "divalent", 3: "trivalent"}[valence]
+    md.close()
+    h.close()
+    return {"system": f"Sec. 4.1 {name} electrolyte, N = {N}, L = {L}, l_B = 3.5, dt = 0.01, "
+                      f"tdamp = {tdamp}, {steps_eq} + {steps_prod} steps",
+            "steps_per_s": (steps_eq + steps_prod) / (t_eq + t_prod),
+            "energy_per_ion_mean": float(e.mean()), "energy_per_ion_var": float(e.var()),
+            "energy_per_ion_sem": sem, "paper_hsma3d_mean_var": PAPER_E1[name],
+            "temperature_mean": float(T.mean()),
+            "kinetic_per_ion_var": float(np.var(th[:, 0] / N)),
+            "potential_per_ion_var": float(np.var((th[:, 1] + th[:, 2]) / N)),
+            "kinetic_potential_cov": float(np.cov(th[:, 0] / N, (th[:, 1] + th[:, 2]) / N)[0, 1]),
+            "canonical_kinetic_per_ion_var": 0.5 * (3 * N - 3) / N ** 2,
+            "coulomb_per_ion_mean": float(th[:, 2].mean() / N), "lj_per_ion_mean": float(th[:, 1].mean() / N),
+            "g_ca_peak": [float(r[k]), float(g_ca[k])], "rdf_samples": int(samples),
+            "g_ca": [round(float(v), 4) for v in g_ca]}
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -436,6 +500,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other-cases", action="store_true")
     ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
+    ap.add_argument("--md", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="run the Sec. 4.1 electrolyte MD validation with this valence and exit")
+    ap.add_argument("--md-steps", type=int, default=200000, help="production steps of --md")
+    ap.add_argument("--md-tdamp", type=float, default=0.01, help="thermostat damping time of --md")
     ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
                     help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
@@ -457,6 +525,14 @@ def main():
     if dist:
         dist.barrier()
     import paper_2104_05260_gb300 as P
+
+    if args.md:
+        if rank == 0:
+            print(json.dumps({"md_validation": md_e1(P, valence=args.md, steps_prod=args.md_steps,
+                                                     tdamp=args.md_tdamp)}), flush=True)
+        if dist:
+            dist.barrier()
+        return
 
     x, q = workloads.electrolyte(c, seed=c.seed + 1000 * rank)
     N = c.N
@@ -619,6 +695,7 @@ def main():
                 option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), grad_rows=1)]
         line["other_cases"] = other_cases(P, torch, dev, stream)
         line["paper_like"] = paper_like(P, torch, dev, stream)
+        line["md_e1_short"] = md_e1(P, valence=1, steps_eq=500, steps_prod=2000, rdf_every=100)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -280,6 +280,64 @@ int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces);
  */
 int hsma_server_step(hsma_t server);
 
+/*
+ * MD loop: the validation workload of Sec. 4.1 on the device.  A primitive
+ * electrolyte of soft spheres (the shifted-truncated LJ repulsion cut at
+ * 2^(1/6) sigma, energy 4 eps [(sigma/r)^12 - (sigma/r)^6] + eps) plus the
+ * electrostatics of an HSMA3D handle, integrated by velocity Verlet, in the
+ * canonical ensemble with a Nose-Hoover thermostat (one thermostat, symmetric
+ * Trotter splitting, Q = g kT tdamp^2, g = 3N - 3) or in NVE (tdamp <= 0).
+ * Each step runs as one CUDA graph replay on the handle's stream: kick and
+ * drift, cell list and LJ forces, the full HSMA evaluation, kick,
+ * thermostat, one thermo row.  Nothing returns to the host between steps.
+ * The paper runs this loop inside LAMMPS; here it is part of the library.
+ */
+typedef struct hsma_md* hsma_md_t;
+
+/*
+ * hsma_md_create -- start an MD loop around the 3D handle h (its box,
+ * p, M, options and coulomb_prefactor, which is l_B kT in reduced units).
+ * x, v: N*3 positions and velocities; q: N charges (host or device).  Copies
+ * them, wraps x into the box, computes the forces and takes the first
+ * thermostat half step.  h must stay alive and must not be used for another
+ * N or have its options changed while the loop exists.
+ * Errors: HSMA_ERR_ARG (dims != 3, N < 2, a box side under 3 x 2^(1/6) sigma,
+ * bad parameters), HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_NOMEM, HSMA_ERR_CUDA.
+ */
+int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, int64_t N,
+                   double mass, double dt, double kT, double tdamp, double lj_sigma,
+                   double lj_eps, hsma_md_t* out);
+
+/*
+ * hsma_md_set_option -- "rdf_every" (accumulate the RDF pair counts every
+ * k-th step, 0 = never), "rdf_bins" (200), "rdf_rmax" (5.0, at most L/2)
+ * (changing either clears the counts), "cell_capacity" (particles per LJ
+ * cell, 8; a run that overflows it fails with HSMA_ERR_ARG).
+ */
+int hsma_md_set_option(hsma_md_t md, const char* key, double value);
+
+/*
+ * hsma_md_run -- advance `steps` steps and wait for them.  thermo (NULL or
+ * steps*6 doubles, host or device) receives per step: kinetic energy, LJ
+ * energy, Coulomb energy, xi, eta, and the conserved extended energy
+ * K + U + Q xi^2/2 + g kT eta (K + U in NVE).
+ */
+int hsma_md_run(hsma_md_t md, int64_t steps, double* thermo);
+
+/*
+ * hsma_md_get -- copy state to the host: "x" (N*3, wrapped), "x_unwrapped",
+ * "v", "forces" (LJ + Coulomb at the current positions), "rdf" (3*rdf_bins
+ * pair counts: cation-anion, cation-cation, anion-anion), "state" (xi, eta,
+ * last K, last U, RDF samples, velocity scale).  n is the capacity of out.
+ */
+int hsma_md_get(hsma_md_t md, const char* name, double* out, int64_t n);
+
+/* hsma_md_last_error -- message of the last failure on this MD loop. */
+const char* hsma_md_last_error(hsma_md_t md);
+
+/* hsma_md_destroy -- free the loop (not the electrostatics handle). */
+void hsma_md_destroy(hsma_md_t md);
+
 #ifdef __cplusplus
 }
 #endif

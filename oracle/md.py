@@ -79,8 +79,21 @@ class State:
         self.U = None
 
     def wrap(self):
+        """x into [0, L) per component, the image counters keeping x + img L.
+        The quotient x / L can round across an integer; the two fix-ups put
+        such a coordinate back inside."""
         k = np.floor(self.x / self.box)
         self.x -= k * self.box
+        L = np.broadcast_to(self.box, self.x.shape)
+        hi = self.x >= L
+        self.x[hi] -= L[hi]
+        k[hi] += 1
+        lo = self.x < 0.0
+        self.x[lo] += L[lo]
+        k[lo] -= 1
+        top = lo & (self.x >= L)
+        self.x[top] = 0.0
+        k[top] += 1
         self.img += k.astype(np.int64)
 
     def kinetic(self):

@@ -44,6 +44,12 @@ SIGNATURES = {
     "hsma_geometry_array": (_I, [ctypes.POINTER(_D), _I, _I, _I, _D, _D, _D, _I, _I, _D,
                                  ctypes.c_char_p, _P, _L]),
     "hsma_pair_sum_static": (_I, [_P, _L, _P, _L, _P, _I, _P]),
+    "hsma_md_create": (_I, [_P, _P, _P, _P, _L, _D, _D, _D, _D, _D, _D, ctypes.POINTER(_P)]),
+    "hsma_md_set_option": (_I, [_P, ctypes.c_char_p, _D]),
+    "hsma_md_run": (_I, [_P, _L, _P]),
+    "hsma_md_get": (_I, [_P, ctypes.c_char_p, _P, _L]),
+    "hsma_md_last_error": (ctypes.c_char_p, [_P]),
+    "hsma_md_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -255,6 +261,87 @@ class HSMA:
         if self.h is not None:
             hsma_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- MD loop
+def _md_check(m, rc):
+    if rc < 0:
+        msg = lib().hsma_md_last_error(m)
+        raise HSMAError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def hsma_md_create(h, x, v, q, mass=1.0, dt=0.01, kT=1.0, tdamp=0.0, lj_sigma=1.0, lj_eps=1.0):
+    x, v, q = _as_input(x), _as_input(v), _as_input(q)
+    N = q.shape[0] if _is_torch(q) else q.size
+    out = ctypes.c_void_p()
+    rc = lib().hsma_md_create(h, _ptr(x, 3 * N), _ptr(v, 3 * N), _ptr(q, N), int(N), float(mass), float(dt),
+                              float(kT), float(tdamp), float(lj_sigma), float(lj_eps), ctypes.byref(out))
+    if rc != HSMA_OK:
+        msg = lib().hsma_last_error(h)
+        raise HSMAError(rc, "hsma_md_create failed" + (": " + msg.decode() if msg else ""))
+    return out
+
+
+def hsma_md_set_option(m, key, value):
+    return _md_check(m, lib().hsma_md_set_option(m, key.encode(), float(value)))
+
+
+def hsma_md_run(m, steps, thermo=None):
+    """Advance steps; thermo (steps x 6, float64, host or CUDA) or None."""
+    p = _ptr(thermo, 6 * steps) if thermo is not None else None
+    return _md_check(m, lib().hsma_md_run(m, int(steps), p))
+
+
+def hsma_md_get(m, name, n):
+    out = np.empty(int(n), dtype=np.float64)
+    _md_check(m, lib().hsma_md_get(m, name.encode(), ctypes.c_void_p(out.ctypes.data), int(n)))
+    return out
+
+
+def hsma_md_destroy(m):
+    lib().hsma_md_destroy(m)
+
+
+class MD:
+    """The MD loop of the validation workload (include/hsma.h, hsma_md_*)
+    around an HSMA handle."""
+
+    def __init__(self, hsma, x, v, q, **kw):
+        self.hsma = hsma
+        self.N = len(q)
+        self.m = hsma_md_create(hsma.h, x, v, q, **kw)
+
+    def set_option(self, key, value):
+        hsma_md_set_option(self.m, key, value)
+        if key == "rdf_bins":
+            self.rdf_bins = int(value)
+
+    def run(self, steps):
+        t = np.empty((int(steps), 6))
+        hsma_md_run(self.m, steps, t if steps > 0 else None)
+        return t
+
+    def get(self, name):
+        n = {"state": 6}.get(name)
+        if name == "rdf":
+            n = int(3 * self._rdf_bins())
+        return hsma_md_get(self.m, name, n if n else 3 * self.N).reshape(
+            (-1, 3) if name in ("x", "v", "x_unwrapped", "forces") else (-1,))
+
+    def _rdf_bins(self):
+        return getattr(self, "rdf_bins", 200)
+
+    def close(self):
+        if self.m is not None:
+            hsma_md_destroy(self.m)
+            self.m = None
 
     def __del__(self):
         try:

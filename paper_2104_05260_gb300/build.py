@@ -15,9 +15,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsma.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["pair.cu", "kernels.cu", "noalloc.cu"]
-CPP = ["geometry.cpp", "api.cpp", "serve.cpp"]
-HEADERS = ["geometry.hpp", "internal.hpp", "api_internal.hpp"]
+CU = ["pair.cu", "kernels.cu", "noalloc.cu", "md.cu"]
+CPP = ["geometry.cpp", "api.cpp", "serve.cpp", "md.cpp"]
+HEADERS = ["geometry.hpp", "internal.hpp", "api_internal.hpp", "md_internal.hpp"]
 
 
 def _nvcc():

@@ -1,0 +1,126 @@
+"""GPU MD loop (hsma_md_*, the validation workload of Sec. 4.1) against the
+oracle's MD loop (oracle/md.py) driven by the oracle's HSMA, from the same
+state: positions, velocities and thermo rows after a few steps of velocity
+Verlet with the Nose-Hoover thermostat, FP64 electrostatics.  Also bitwise
+reproducibility, NVE energy conservation and the RDF pair counts."""
+import numpy as np
+import pytest
+
+from oracle import hsma as O
+from oracle import md as OM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def system(n_side=4, L=6.0, seed=1, kT=1.0):
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) + 0.5) * (L / n_side)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = x + rng.uniform(-0.15, 0.15, x.shape)
+    n = len(x)
+    q = np.where(rng.permutation(n) % 2 == 0, 1.0, -1.0)
+    if n % 2:
+        q[np.nonzero(q > 0)[0][0]] = 0.0          # neutral with an odd count
+    v = OM.maxwell_velocities(n, kT, 1.0, rng)
+    return x, v, q, [L, L, L]
+
+
+def oracle_run(x, v, q, box, steps, dt, tdamp, lb, p, M):
+    st = O.make_setup(box, 3, p, M, prefactor=lb)
+
+    def coul(xx, qq):
+        out = O.evaluate(st, xx, qq)
+        return out["energy"], out["forces"]
+    it = OM.Integrator(coul, dt=dt, kT=1.0, tdamp=tdamp)
+    s = OM.State(x, v, q, box)
+    rows = []
+    for _ in range(steps):
+        it.step(s)
+        rows.append([s.kinetic(), s.U_lj, s.U_c, s.xi, s.eta, it.extended_energy(s)])
+    return s, np.array(rows)
+
+
+@pytest.mark.parametrize("tdamp", [0.05, 0.0])
+def test_md_matches_oracle(P, tdamp):
+    x, v, q, box = system()
+    lb, p, M, dt, steps = 3.5, 6, 400, 0.004, 12
+    h = P.HSMA(box, 3, p, M, precision=0, coulomb_prefactor=lb)
+    md = P.MD(h, x, v, q, dt=dt, kT=1.0, tdamp=tdamp)
+    t = md.run(steps)
+    s, ref = oracle_run(x, v, q, box, steps, dt, tdamp if tdamp > 0 else None, lb, p, M)
+    scale = np.abs(ref).max(axis=0) + 1e-300
+    assert np.all(np.abs(t - ref) <= 1e-9 * np.maximum(scale, 1.0)), np.abs(t - ref).max(axis=0)
+    assert np.abs(md.get("x_unwrapped") - s.unwrapped()).max() < 1e-10
+    assert np.abs(md.get("x") - s.x).max() < 1e-10
+    assert np.abs(md.get("v") - s.v).max() < 1e-9
+    md.close()
+    h.close()
+
+
+def test_md_is_bitwise_reproducible_and_conserves_energy(P):
+    x, v, q, box = system(n_side=5, L=8.0, seed=2)
+    h = P.HSMA(box, 3, 6, 400, precision=0, coulomb_prefactor=1.0)
+    rows = []
+    for _ in range(2):
+        md = P.MD(h, x, v, q, dt=0.002, kT=1.0, tdamp=0.0)
+        rows.append(md.run(300))
+        md.close()
+    assert np.array_equal(rows[0], rows[1])
+    H = rows[0][:, 5]
+    # velocity Verlet: bounded energy error; the HSMA forces are not exactly
+    # conservative (a fit per configuration), so allow a small drift
+    assert np.abs(H - H[0]).max() < 2e-3 * (abs(H[0]) + rows[0][:, 0].mean())
+    h.close()
+
+
+def test_md_rdf_counts_match_oracle(P):
+    x, v, q, box = system(n_side=5, L=8.0, seed=3)
+    h = P.HSMA(box, 3, 6, 400, precision=1)
+    md = P.MD(h, x, v, q, dt=0.002, kT=1.0, tdamp=0.1)
+    md.set_option("rdf_bins", 40)
+    md.set_option("rdf_rmax", 4.0)
+    md.set_option("rdf_every", 1)
+    md.run(1)
+    counts = md.get("rdf").reshape(3, 40)
+    xs = md.get("x")
+    cat, an = q > 0, q < 0
+    assert int(md.get("state")[4]) == 1
+    assert np.array_equal(counts[0], OM.rdf_counts(xs, box, cat, an, 4.0, 40))
+    assert np.array_equal(2 * counts[1], OM.rdf_counts(xs, box, cat, cat, 4.0, 40))
+    assert np.array_equal(2 * counts[2], OM.rdf_counts(xs, box, an, an, 4.0, 40))
+    md.close()
+    h.close()
+
+
+def test_md_thermostat_holds_the_temperature_fp32(P):
+    x, v, q, box = system(n_side=6, L=9.0, seed=4, kT=2.0)
+    h = P.HSMA(box, 3, 6, 400, precision=1, coulomb_prefactor=1.0)
+    md = P.MD(h, x, v, q, dt=0.004, kT=1.0, tdamp=0.1)
+    t = md.run(3000)
+    n = len(q)
+    T = 2 * t[1000:, 0] / (3 * n - 3)
+    assert abs(T.mean() - 1.0) < 0.05
+    assert np.abs(t[:, 5] - t[0, 5]).max() < 0.02 * abs(t[0, 5]) + 0.05 * n
+    md.close()
+    h.close()
+
+
+def test_md_rejects_bad_arguments(P):
+    x, v, q, box = system()
+    h = P.HSMA(box, 3, 6, 400)
+    with pytest.raises(P.HSMAError):
+        P.MD(h, x, v, q[:-1] * 0 + 1, dt=0.01)          # sizes / neutrality
+    h2 = P.HSMA([3.0, 3.0, 3.0], 3, 4, 100)
+    with pytest.raises(P.HSMAError):
+        P.MD(h2, x[:8] * 0.5, v[:8], q[:8], dt=0.01)    # box under 3 LJ cells a side
+    h.close()
+    h2.close()
