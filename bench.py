@@ -504,6 +504,7 @@ def main():
                     help="run the Sec. 4.1 electrolyte MD validation with this valence and exit")
     ap.add_argument("--md-steps", type=int, default=200000, help="production steps of --md")
     ap.add_argument("--md-tdamp", type=float, default=0.01, help="thermostat damping time of --md")
+    ap.add_argument("--md-eq", type=int, default=20000, help="equilibration steps of --md")
     ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
                     help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
@@ -528,8 +529,9 @@ def main():
 
     if args.md:
         if rank == 0:
-            print(json.dumps({"md_validation": md_e1(P, valence=args.md, steps_prod=args.md_steps,
-                                                     tdamp=args.md_tdamp)}), flush=True)
+            print(json.dumps({"md_validation": md_e1(P, valence=args.md, steps_eq=args.md_eq,
+                                                     steps_prod=args.md_steps, tdamp=args.md_tdamp)}),
+                  flush=True)
         if dist:
             dist.barrier()
         return

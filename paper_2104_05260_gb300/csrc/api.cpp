@@ -109,7 +109,7 @@ hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
-                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm})
+                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -225,7 +225,8 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
              h->d_blkaq.ensure(nblk * 8) || h->d_forces.ensure(n * 24) || h->d_pot.ensure(n * 8) ||
              h->d_grad.ensure(n * 24) || h->d_blke.ensure(nblk * 8) ||
              h->d_part.ensure((size_t)std::max(h->chunks1, h->part_chunks_min) * 4 * nt * 8) ||
-             h->d_fpart.ensure((size_t)h->chunks2 * 4 * n * 8);
+             h->d_fpart.ensure((size_t)h->chunks2 * 4 * n * 8) || h->d_red1.ensure(4 * nt * 8) ||
+             h->d_red2.ensure(4 * n * 8);
   if (prec == 0)
     bad = bad || h->d_src64.ensure(simg * 32) || h->d_tgt64.ensure(nt * 32);
   else
@@ -310,7 +311,12 @@ PairArgs near_args(hsma_ctx* h, int64_t N) {
 int stage_fit(hsma_ctx* h, int64_t N) {
   const Geometry& g = h->geo;
   const int prec = h->precision;
-  cudaError_t e = launch_fit(g.par.dims, (const double*)h->d_part.p, h->chunks1, h->n_tgt1, (int)N,
+  // the near/check partials summed over chunks once; the fit and the
+  // assembly read the single row set
+  cudaError_t e = launch_reduce_chunks((const double*)h->d_part.p, h->chunks1, h->n_tgt1, h->n_tgt1,
+                                       (double*)h->d_red1.p, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
+  e = launch_fit(g.par.dims, (const double*)h->d_red1.p, 1, h->n_tgt1, (int)N,
                              g.n_check, g.par.grad_rows ? 2 * g.n_mon : 0, geo_P(h), g.nA, g.nv, geo_W(h), g.par.M, geo_Y(h), h->gscale,
                              (double*)h->d_v.p, (double*)h->d_A.p, (double*)h->d_cphi.p,
                              (double*)h->d_cdz.p, (double*)h->d_Q.p,
@@ -340,8 +346,14 @@ PairArgs far_args(hsma_ctx* h, int64_t N) {
 // Stage 5: potentials, forces, energy; scalars back to pinned host memory.
 int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   const int prec = h->precision;
-  cudaError_t e = launch_assemble((const double*)h->d_part.p, h->chunks1, h->n_tgt1,
-                                  (const double*)h->d_fpart.p, h->far_series ? 1 : h->chunks2, (int)N,
+  const bool far_one = h->far_series || h->chunks2 == 1;
+  cudaError_t e = cudaSuccess;
+  if (!far_one)
+    e = launch_reduce_chunks((const double*)h->d_fpart.p, h->chunks2, (int)N, (int)N, (double*)h->d_red2.p,
+                             h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
+  e = launch_assemble((const double*)h->d_red1.p, 1, h->n_tgt1,
+                                  (const double*)(far_one ? h->d_fpart.p : h->d_red2.p), 1, (int)N,
                                   prec ? (const double*)h->d_self.p : nullptr,
                                   (const double*)h->d_q.p, (int)N, h->pref, (DevScalars*)h->d_sc.p,
                                   forces_dev, pot_dev, (double*)h->d_grad.p, (double*)h->d_blke.p,

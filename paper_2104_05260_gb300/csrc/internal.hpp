@@ -90,6 +90,10 @@ int pair_ragged_variant();   // kernel code the ragged launch runs (plan tiles w
 cudaError_t launch_far_series(int precision, const void* tgt, int N, const double* A, const double* norm,
                               int p, double inv_rc, double* out, cudaStream_t s);
 // scale multiplies W and ysurf (a geometry built for the box divided by scale)
+// Sum a pair launch's per-chunk partials (rows 0..n_rows of leading
+// dimension ld) into out[c*ld + r], the layout of a single chunk; fixed order.
+cudaError_t launch_reduce_chunks(const double* part, int n_chunks, int ld, int n_rows, double* out,
+                                 cudaStream_t s);
 // n_grad: check points (2 N_m, monitoring points then wraps) whose gradients
 // also enter v for the gradient-periodicity rows; 0 without them.
 cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N, int n_check,

@@ -438,6 +438,43 @@ cudaError_t launch_far_series(int precision, const void* tgt, int N, const doubl
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ chunk partials
+// Sum the per-chunk FP64 partials of a pair launch, part[(ch*4 + c)*ld + r],
+// into one row set out[c*ld + r] (the layout of a single chunk).  A block
+// takes 32 targets; its 8 lanes per target sum the chunks ch = lane (mod 8)
+// in increasing order, then a fixed tree adds the 8 lane sums, so the result
+// does not depend on the launch.  Reads are coalesced along the targets.
+constexpr int kRedTargets = 32, kRedLanes = 8;
+
+__global__ void __launch_bounds__(kRedTargets * kRedLanes) k_reduce_chunks(const double* __restrict__ part,
+                                                                           int n_chunks, int ld, int n_rows,
+                                                                           double* __restrict__ out) {
+  __shared__ double sh[kRedLanes][4][kRedTargets];
+  const int tx = threadIdx.x % kRedTargets, ty = threadIdx.x / kRedTargets;
+  const int r = blockIdx.x * kRedTargets + tx;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (r < n_rows)
+    for (int ch = ty; ch < n_chunks; ch += kRedLanes)
+      for (int c = 0; c < 4; ++c) acc[c] += part[((size_t)ch * 4 + c) * ld + r];
+  for (int c = 0; c < 4; ++c) sh[ty][c][tx] = acc[c];
+  __syncthreads();
+  for (int w = kRedLanes / 2; w > 0; w >>= 1) {
+    if (ty < w)
+      for (int c = 0; c < 4; ++c) sh[ty][c][tx] += sh[ty + w][c][tx];
+    __syncthreads();
+  }
+  if (ty == 0 && r < n_rows)
+    for (int c = 0; c < 4; ++c) out[(size_t)c * ld + r] = sh[0][c][tx];
+}
+
+cudaError_t launch_reduce_chunks(const double* part, int n_chunks, int ld, int n_rows, double* out,
+                                 cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  k_reduce_chunks<<<(n_rows + kRedTargets - 1) / kRedTargets, kRedTargets * kRedLanes, 0, s>>>(
+      part, n_chunks, ld, n_rows, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ assembly
 constexpr int kAsmThreads = 256;
 

@@ -217,7 +217,7 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
   const int nb = hsma::md_blocks((int)N);
   if (m->x.ensure(n3 * 8) || m->v.ensure(n3 * 8) || m->img.ensure(n3 * 4) || m->q.ensure((size_t)N * 8) ||
       m->f_lj.ensure(n3 * 8) || m->f_c.ensure(n3 * 8) || m->blk_k.ensure((size_t)nb * 8) ||
-      m->blk_u.ensure((size_t)nb * 8) || m->sc.ensure(sizeof(MdScalars)) ||
+      m->blk_u.ensure((size_t)hsma::md_lj_blocks((int)N) * 8) || m->sc.ensure(sizeof(MdScalars)) ||
       m->cells.ensure((size_t)m->n_cells * (1 + m->cap) * 4) || m->rdf.ensure((size_t)3 * m->rdf_bins * 8) ||
       ensure_thermo(m, 1)) {
     delete m;

@@ -89,54 +89,70 @@ __global__ void __launch_bounds__(kMdThreads) k_md_cell_sort(MdArgs a, int n_cel
   }
 }
 
-// shifted-truncated LJ repulsion: full neighbour sum per particle (no
-// Newton's-third-law sharing), cells visited in a fixed order; per-block
-// energy partials (half of each pair to each partner)
+// shifted-truncated LJ repulsion: one warp per particle, lane k < 27 takes
+// neighbour cell k (fixed order), the periodic shift of that cell applied
+// explicitly (cells are at least r_c wide and at least 3 a side, so the
+// shifted copy is the minimum image); lane sums are added by a fixed
+// butterfly.  Per-block energy partials hold half of each pair's energy.
+constexpr int kLjWarps = kMdThreads / 32;
+
 __global__ void __launch_bounds__(kMdThreads) k_md_lj(MdArgs a) {
   __shared__ double sh[kMdThreads];
-  const int i = blockIdx.x * kMdThreads + threadIdx.x;
-  double u = 0.0;
-  if (i < a.N) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kLjWarps + (threadIdx.x >> 5);
+  double fx = 0.0, fy = 0.0, fz = 0.0, u = 0.0;
+  if (i < a.N && lane < 27) {
     const double xi = a.x[3 * (size_t)i], yi = a.x[3 * (size_t)i + 1], zi = a.x[3 * (size_t)i + 2];
-    const int cx = md_cell_of(xi, a.inv_w[0], a.nc[0]);
-    const int cy = md_cell_of(yi, a.inv_w[1], a.nc[1]);
-    const int cz = md_cell_of(zi, a.inv_w[2], a.nc[2]);
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int z = (cz + dz + a.nc[2]) % a.nc[2];
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int y = (cy + dy + a.nc[1]) % a.nc[1];
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x = (cx + dx + a.nc[0]) % a.nc[0];
-          const int c = (z * a.nc[1] + y) * a.nc[0] + x;
-          const int n = min(a.cell_count[c], a.cap);
-          const int* l = a.cell_list + (size_t)c * a.cap;
-          for (int k = 0; k < n; ++k) {
-            const int j = l[k];
-            if (j == i) continue;
-            double ddx = a.x[3 * (size_t)j] - xi, ddy = a.x[3 * (size_t)j + 1] - yi,
-                   ddz = a.x[3 * (size_t)j + 2] - zi;
-            ddx -= a.L[0] * rint(ddx / a.L[0]);
-            ddy -= a.L[1] * rint(ddy / a.L[1]);
-            ddz -= a.L[2] * rint(ddz / a.L[2]);
-            const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < a.rc2) {
-              const double s2 = a.sigma2 / r2;
-              const double s6 = s2 * s2 * s2;
-              u += 0.5 * (4.0 * a.eps * (s6 * s6 - s6) + a.eps);
-              const double f = 24.0 * a.eps * (2.0 * s6 * s6 - s6) / r2;   // force on i is -f d
-              fx -= f * ddx;
-              fy -= f * ddy;
-              fz -= f * ddz;
-            }
-          }
-        }
+    const int c0[3] = {md_cell_of(xi, a.inv_w[0], a.nc[0]), md_cell_of(yi, a.inv_w[1], a.nc[1]),
+                       md_cell_of(zi, a.inv_w[2], a.nc[2])};
+    const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+    int cc[3];
+    double shift[3];
+    for (int d = 0; d < 3; ++d) {
+      cc[d] = c0[d] + off[d];
+      shift[d] = 0.0;
+      if (cc[d] < 0) {
+        cc[d] += a.nc[d];
+        shift[d] = -a.L[d];
+      } else if (cc[d] >= a.nc[d]) {
+        cc[d] -= a.nc[d];
+        shift[d] = a.L[d];
       }
     }
+    const int c = (cc[2] * a.nc[1] + cc[1]) * a.nc[0] + cc[0];
+    const int n = min(a.cell_count[c], a.cap);
+    const int* l = a.cell_list + (size_t)c * a.cap;
+    for (int k = 0; k < n; ++k) {
+      const int j = l[k];
+      if (j == i) continue;
+      const double dx = (a.x[3 * (size_t)j] + shift[0]) - xi;
+      const double dy = (a.x[3 * (size_t)j + 1] + shift[1]) - yi;
+      const double dz = (a.x[3 * (size_t)j + 2] + shift[2]) - zi;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < a.rc2) {
+        const double s2 = a.sigma2 / r2;
+        const double s6 = s2 * s2 * s2;
+        u += 0.5 * (4.0 * a.eps * (s6 * s6 - s6) + a.eps);
+        const double f = 24.0 * a.eps * (2.0 * s6 * s6 - s6) / r2;   // force on i is -f d
+        fx -= f * dx;
+        fy -= f * dy;
+        fz -= f * dz;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  if (lane == 0 && i < a.N) {
     a.f_lj[3 * (size_t)i] = fx;
     a.f_lj[3 * (size_t)i + 1] = fy;
     a.f_lj[3 * (size_t)i + 2] = fz;
   }
+  // one energy value per warp (lane 0), the rest zero, then the block tree
+  u = (lane == 0) ? u : 0.0;
   u = md_block_sum(u, sh);
   if (threadIdx.x == 0) a.blk_u[blockIdx.x] = u;
 }
@@ -166,10 +182,7 @@ __global__ void __launch_bounds__(kMdThreads) k_md_ke(MdArgs a) {
   if (i < a.N)
     for (int d = 0; d < 3; ++d) k2 += a.v[3 * (size_t)i + d] * a.v[3 * (size_t)i + d];
   k2 = md_block_sum(k2, sh);
-  if (threadIdx.x == 0) {
-    a.blk_k[blockIdx.x] = k2;
-    a.blk_u[blockIdx.x] = 0.0;
-  }
+  if (threadIdx.x == 0) a.blk_k[blockIdx.x] = k2;
 }
 
 // Thermostat half step of length dt/2 on the kinetic energy K (returns the
@@ -187,14 +200,18 @@ __device__ double nh_half(MdScalars* sc, const MdArgs& a, double* K) {
 // One block: totals in fixed order, thermostat, thermo row.
 //  mode 0: end of a step (end-of-step half, record, start-of-next half)
 //  mode 1: start of a run (the start-of-step half only)
-__global__ void __launch_bounds__(kMdThreads) k_md_finish(MdArgs a, int nblk, int mode) {
+__global__ void __launch_bounds__(kMdThreads) k_md_finish(MdArgs a, int nblk_k, int nblk_u, int mode) {
   __shared__ double sh[kMdThreads];
-  const int per = (nblk + kMdThreads - 1) / kMdThreads;
-  const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
   double k2 = 0.0, u = 0.0;
-  for (int b = b0; b < b1; ++b) {
-    k2 += a.blk_k[b];
-    u += a.blk_u[b];
+  {
+    const int per = (nblk_k + kMdThreads - 1) / kMdThreads;
+    const int b0 = threadIdx.x * per, b1 = min(nblk_k, b0 + per);
+    for (int b = b0; b < b1; ++b) k2 += a.blk_k[b];
+  }
+  {
+    const int per = (nblk_u + kMdThreads - 1) / kMdThreads;
+    const int b0 = threadIdx.x * per, b1 = min(nblk_u, b0 + per);
+    for (int b = b0; b < b1; ++b) u += a.blk_u[b];
   }
   k2 = md_block_sum(k2, sh);
   u = md_block_sum(u, sh);
@@ -264,19 +281,19 @@ cudaError_t md_launch_lj(const MdArgs& a, int n_cells, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_md_cell_fill<<<blocks(a.N), kMdThreads, 0, s>>>(a);
   k_md_cell_sort<<<blocks(n_cells), kMdThreads, 0, s>>>(a, n_cells);
-  k_md_lj<<<blocks(a.N), kMdThreads, 0, s>>>(a);
+  k_md_lj<<<(a.N + kLjWarps - 1) / kLjWarps, kMdThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t md_launch_kick_finish(const MdArgs& a, cudaStream_t s) {
   k_md_kick<<<blocks(a.N), kMdThreads, 0, s>>>(a);
-  k_md_finish<<<1, kMdThreads, 0, s>>>(a, blocks(a.N), 0);
+  k_md_finish<<<1, kMdThreads, 0, s>>>(a, blocks(a.N), (a.N + kLjWarps - 1) / kLjWarps, 0);
   return cudaGetLastError();
 }
 
 cudaError_t md_launch_start(const MdArgs& a, cudaStream_t s) {
   k_md_ke<<<blocks(a.N), kMdThreads, 0, s>>>(a);
-  k_md_finish<<<1, kMdThreads, 0, s>>>(a, blocks(a.N), 1);
+  k_md_finish<<<1, kMdThreads, 0, s>>>(a, blocks(a.N), 0, 1);
   return cudaGetLastError();
 }
 
@@ -287,5 +304,6 @@ cudaError_t md_launch_rdf(const MdArgs& a, cudaStream_t s) {
 }
 
 int md_blocks(int N) { return blocks(N); }
+int md_lj_blocks(int N) { return (N + kLjWarps - 1) / kLjWarps; }
 
 }  // namespace hsma

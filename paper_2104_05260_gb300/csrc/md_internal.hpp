@@ -31,7 +31,7 @@ struct MdArgs {
   const double* f_c;    // N*3, Coulomb forces (electrostatics' output)
   const double* coul_energy;   // device scalar (electrostatics' energy) or null
   double* blk_k;        // per-block sums of v^2
-  double* blk_u;        // per-block LJ energy
+  double* blk_u;        // per-block LJ energy (md_lj_blocks entries)
   MdScalars* sc;
   double* thermo;       // thermo_cap rows of MD_THERMO_COLS
   long long thermo_cap;
@@ -52,7 +52,8 @@ struct MdArgs {
   double rdf_rmax;
 };
 
-int md_blocks(int N);
+int md_blocks(int N);      // blocks of the per-particle kernels (blk_k entries)
+int md_lj_blocks(int N);   // blocks of the LJ kernel (blk_u entries)
 cudaError_t md_launch_kick_drift(const MdArgs& a, cudaStream_t s);
 cudaError_t md_launch_lj(const MdArgs& a, int n_cells, cudaStream_t s);
 cudaError_t md_launch_kick_finish(const MdArgs& a, cudaStream_t s);
