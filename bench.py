@@ -337,6 +337,41 @@ def far_series_compare(P, torch, stream, c, xd, qd, fd, h_surface, n=10):
     return rec
 
 
+def pair_sources_sha1():
+    """Hash of the pair kernels' sources: pair.cu and the two structs of
+    internal.hpp they read (PairArgs, DevScalars).  A stored DRAM-traffic
+    figure is used only while this matches the one it was captured with."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2104_05260_gb300", "csrc")
+    hdr = open(os.path.join(csrc, "internal.hpp")).read()
+    blocks = [m.group(0) for m in re.finditer(r"struct (PairArgs|DevScalars) \{.*?\n\};", hdr, re.S)]
+    src = open(os.path.join(csrc, "pair.cu"), "rb").read() + "".join(blocks).encode()
+    return hashlib.sha1(src).hexdigest()
+
+
+def record_traffic(csv_path, kernel, workload, chunks, command):
+    """Write profiles/traffic.json from an ncu CSV (--csv --log-file) holding
+    dram__bytes_read.sum and dram__bytes_write.sum of one launch."""
+    import csv
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 10]
+    h = rows[0]
+    vals = {}
+    for r in rows[1:]:
+        name, unit, v = r[h.index("Metric Name")], r[h.index("Metric Unit")], r[h.index("Metric Value")]
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit)
+        if scale is not None:
+            vals[name] = float(v.replace(",", "")) * scale
+    rd, wr = vals["dram__bytes_read.sum"], vals["dram__bytes_write.sum"]
+    rec = {"kernel": kernel, "workload": workload, "pair_sources_sha1": pair_sources_sha1(), "chunks": chunks,
+           "bytes_per_launch": int(rd + wr), "read_bytes": int(rd), "write_bytes": int(wr),
+           "command": command,
+           "hash_covers": "paper_2104_05260_gb300/csrc/pair.cu and the PairArgs and DevScalars structs of "
+                          "internal.hpp; any change there nulls the figure in bench.py"}
+    json.dump(rec, open(os.path.join(ROOT, "profiles", "traffic.json"), "w"), indent=1)
+    return rec
+
+
 def option_variant(P, torch, stream, c, xd, qd, fd, e_default, n=3, **opt):
     """The main workload with one option changed: evaluations/s, N_s and the
     energy / force difference from the default configuration (fd, e_default)."""
@@ -438,6 +473,12 @@ def md_e1(P, valence=1, steps_eq=20000, steps_prod=200000, rdf_every=100, seed=1
     k = int(np.argmax(g_ca))
     T = 2 * th[:, 0] / (3 * N - 3)
     name = {1: "monovalent", 2: "divalent", 3: "trivalent"}[valence]
+    # mean-spherical approximation of the primitive model with equal diameters
+    # sigma = 1: 2 Gamma (1 + Gamma) = kappa, U / N = -l_B Gamma / (1 + Gamma) <z^2>
+    z2 = float(np.mean(q * q))
+    kappa = math.sqrt(4.0 * math.pi * 3.5 * z2 * N / L ** 3)
+    gam = (-1.0 + math.sqrt(1.0 + 2.0 * kappa)) / 2.0
+    msa = -3.5 * gam / (1.0 + gam) * z2
     md.close()
     h.close()
     return {"system": f"Sec. 4.1 {name} electrolyte, N = {N}, L = {L}, l_B = 3.5, dt = 0.01, "
@@ -450,7 +491,8 @@ def md_e1(P, valence=1, steps_eq=20000, steps_prod=200000, rdf_every=100, seed=1
             "potential_per_ion_var": float(np.var((th[:, 1] + th[:, 2]) / N)),
             "kinetic_potential_cov": float(np.cov(th[:, 0] / N, (th[:, 1] + th[:, 2]) / N)[0, 1]),
             "canonical_kinetic_per_ion_var": 0.5 * (3 * N - 3) / N ** 2,
-            "coulomb_per_ion_mean": float(th[:, 2].mean() / N), "lj_per_ion_mean": float(th[:, 1].mean() / N),
+            "coulomb_per_ion_mean": float(th[:, 2].mean() / N), "coulomb_per_ion_msa": msa,
+            "lj_per_ion_mean": float(th[:, 1].mean() / N),
             "g_ca_peak": [float(r[k]), float(g_ca[k])], "rdf_samples": int(samples),
             "g_ca": [round(float(v), 4) for v in g_ca]}
 
@@ -500,6 +542,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other-cases", action="store_true")
     ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
+    ap.add_argument("--record-traffic", default=None,
+                    help="write profiles/traffic.json from this ncu CSV (near-field launch) and exit")
     ap.add_argument("--md", type=int, default=0, choices=[0, 1, 2, 3],
                     help="run the Sec. 4.1 electrolyte MD validation with this valence and exit")
     ap.add_argument("--md-steps", type=int, default=200000, help="production steps of --md")
@@ -509,6 +553,14 @@ def main():
                     help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.record_traffic:
+        print(json.dumps(record_traffic(
+            args.record_traffic, "k_pair_f32x2s<2> near field + check points", "hsma3d_n100000_rho0.1_p8_M2000",
+            46, "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                "--clock-control none -k regex:k_pair -s 23 -c 1 --csv --log-file near_traffic.csv "
+                "python bench.py --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --no-serve "
+                "--no-other-cases")))
+        return
     c = workloads.case(args.case)
     dist, rank, ws, local = dist_init(args)
     if args.impl == "reference":
@@ -647,11 +699,8 @@ def main():
     tr = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr):
         try:
-            import hashlib
             rec = json.load(open(tr))
-            csrc = os.path.join(ROOT, "paper_2104_05260_gb300", "csrc")
-            src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("pair.cu", "internal.hpp"))
-            if (rec.get("pair_sources_sha1") == hashlib.sha1(src).hexdigest()
+            if (rec.get("pair_sources_sha1") == pair_sources_sha1()
                     and rec.get("chunks") == plan["chunks"] and rec.get("kernel", "").startswith(plan["kernel"])):
                 roof["traffic"] = rec.get("bytes_per_launch")
         except Exception:

@@ -470,8 +470,12 @@ static int tune_near(hsma_ctx* h, int64_t N) {
     a.n_tiles = (h->n_tgt1 + tile - 1) / tile;
     a.n_chunks = c.chunks;
     const int grid = (int)std::min<long>((long)a.n_tiles * a.n_chunks, pair_slots(prec, c.tpt));
+    // timed with the chunk reduction that consumes its partials: more
+    // chunks fill the GPU at small N but cost partial traffic
     cudaEventRecord(h->ev[0], s);
     cudaError_t e = launch_pair(prec, prec ? c.tpt : 1, a, grid, s);
+    if (e == cudaSuccess)
+      e = launch_reduce_chunks(a.part, a.n_chunks, a.ld, h->n_tgt1, (double*)h->d_red1.p, s);
     cudaEventRecord(h->ev[1], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(h->ev[1]);
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
