@@ -302,6 +302,24 @@ def other_cases(P, torch, dev, stream):
             h.close()
         if 0 in energies:
             rec["fp32_vs_fp64_rel_energy"] = abs(energies[1] - energies[0]) / abs(energies[0])
+        if c.dims == 3 and c.N >= 100000:
+            # the tree evaluation of the near field (option near_tree) beside it
+            h = P.HSMA(c.box, c.dims, c.p, c.M, precision=1, near_tree=1)
+            P.hsma_set_stream(h.h, stream.cuda_stream)
+            e = np.zeros(1)
+            ft = torch.empty_like(fd)
+            P.hsma_eval_into(h.h, xd, qd, c.N, e, ft)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(max(3, n32)):
+                P.hsma_eval_into(h.h, xd, qd, c.N, e, ft)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rec["tree_fp32_evals_per_s"] = 1e3 * max(3, n32) / a.elapsed_time(b)
+            rec["tree_levels"] = int(P.hsma_get_info(h.h, "tree_levels"))
+            rec["tree_vs_dense_rel_energy"] = abs(float(e[0]) - energies[1]) / abs(energies[1])
+            h.close()
         out[c.name] = rec
     return out
 
@@ -743,7 +761,9 @@ def main():
             torch.cuda.synchronize()
             line["option_variants"] = [
                 option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), sphere_mask=0),
-                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), grad_rows=1)]
+                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), grad_rows=1),
+                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), n=10, near_tree=1),
+                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), n=10, near_tree=1, far_field=1)]
         line["other_cases"] = other_cases(P, torch, dev, stream)
         line["paper_like"] = paper_like(P, torch, dev, stream)
         line["md_e1_short"] = md_e1(P, valence=1, steps_eq=500, steps_prod=2000, rdf_every=100)

@@ -120,6 +120,18 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       too, weighted by grad_weight * R_c.  Not in the
  *                       paper's fit; 0 (default) = the paper's rows only.
  *   "grad_weight"       weight of those rows in units of R_c (> 0; 0.1).
+ *   "near_tree"         1 = evaluate the near-field and check-point sums by a
+ *                       tree (the paper's O(N) path, which it runs through an
+ *                       FMM library): images binned into a uniform octree over
+ *                       [-R_s, R_s]^3, multipole expansions of order
+ *                       tree_order per cell, FMM interaction lists evaluated
+ *                       at each target, direct FP32 pairs with the 27
+ *                       neighbouring leaves.  An approximation of the sums:
+ *                       at tree_order 10, force RMS about 2e-6 and energy
+ *                       4e-6 relative to the direct sums.  Needs precision 1;
+ *                       0 (default) = direct sums.
+ *   "tree_order"        expansion order of the tree: 4, 6, 8, 10 (default),
+ *                       12 or 14.
  *   "far_field"         0 (default) = the far field from the M surface charges
  *                       (Eq. 8, the paper's choice); 1 = the fitted series of
  *                       Eq. 5 itself, sum over n >= 1 of A_nm (r/R_c)^n Y_nm,
@@ -165,7 +177,8 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * Keys: "Rc", "Rs", "n_shifts", "n_check", "rank", "Ns" (images in B at the
  * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
- * "far_chunks", "far_field", "grid", "slots", "kernel", "tile_targets".
+ * "far_chunks", "far_field", "tree_levels" (leaf level L of the tree, 0 when
+ * off), "grid", "slots", "kernel", "tile_targets".
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);

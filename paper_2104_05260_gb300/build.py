@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsma.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["pair.cu", "kernels.cu", "noalloc.cu", "md.cu"]
+CU = ["pair.cu", "kernels.cu", "noalloc.cu", "md.cu", "tree.cu"]
 CPP = ["geometry.cpp", "api.cpp", "serve.cpp", "md.cpp"]
 HEADERS = ["geometry.hpp", "internal.hpp", "api_internal.hpp", "md_internal.hpp"]
 

@@ -109,7 +109,9 @@ hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
-                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2})
+                    &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2, &d_tkey_s,
+                    &d_tcnt_s, &d_tstart_s, &d_tcur_s, &d_tord_s, &d_tkey_t, &d_tcnt_t, &d_tstart_t, &d_tcur_t,
+                    &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -195,6 +197,88 @@ void drop_graph(hsma_ctx* h) {
   h->graph_N = -1;
 }
 
+// Tree plan: leaf level from the expected image count (about 32 images per
+// occupied leaf; the sphere fills 52 % of the root cube), buffers, the
+// normalisation tables of the expansion.
+static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
+  const Geometry& g = h->geo;
+  const int P = h->tree_order;
+  const double per_leaf = h->ns_est / (32.0 * 0.52);
+  int L = (int)std::floor(std::log(std::max(per_leaf, 1.0)) / std::log(8.0));
+  L = std::max(2, std::min(6, L));
+  const size_t nleaf = (size_t)1 << (3 * L);
+  const int nc = (P + 1) * (P + 1);
+  TreeArgs& t = h->tree_args;
+  t.L = L;
+  t.P = P;
+  t.Rs = (float)g.Rs;
+  t.D = (float)(2.0 * g.Rs);
+  t.inv_wL = (float)((double)(1 << L) / (2.0 * g.Rs));
+  size_t off = 0;
+  for (int l = 0; l < 8; ++l) {
+    t.moff[l] = (int)off;
+    if (l >= 2 && l <= L) off += ((size_t)1 << (3 * l)) * nc;
+  }
+  std::vector<float> norm(nc), fac(nc);
+  for (int nn = 0; nn <= P; ++nn)
+    for (int m = 0; m <= nn; ++m) {
+      double ratio = 1.0;
+      for (int k = nn - m + 1; k <= nn + m; ++k) ratio /= k;
+      double c = std::sqrt((2 * nn + 1) / (4.0 * 3.14159265358979323846) * ratio);
+      if (m > 0) {
+        c *= std::sqrt(2.0);
+        for (int k = 2 * m - 1; k > 1; k -= 2) c *= k;
+      }
+      norm[nn * (P + 1) + m] = (float)c;
+      const double f = 4.0 * 3.14159265358979323846 / (2 * nn + 1) * c * c;   // the evaluation has no norm
+      fac[nn * nn + nn + m] = (float)f;
+      fac[nn * nn + nn - m] = (float)f;
+    }
+  const bool bad = h->d_tkey_s.ensure(simg * 4) || h->d_tord_s.ensure(simg * 4) || h->d_tsrc.ensure(simg * 16) ||
+                   h->d_tcnt_s.ensure(nleaf * 4) || h->d_tcur_s.ensure(nleaf * 4) ||
+                   h->d_tstart_s.ensure((nleaf + 1) * 4) || h->d_tkey_t.ensure(nt * 4) ||
+                   h->d_tord_t.ensure(nt * 4) || h->d_tcnt_t.ensure(nleaf * 4) || h->d_tcur_t.ensure(nleaf * 4) ||
+                   h->d_tstart_t.ensure((nleaf + 1) * 4) || h->d_tpart.ensure(nleaf * nc * 8) ||
+                   h->d_tM.ensure(off * 4) || h->d_tnorm.ensure((size_t)nc * 4) || h->d_tfac.ensure((size_t)nc * 4);
+  if (bad) return fail(h, HSMA_ERR_NOMEM, "tree buffers");
+  cudaError_t e = cudaMemcpy(h->d_tnorm.p, norm.data(), (size_t)nc * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tfac.p, fac.data(), (size_t)nc * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tree tables");
+  t.norm = (const float*)h->d_tnorm.p;
+  t.fac = (const float*)h->d_tfac.p;
+  h->tree_L = L;
+  (void)n;
+  return HSMA_OK;
+}
+
+static int launch_near_tree(hsma_ctx* h, int64_t N) {
+  TreeLaunch T;
+  T.t = h->tree_args;
+  T.src = (const float4*)h->d_src32.p;
+  T.sc = (const DevScalars*)h->d_sc.p;
+  T.tgt = (const float4*)h->d_tgt32.p;
+  T.n_tgt = h->n_tgt1;
+  T.n_ions = (int)N;
+  T.src_key = (int*)h->d_tkey_s.p;
+  T.src_count = (int*)h->d_tcnt_s.p;
+  T.src_start = (int*)h->d_tstart_s.p;
+  T.src_cursor = (int*)h->d_tcur_s.p;
+  T.src_order = (int*)h->d_tord_s.p;
+  T.tgt_key = (int*)h->d_tkey_t.p;
+  T.tgt_count = (int*)h->d_tcnt_t.p;
+  T.tgt_start = (int*)h->d_tstart_t.p;
+  T.tgt_cursor = (int*)h->d_tcur_t.p;
+  T.tgt_order = (int*)h->d_tord_t.p;
+  T.src_sorted = (float4*)h->d_tsrc.p;
+  T.part = (double*)h->d_tpart.p;
+  T.M = (float*)h->d_tM.p;
+  T.out = (double*)h->d_red1.p;
+  T.ld = h->n_tgt1;
+  cudaError_t e = launch_tree(T, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tree launch");
+  return HSMA_OK;
+}
+
 int mask_words(const Geometry& g) { return std::max<int>(1, ((int)g.shifts.size() - 1 + 31) / 32); }
 
 // Launch plan and buffers for N particles.
@@ -233,6 +317,11 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
     bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16) ||
           h->d_ioff.ensure(n * 4) || h->d_self.ensure(n * 32);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
+  if (h->near_tree) {
+    if (prec == 0) return fail(h, HSMA_ERR_ARG, "near_tree needs precision 1 (FP32 pair arithmetic)");
+    int rc = plan_tree(h, n, nt, simg);
+    if (rc) return rc;
+  }
   h->plan_N = N;
   drop_graph(h);
   return HSMA_OK;
@@ -313,8 +402,10 @@ int stage_fit(hsma_ctx* h, int64_t N) {
   const int prec = h->precision;
   // the near/check partials summed over chunks once; the fit and the
   // assembly read the single row set
-  cudaError_t e = launch_reduce_chunks((const double*)h->d_part.p, h->chunks1, h->n_tgt1, h->n_tgt1,
-                                       (double*)h->d_red1.p, h->stream);
+  cudaError_t e = cudaSuccess;
+  if (!h->near_tree)   // the tree writes its single row set directly
+    e = launch_reduce_chunks((const double*)h->d_part.p, h->chunks1, h->n_tgt1, h->n_tgt1,
+                             (double*)h->d_red1.p, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
   e = launch_fit(g.par.dims, (const double*)h->d_red1.p, 1, h->n_tgt1, (int)N,
                              g.n_check, g.par.grad_rows ? 2 * g.n_mon : 0, geo_P(h), g.nA, g.nv, geo_W(h), g.par.M, geo_Y(h), h->gscale,
@@ -354,7 +445,7 @@ int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) 
   if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
   e = launch_assemble((const double*)h->d_red1.p, 1, h->n_tgt1,
                                   (const double*)(far_one ? h->d_fpart.p : h->d_red2.p), 1, (int)N,
-                                  prec ? (const double*)h->d_self.p : nullptr,
+                                  (prec && !h->near_tree) ? (const double*)h->d_self.p : nullptr,
                                   (const double*)h->d_q.p, (int)N, h->pref, (DevScalars*)h->d_sc.p,
                                   forces_dev, pot_dev, (double*)h->d_grad.p, (double*)h->d_blke.p,
                                   h->stream);
@@ -374,8 +465,14 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   int rc = stage_prep(h, N);
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[1], s);
-  cudaError_t e = launch_pair(prec, tpt, near_args(h, N), h->grid1, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
+  cudaError_t e = cudaSuccess;
+  if (h->near_tree) {
+    rc = launch_near_tree(h, N);
+    if (rc) return rc;
+  } else {
+    e = launch_pair(prec, tpt, near_args(h, N), h->grid1, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "near/check launch");
+  }
   if (tm) cudaEventRecord(h->ev[2], s);
   rc = stage_fit(h, N);
   if (rc) return rc;
@@ -509,7 +606,7 @@ static int eval_impl(hsma_ctx* h, const double* x, const double* q, int64_t N, d
   cudaError_t e = cudaMemcpyAsync(h->d_x.p, x, (size_t)N * 24, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q.p, q, (size_t)N * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
-  if (h->autotune && h->chunks_opt == 0 && h->tuned_N != N) {
+  if (h->autotune && h->chunks_opt == 0 && h->tuned_N != N && !h->near_tree) {
     rc = tune_near(h, N);
     if (rc) return rc;
   }
@@ -633,6 +730,15 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     if (!(v > 0) || !std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "grad_weight must be > 0");
     h->gp.grad_weight = v;
     h->geo_dirty = true;
+  } else if (k == "near_tree") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "near_tree must be 0 or 1");
+    h->near_tree = (int)v;
+    h->plan_N = -1;
+  } else if (k == "tree_order") {
+    if (!(v >= 4) || v > tree_max_order() || std::fmod(v, 2.0) != 0.0)
+      return fail(h, HSMA_ERR_ARG, "tree_order must be one of 4, 6, 8, 10, 12, 14");
+    h->tree_order = (int)v;
+    h->plan_N = -1;
   } else if (k == "far_field") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "far_field must be 0 (surface charges) or 1 (series)");
     h->far_series = (int)v;
@@ -712,6 +818,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "kernel") *value = h->precision ? h->tpt : 0;
   else if (k == "far_chunks") *value = h->far_series ? 1 : h->chunks2;
   else if (k == "far_field") *value = h->far_series;
+  else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;
   else if (k == "tile_targets") *value = pair_tile_targets(h->precision, h->precision ? h->tpt : 1);

@@ -69,6 +69,13 @@ struct hsma_ctx {
   // graph_N particles under the current plan and options
   int use_graphs = 1;
   int far_series = 0;  // far field: 0 surface charges (Eq. 8), 1 the fitted series (Eq. 5)
+  // tree evaluation of the near-field and check-point sums (tree.cu)
+  int near_tree = 0;
+  int tree_order = 10;
+  int tree_L = 0;
+  hsma::DevBuf d_tkey_s, d_tcnt_s, d_tstart_s, d_tcur_s, d_tord_s, d_tkey_t, d_tcnt_t, d_tstart_t, d_tcur_t,
+      d_tord_t, d_tsrc, d_tpart, d_tM, d_tnorm, d_tfac;
+  hsma::TreeArgs tree_args = {};
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_N = -1;
   // autotuning of the near/check launch (kernel variant, source chunks)

@@ -90,6 +90,32 @@ int pair_ragged_variant();   // kernel code the ragged launch runs (plan tiles w
 cudaError_t launch_far_series(int precision, const void* tgt, int N, const double* A, const double* norm,
                               int p, double inv_rc, double* out, cudaStream_t s);
 // scale multiplies W and ysurf (a geometry built for the box divided by scale)
+// Tree evaluation of the near-field and check-point sums (tree.cu).
+struct TreeArgs {
+  int L, P;              // leaf level (8^L leaves), expansion order
+  float Rs, D, inv_wL;   // root cube [-Rs, Rs]^3 of side D; 1 / leaf width
+  int moff[8];           // offset (floats) of level l's multipoles in M
+  const float* norm;     // (P+1)^2: c_n0, sqrt(2) c_nm (2m-1)!! at n*(P+1) + m
+  const float* fac;      // (P+1)^2: 4 pi/(2n+1) * norm^2 at k = n^2 + n + m
+};
+struct TreeLaunch {
+  TreeArgs t;
+  const float4* src;     // images in B (x, y, z, q), count sc->Ns
+  const DevScalars* sc;
+  const float4* tgt;     // targets: ions (n_ions) then check points (n_tgt total)
+  int n_tgt, n_ions;
+  int *src_key, *src_count, *src_start, *src_cursor, *src_order;   // leaves: 8^L (+1)
+  int *tgt_key, *tgt_count, *tgt_start, *tgt_cursor, *tgt_order;
+  float4* src_sorted;    // images in leaf order
+  double* part;          // 8^L * (P+1)^2 P2M partials
+  float* M;              // multipoles of levels 2..L
+  double* out;           // out[c*ld + t], c = phi, grad (one chunk's layout)
+  int ld;
+};
+cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
+size_t tree_eval_smem(int P);
+int tree_max_order();
+
 // Sum a pair launch's per-chunk partials (rows 0..n_rows of leading
 // dimension ld) into out[c*ld + r], the layout of a single chunk; fixed order.
 cudaError_t launch_reduce_chunks(const double* part, int n_chunks, int ld, int n_rows, double* out,

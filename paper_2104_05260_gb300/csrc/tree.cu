@@ -1,0 +1,453 @@
+// Tree evaluation of the near-field and check-point sums (the O(N) path the
+// paper takes with an FMM library, Sec. 2.2 last step): the images in B are
+// binned into a uniform octree over the cube [-R_s, R_s]^3, each cell at
+// levels 2..L gets a multipole expansion of order P, and every target sums
+//   - the multipoles of the cells in its FMM interaction lists (children of
+//     its parent's neighbours that are not its own neighbours), level by
+//     level (multipole-to-particle), and
+//   - the sources of its 27 neighbouring leaves directly (FP32 pairs),
+// which covers every source exactly once.  The expansion uses the real
+// orthonormal solid harmonics of the fit (Eq. 5) and the addition theorem
+//   1/|x - s| = sum_n 4 pi/(2n+1) sum_m R_nm(s - c) I_nm(x - c),
+// R_nm = r^n Y_nm, I_nm = r^(-n-1) Y_nm, in coordinates scaled by the cell
+// width.  Both are polynomials in x, y, z (and 1/r^2 for I) evaluated by
+// three-term recursions; norm[n*(P+1) + m] folds in the normalisation and
+// (2m-1)!! as in the series far field.
+//
+// Binning uses atomic slots followed by a per-bin sort by index, and every
+// sum has a fixed order, so the result is deterministic.  All arithmetic of
+// the expansions is FP32 with FP64 sums across levels; the identity image of
+// an ion is the only source a target skips (its other images are summed
+// like any source).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.hpp"
+
+namespace hsma {
+
+constexpr int kTreeThreads = 128;    // targets per M2P/P2P pass
+constexpr int kMaxOrder = 14;   // orders 4, 6, ..., 14 are compiled
+
+__device__ __forceinline__ int spread3(int v) {
+  // interleave the low 10 bits of v with two zero bits between each
+  unsigned x = (unsigned)v & 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return (int)x;
+}
+
+__device__ __forceinline__ int morton(int ix, int iy, int iz) {
+  return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
+__device__ __forceinline__ int cell_coord(float x, float origin, float inv_w, int n) {
+  int c = (int)floorf((x - origin) * inv_w);
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// ---------------------------------------------------------------- binning
+__global__ void k_tree_bin(const float4* __restrict__ pts, int n_fixed, const DevScalars* sc, TreeArgs t,
+                           int* __restrict__ key, int* __restrict__ count) {
+  const int n = sc ? sc->Ns : n_fixed;
+  const int nside = 1 << t.L;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 p = pts[i];
+    const int k = morton(cell_coord(p.x, -t.Rs, t.inv_wL, nside), cell_coord(p.y, -t.Rs, t.inv_wL, nside),
+                         cell_coord(p.z, -t.Rs, t.inv_wL, nside));
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+  }
+}
+
+// exclusive scan of count[0..n) into start[0..n], one block
+__global__ void __launch_bounds__(1024) k_tree_scan(const int* __restrict__ count, int n, int* __restrict__ start) {
+  __shared__ int sh[1024];
+  const int per = (n + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+  int s = 0;
+  for (int b = b0; b < b1; ++b) s += count[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int v = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - s;
+  for (int b = b0; b < b1; ++b) {
+    start[b] = run;
+    run += count[b];
+  }
+  if (threadIdx.x == 1023) start[n] = sh[1023];
+}
+
+__global__ void k_tree_fill(int n_fixed, const DevScalars* sc, const int* __restrict__ key,
+                            const int* __restrict__ start, int* __restrict__ cursor, int* __restrict__ order) {
+  const int n = sc ? sc->Ns : n_fixed;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = key[i];
+    order[start[k] + atomicAdd(&cursor[k], 1)] = i;
+  }
+}
+
+// each bin's entries in increasing index order (deterministic sums)
+__global__ void k_tree_sort_bins(const int* __restrict__ start, int n_bins, int* __restrict__ order) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bins) return;
+  int* l = order + start[b];
+  const int n = start[b + 1] - start[b];
+  for (int k = 1; k < n; ++k) {
+    const int v = l[k];
+    int j = k - 1;
+    while (j >= 0 && l[j] > v) {
+      l[j + 1] = l[j];
+      --j;
+    }
+    l[j + 1] = v;
+  }
+}
+
+// sources in bin order (positions and charges), for the P2M and P2P loops
+__global__ void k_tree_gather(const float4* __restrict__ src, const int* __restrict__ order, int n_fixed,
+                              const DevScalars* sc, float4* __restrict__ out) {
+  const int n = sc ? sc->Ns : n_fixed;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = src[order[i]];
+}
+
+// ---------------------------------------------------------------- P2M
+// One thread per coefficient (n, m) of one item: the sources of the item
+// (a cell of level il >= l, a contiguous range of leaves in Morton order)
+// expanded about the centre of its level-l ancestor.  part[item * nc + k]
+// (FP64 sums in source order).
+__global__ void k_tree_p2m(TreeArgs t, int l, int il, const float4* __restrict__ srcs,
+                           const int* __restrict__ leaf_start, double* __restrict__ part) {
+  const int item = blockIdx.x;
+  const int nc = (t.P + 1) * (t.P + 1);
+  const int k = threadIdx.x;
+  const int shift = 3 * (t.L - il);
+  const int s0 = leaf_start[item << shift], s1 = leaf_start[(item + 1) << shift];
+  if (k >= nc) return;
+  double acc = 0.0;
+  if (s1 > s0) {
+    const int n = (int)sqrtf((float)k + 0.5f);   // k = n^2 + n + m
+    const int m = k - n * n - n;
+    const int am = m < 0 ? -m : m;
+    // centre of the level-l ancestor of this item
+    const int code = item >> (3 * (il - l));
+    int ix = 0, iy = 0, iz = 0;
+    for (int b = 0; b < l; ++b) {
+      ix |= ((code >> (3 * b)) & 1) << b;
+      iy |= ((code >> (3 * b + 1)) & 1) << b;
+      iz |= ((code >> (3 * b + 2)) & 1) << b;
+    }
+    const float w = t.D / (float)(1 << l), inv_w = 1.0f / w;
+    const float cx = -t.Rs + (ix + 0.5f) * w, cy = -t.Rs + (iy + 0.5f) * w, cz = -t.Rs + (iz + 0.5f) * w;
+    for (int s = s0; s < s1; ++s) {
+      const float4 p = srcs[s];
+      const float x = (p.x - cx) * inv_w, y = (p.y - cy) * inv_w, z = (p.z - cz) * inv_w;
+      const float r2 = x * x + y * y + z * z;
+      // (x + iy)^|m|
+      float C = 1.0f, S = 0.0f;
+      for (int j = 0; j < am; ++j) {
+        const float nC = x * C - y * S;
+        S = x * S + y * C;
+        C = nC;
+      }
+      // V'_n^|m| by the regular recursion
+      float v1 = 1.0f, v2 = 0.0f;
+      for (int j = am + 1; j <= n; ++j) {
+        const float v = (j == am + 1) ? (float)(2 * am + 1) * z * v1
+                                      : ((float)(2 * j - 1) * z * v1 - (float)(j + am - 1) * r2 * v2) / (float)(j - am);
+        v2 = v1;
+        v1 = v;
+      }
+      const float T = (m > 0) ? C : (m < 0 ? S : 1.0f);
+      acc += (double)(p.w * v1 * T);
+    }
+    acc *= t.fac[k];
+  }
+  part[(size_t)item * nc + k] = acc;
+}
+
+// M[cell][k] = sum over the cell's items (contiguous in Morton order) of part
+__global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_cell, int n_cells, int nc,
+                                float* __restrict__ M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cells * nc) return;
+  const int c = i / nc, k = i - c * nc;
+  double s = 0.0;
+  for (int j = 0; j < items_per_cell; ++j) s += part[((size_t)c * items_per_cell + j) * nc + k];
+  M[i] = (float)s;
+}
+
+// ---------------------------------------------------------------- M2P + P2P
+// One block per cell G of level L-1 (its 8 leaves' targets, in index order
+// within each leaf, kTreeThreads at a time).  For levels l < L the
+// interaction list depends only on G's ancestor, so each listed cell's
+// multipole is staged once in shared memory for all of G's targets.  At the
+// leaf level the list is the children of G's neighbours; a thread skips the
+// leaves adjacent to its own.  Direct pairs come from the 4 x 4 x 4 leaves
+// around G, each thread taking those adjacent to its own leaf.
+//
+// Multipoles hold 4 pi/(2n+1) norm^2 sum q V'T, so the evaluation multiplies
+// by the irregular polynomial U'T alone; 1/(n-m) comes from a table.
+template <int P>
+__device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, float x, float y, float z, float* phi,
+                                               float* gx, float* gy, float* gz) {
+  // P is a compile-time constant: both loops unroll, the recursion
+  // coefficients fold, and the independent m-chains interleave
+  const float r2 = x * x + y * y + z * z;
+  const float rho = 1.0f / r2;
+  const float rinv = rsqrtf(r2);
+  float C = 1.0f, S = 0.0f, Cx = 0.0f, Cy = 0.0f, Sx = 0.0f, Sy = 0.0f;
+  float um = rinv;   // r^-(2m+1) for m = 0
+  float p = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int m = 0; m <= P; ++m) {
+    float u1 = um, z1 = 0.0f, q1 = -((float)m + 0.5f) * rho * um;   // U, dU/dz, dU/d(r^2)
+    float u2 = 0.0f, z2 = 0.0f, q2 = 0.0f;
+#pragma unroll
+    for (int n = m; n <= P; ++n) {
+      float u, uz, uq;
+      if (n == m) {
+        u = u1; uz = z1; uq = q1;
+      } else {
+        if (n == m + 1) {
+          const float a = (float)(2 * m + 1) * rho;
+          u = a * z * u1;
+          uz = a * (u1 + z * z1);
+          uq = a * z * q1 - u * rho;
+        } else {
+          const float a = ((float)(2 * n - 1) / (float)(n - m)) * rho;
+          const float b = ((float)(n + m - 1) / (float)(n - m)) * rho;
+          u = a * z * u1 - b * u2;
+          uz = a * (u1 + z * z1) - b * z2;
+          uq = a * z * q1 - b * q2 - u * rho;
+        }
+        u2 = u1; z2 = z1; q2 = q1;
+        u1 = u; z1 = uz; q1 = uq;
+      }
+      const float Ux = 2.0f * x * uq, Uy = 2.0f * y * uq, Uz = uz + 2.0f * z * uq;
+      const int base = n * n + n;
+      if (m == 0) {
+        const float a0 = Mc[base];
+        p += a0 * u;
+        ax += a0 * Ux;
+        ay += a0 * Uy;
+        az += a0 * Uz;
+      } else {
+        const float ac = Mc[base + m], as = Mc[base - m];
+        const float wv = ac * C + as * S;
+        const float wx = ac * Cx + as * Sx, wy = ac * Cy + as * Sy;
+        p += u * wv;
+        ax += Ux * wv + u * wx;
+        ay += Uy * wv + u * wy;
+        az += Uz * wv;
+      }
+    }
+    const float nC = x * C - y * S, nS = x * S + y * C;
+    const float nCx = C + x * Cx - y * Sx, nSx = S + x * Sx + y * Cx;
+    const float nCy = x * Cy - S - y * Sy, nSy = x * Sy + C + y * Cy;
+    C = nC; S = nS; Cx = nCx; Sx = nSx; Cy = nCy; Sy = nSy;
+    um *= rho;
+  }
+  *phi += p;
+  *gx += ax;
+  *gy += ay;
+  *gz += az;
+}
+
+__device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y, int* z) {
+  int ix = 0, iy = 0, iz = 0;
+  for (int b = 0; b < bits; ++b) {
+    ix |= ((code >> (3 * b)) & 1) << b;
+    iy |= ((code >> (3 * b + 1)) & 1) << b;
+    iz |= ((code >> (3 * b + 2)) & 1) << b;
+  }
+  *x = ix;
+  *y = iy;
+  *z = iz;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
+                                                            int n_ions, const int* __restrict__ tgt_start,
+                                                            const int* __restrict__ tgt_order,
+                                                            const float4* __restrict__ srcs,
+                                                            const int* __restrict__ src_order,
+                                                            const int* __restrict__ leaf_start,
+                                                            const float* __restrict__ M, double* __restrict__ out,
+                                                            int ld) {
+  extern __shared__ __align__(16) float tree_smem[];
+  const int nc = (t.P + 1) * (t.P + 1);
+  const int nc4 = (nc + 3) & ~3;
+  float* sM = tree_smem;                  // one cell's multipole
+  float* srecip = tree_smem + nc4;        // 1/k, k = 0..P (padded)
+  float4* stile = reinterpret_cast<float4*>(srecip + ((t.P + 4) & ~3));   // direct-pair source tile
+  int* sid = reinterpret_cast<int*>(stile + kTreeThreads);
+  const int G = blockIdx.x;                       // cell of level L-1
+  const int t0 = tgt_start[G << 3], t1 = tgt_start[(G + 1) << 3];
+  if (t1 <= t0) return;
+  for (int k = threadIdx.x; k <= t.P; k += blockDim.x) srecip[k] = k ? 1.0f / (float)k : 0.0f;
+  int gx0, gy0, gz0;
+  morton_decode(G, t.L - 1, &gx0, &gy0, &gz0);
+  const int nsideL = 1 << t.L;
+  __syncthreads();
+  for (int base = t0; base < t1; base += kTreeThreads) {
+    const int slot = base + threadIdx.x;
+    const bool active = slot < t1;
+    const int ti = active ? tgt_order[slot] : 0;
+    const float4 p = tgt[ti];
+    // this target's leaf (the first leaf of G whose range holds the slot)
+    int leaf = G << 3;
+    while (leaf < ((G + 1) << 3) - 1 && tgt_start[leaf + 1] <= slot) ++leaf;
+    int lx, ly, lz;
+    morton_decode(leaf, t.L, &lx, &ly, &lz);
+    double phi = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int l = 2; l <= t.L; ++l) {
+      // the reference cell: G's ancestor at l < L; at l = L the lists of all
+      // eight leaves together (children of G's neighbours)
+      const int sh = (t.L - 1) - l;
+      const int cx = l < t.L ? gx0 >> sh : gx0, cy = l < t.L ? gy0 >> sh : gy0, cz = l < t.L ? gz0 >> sh : gz0;
+      const int px = l < t.L ? cx >> 1 : gx0, py = l < t.L ? cy >> 1 : gy0, pz = l < t.L ? cz >> 1 : gz0;
+      const int nside = 1 << l;
+      const float w = t.D / (float)nside, inv_w = 1.0f / w;
+      const int lshift = 3 * (t.L - l);
+      float fp = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+      for (int j = 0; j < 216; ++j) {
+        const int ox = 2 * (px + (j % 3) - 1) + ((j / 27) & 1);
+        const int oy = 2 * (py + ((j / 3) % 3) - 1) + ((j / 54) & 1);
+        const int oz = 2 * (pz + ((j / 9) % 3) - 1) + ((j / 108) & 1);
+        if (ox < 0 || oy < 0 || oz < 0 || ox >= nside || oy >= nside || oz >= nside) continue;
+        if (l < t.L && abs(ox - cx) <= 1 && abs(oy - cy) <= 1 && abs(oz - cz) <= 1) continue;
+        const int code = morton(ox, oy, oz);
+        if (leaf_start[(code + 1) << lshift] == leaf_start[code << lshift]) continue;   // empty cell
+        __syncthreads();
+        const float* Mc = M + t.moff[l] + (size_t)code * nc;
+        for (int k = threadIdx.x; k < nc; k += blockDim.x) sM[k] = Mc[k];
+        __syncthreads();
+        const bool take = active && (l < t.L || abs(ox - lx) > 1 || abs(oy - ly) > 1 || abs(oz - lz) > 1);
+        if (take) {
+          const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
+          const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
+          const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
+          float a = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+          m2p_accumulate<P>(sM, dx, dy, dz, &a, &bx, &by, &bz);
+          fp += a;
+          fx += bx;
+          fy += by;
+          fz += bz;
+        }
+      }
+      phi += (double)fp * (double)inv_w;
+      gx += (double)fx * (double)(inv_w * inv_w);
+      gy += (double)fy * (double)(inv_w * inv_w);
+      gz += (double)fz * (double)(inv_w * inv_w);
+    }
+    // direct pairs: the 4 x 4 x 4 leaves around G, each thread its own 27
+    // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is skipped
+    for (int j = 0; j < 64; ++j) {
+      const int ox = 2 * gx0 - 1 + (j & 3), oy = 2 * gy0 - 1 + ((j >> 2) & 3), oz = 2 * gz0 - 1 + (j >> 4);
+      if (ox < 0 || oy < 0 || oz < 0 || ox >= nsideL || oy >= nsideL || oz >= nsideL) continue;
+      const int code = morton(ox, oy, oz);
+      const int s0 = leaf_start[code], s1 = leaf_start[code + 1];
+      if (s1 <= s0) continue;
+      const bool take = active && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1;
+      float fp = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+      for (int sb = s0; sb < s1; sb += kTreeThreads) {
+        __syncthreads();
+        if (sb + (int)threadIdx.x < s1) {
+          stile[threadIdx.x] = srcs[sb + threadIdx.x];
+          sid[threadIdx.x] = src_order[sb + threadIdx.x];
+        }
+        __syncthreads();
+        const int nb = min(kTreeThreads, s1 - sb);
+        if (take)
+          for (int k = 0; k < nb; ++k) {
+            if (ti < n_ions && sid[k] == ti) continue;
+            const float4 s = stile[k];
+            const float dx = s.x - p.x, dy = s.y - p.y, dz = s.z - p.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float ri = rsqrtf(r2);
+            const float qr = s.w * ri;
+            const float qr3 = qr * ri * ri;
+            fp += qr;
+            fx += qr3 * dx;
+            fy += qr3 * dy;
+            fz += qr3 * dz;
+          }
+      }
+      phi += fp;
+      gx += fx;
+      gy += fy;
+      gz += fz;
+    }
+    if (active) {
+      // as the pair kernels: phi and its gradient with respect to the target
+      out[ti] = phi;
+      out[(size_t)ld + ti] = gx;
+      out[2 * (size_t)ld + ti] = gy;
+      out[3 * (size_t)ld + ti] = gz;
+    }
+  }
+}
+
+size_t tree_eval_smem(int P) {
+  const int nc4 = ((P + 1) * (P + 1) + 3) & ~3;
+  return (size_t)(nc4 + ((P + 4) & ~3)) * 4 + kTreeThreads * 16 + kTreeThreads * 4;
+}
+
+int tree_max_order() { return kMaxOrder; }
+
+cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
+  const TreeArgs& t = T.t;
+  const int nleaf = 1 << (3 * t.L);
+  const int nc = (t.P + 1) * (t.P + 1);
+  const int grid = 4 * 152;
+  cudaError_t e = cudaMemsetAsync(T.src_count, 0, (size_t)nleaf * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.src_cursor, 0, (size_t)nleaf * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.tgt_count, 0, (size_t)nleaf * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(T.tgt_cursor, 0, (size_t)nleaf * 4, s);
+  if (e != cudaSuccess) return e;
+  // sources (count on the device) and targets into leaves
+  k_tree_bin<<<grid, 256, 0, s>>>(T.src, 0, T.sc, t, T.src_key, T.src_count);
+  k_tree_bin<<<grid, 256, 0, s>>>(T.tgt, T.n_tgt, nullptr, t, T.tgt_key, T.tgt_count);
+  k_tree_scan<<<1, 1024, 0, s>>>(T.src_count, nleaf, T.src_start);
+  k_tree_scan<<<1, 1024, 0, s>>>(T.tgt_count, nleaf, T.tgt_start);
+  k_tree_fill<<<grid, 256, 0, s>>>(0, T.sc, T.src_key, T.src_start, T.src_cursor, T.src_order);
+  k_tree_fill<<<grid, 256, 0, s>>>(T.n_tgt, nullptr, T.tgt_key, T.tgt_start, T.tgt_cursor, T.tgt_order);
+  k_tree_sort_bins<<<(nleaf + 255) / 256, 256, 0, s>>>(T.src_start, nleaf, T.src_order);
+  k_tree_sort_bins<<<(nleaf + 255) / 256, 256, 0, s>>>(T.tgt_start, nleaf, T.tgt_order);
+  k_tree_gather<<<grid, 256, 0, s>>>(T.src, T.src_order, 0, T.sc, T.src_sorted);
+  // multipoles, level by level: items are cells of level il = max(l, L - 1)
+  const int p2m_threads = ((nc + 31) / 32) * 32;
+  for (int l = 2; l <= t.L; ++l) {
+    const int il = l >= t.L - 1 ? l : t.L - 1;
+    const int items = 1 << (3 * il);
+    k_tree_p2m<<<items, p2m_threads, 0, s>>>(t, l, il, T.src_sorted, T.src_start, T.part);
+    const int cells = 1 << (3 * l);
+    const int per = items / cells;
+    k_tree_m_reduce<<<(cells * nc + 255) / 256, 256, 0, s>>>(T.part, per, cells, nc, T.M + t.moff[l]);
+  }
+  const size_t sm = tree_eval_smem(t.P);
+#define HSMA_TREE_EVAL(PP)                                                                                  \
+  k_tree_eval<PP><<<nleaf / 8, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order, T.src_sorted, \
+                                                      T.src_order, T.src_start, T.M, T.out, T.ld)
+  switch (t.P) {
+    case 4: HSMA_TREE_EVAL(4); break;
+    case 6: HSMA_TREE_EVAL(6); break;
+    case 8: HSMA_TREE_EVAL(8); break;
+    case 10: HSMA_TREE_EVAL(10); break;
+    case 12: HSMA_TREE_EVAL(12); break;
+    case 14: HSMA_TREE_EVAL(14); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HSMA_TREE_EVAL
+  return cudaGetLastError();
+}
+
+}  // namespace hsma

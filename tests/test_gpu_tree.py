@@ -1,0 +1,87 @@
+"""Tree evaluation of the near-field and check-point sums (option near_tree):
+an approximation of the plain sums the oracle computes, with an error set by
+the expansion order P.  Checked against the oracle (energy, forces,
+potential), for error decreasing with P, for 2D slabs, for bitwise
+repeatability, and against the dense GPU path at the bench workload."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import hsma as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2104_05260_gb300 import build
+    build.build()
+    import paper_2104_05260_gb300 as P
+    P.lib()
+    return P
+
+
+def frms(F, Fr):
+    return math.sqrt(np.mean(np.sum((F - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1)))
+
+
+def run(P, c, x, q, **opt):
+    h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=1, near_tree=1,
+               dtn_grid=c.dtn_grid, **opt)
+    E, F, pot = h.eval(x, q, potential=True)
+    L = int(h.info("tree_levels"))
+    h.close()
+    return E, F, pot, L
+
+
+def test_tree_matches_oracle_and_converges(P):
+    c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 6, 800), x, q)
+    errs = []
+    for order in (4, 6, 8, 10):
+        E, F, pot, L = run(P, c, x, q, tree_order=order)
+        assert L >= 3
+        errs.append((frms(F, ref["forces"]), abs(E - ref["energy"]) / abs(ref["energy"])))
+    # multipole truncation error falls with the order; P = 10 meets the FP32 bounds
+    assert errs[0][0] > errs[1][0] > errs[2][0] > errs[3][0]
+    assert errs[3][0] <= 2e-5 and errs[3][1] <= 1e-5, errs
+
+
+@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.5, -0.3)])
+def test_tree_2d(P, gam):
+    c = workloads.small_case(2000, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam, G=24, seed=12)
+    x, q = workloads.electrolyte(c, margin=0.2)
+    st = O.make_setup(c.box, 2, 6, 600, gam[0], gam[1], dtn_grid=24)
+    ref = O.evaluate(st, x, q)
+    E, F, pot, L = run(P, c, x, q, tree_order=10)
+    scale = 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
+    assert abs(E - ref["energy"]) <= 1e-5 * scale
+    assert frms(F, ref["forces"]) <= 2e-5
+
+
+def test_tree_is_repeatable_and_matches_dense_at_bench_size(P):
+    c = workloads.case(2)
+    x, q = workloads.electrolyte(c)
+    E1, F1, _, L = run(P, c, x, q)
+    E2, F2, _, _ = run(P, c, x, q)
+    assert E1 == E2 and np.array_equal(F1, F2)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1)
+    Ed, Fd, _ = h.eval(x, q)
+    h.close()
+    assert L == 5
+    assert frms(F1, Fd) <= 2e-5
+    assert abs(E1 - Ed) <= 1e-5 * abs(Ed)
+
+
+def test_tree_rejects_fp64_and_bad_order(P):
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=0, near_tree=1)
+    with pytest.raises(P.HSMAError):
+        h.eval(x, q)
+    with pytest.raises(P.HSMAError):
+        h.set_option("tree_order", 40)
+    h.close()
