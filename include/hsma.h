@@ -132,6 +132,9 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       0 (default) = direct sums.
  *   "tree_order"        expansion order of the tree: 4, 6, 8, 10 (default),
  *                       12 or 14.
+ *   "tree_leaf_level"   leaf level L of the tree (8^L leaves over the root
+ *                       cube), 2..6; 0 (default) = about 32 images per
+ *                       occupied leaf.
  *   "far_field"         0 (default) = the far field from the M surface charges
  *                       (Eq. 8, the paper's choice); 1 = the fitted series of
  *                       Eq. 5 itself, sum over n >= 1 of A_nm (r/R_c)^n Y_nm,

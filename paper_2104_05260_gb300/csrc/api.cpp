@@ -205,6 +205,7 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   const int P = h->tree_order;
   const double per_leaf = h->ns_est / (32.0 * 0.52);
   int L = (int)std::floor(std::log(std::max(per_leaf, 1.0)) / std::log(8.0));
+  if (h->tree_leaf_level > 0) L = h->tree_leaf_level;
   L = std::max(2, std::min(6, L));
   const size_t nleaf = (size_t)1 << (3 * L);
   const int nc = (P + 1) * (P + 1);
@@ -738,6 +739,10 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     if (!(v >= 4) || v > tree_max_order() || std::fmod(v, 2.0) != 0.0)
       return fail(h, HSMA_ERR_ARG, "tree_order must be one of 4, 6, 8, 10, 12, 14");
     h->tree_order = (int)v;
+    h->plan_N = -1;
+  } else if (k == "tree_leaf_level") {
+    if (!(v >= 0) || v > 6 || v == 1) return fail(h, HSMA_ERR_ARG, "tree_leaf_level must be 0 (automatic) or in [2, 6]");
+    h->tree_leaf_level = (int)v;
     h->plan_N = -1;
   } else if (k == "far_field") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "far_field must be 0 (surface charges) or 1 (series)");

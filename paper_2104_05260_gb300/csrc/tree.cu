@@ -27,6 +27,7 @@
 namespace hsma {
 
 constexpr int kTreeThreads = 128;    // targets per M2P/P2P pass
+constexpr int kBatch = 8;            // interaction cells staged per barrier
 constexpr int kMaxOrder = 14;   // orders 4, 6, ..., 14 are compiled
 
 __device__ __forceinline__ int spread3(int v) {
@@ -119,58 +120,83 @@ __global__ void k_tree_gather(const float4* __restrict__ src, const int* __restr
 }
 
 // ---------------------------------------------------------------- P2M
-// One thread per coefficient (n, m) of one item: the sources of the item
-// (a cell of level il >= l, a contiguous range of leaves in Morton order)
-// expanded about the centre of its level-l ancestor.  part[item * nc + k]
-// (FP64 sums in source order).
-__global__ void k_tree_p2m(TreeArgs t, int l, int il, const float4* __restrict__ srcs,
-                           const int* __restrict__ leaf_start, double* __restrict__ part) {
+// One block per item (a cell of level il >= l: a contiguous range of leaves
+// in Morton order), its sources expanded about the centre of its level-l
+// ancestor.  Each lane takes one source and walks all (n, m) by the regular
+// recursions (P a compile-time constant); every term is summed over the
+// warp's 32 sources by a fixed butterfly and added to the warp's FP64 row in
+// shared memory; the rows are added in warp order.  part[item * nc + k].
+constexpr int kP2mThreads = 128;
+
+template <int P>
+__global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int il, const float4* __restrict__ srcs,
+                                                          const int* __restrict__ leaf_start,
+                                                          double* __restrict__ part) {
+  constexpr int nc = (P + 1) * (P + 1);
+  __shared__ double acc[kP2mThreads / 32][nc];
   const int item = blockIdx.x;
-  const int nc = (t.P + 1) * (t.P + 1);
-  const int k = threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int shift = 3 * (t.L - il);
   const int s0 = leaf_start[item << shift], s1 = leaf_start[(item + 1) << shift];
-  if (k >= nc) return;
-  double acc = 0.0;
+  for (int k = threadIdx.x; k < (kP2mThreads / 32) * nc; k += kP2mThreads) (&acc[0][0])[k] = 0.0;
+  __syncthreads();
   if (s1 > s0) {
-    const int n = (int)sqrtf((float)k + 0.5f);   // k = n^2 + n + m
-    const int m = k - n * n - n;
-    const int am = m < 0 ? -m : m;
-    // centre of the level-l ancestor of this item
-    const int code = item >> (3 * (il - l));
-    int ix = 0, iy = 0, iz = 0;
-    for (int b = 0; b < l; ++b) {
-      ix |= ((code >> (3 * b)) & 1) << b;
-      iy |= ((code >> (3 * b + 1)) & 1) << b;
-      iz |= ((code >> (3 * b + 2)) & 1) << b;
+    int ix, iy, iz;
+    {
+      const int code = item >> (3 * (il - l));
+      ix = iy = iz = 0;
+      for (int b = 0; b < l; ++b) {
+        ix |= ((code >> (3 * b)) & 1) << b;
+        iy |= ((code >> (3 * b + 1)) & 1) << b;
+        iz |= ((code >> (3 * b + 2)) & 1) << b;
+      }
     }
     const float w = t.D / (float)(1 << l), inv_w = 1.0f / w;
     const float cx = -t.Rs + (ix + 0.5f) * w, cy = -t.Rs + (iy + 0.5f) * w, cz = -t.Rs + (iz + 0.5f) * w;
-    for (int s = s0; s < s1; ++s) {
-      const float4 p = srcs[s];
-      const float x = (p.x - cx) * inv_w, y = (p.y - cy) * inv_w, z = (p.z - cz) * inv_w;
+    for (int sb = s0 + warp * 32; sb < s1; sb += kP2mThreads) {
+      const int si = sb + lane;
+      float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);   // lanes past the end carry q = 0
+      if (si < s1) pt = srcs[si];
+      const float x = (pt.x - cx) * inv_w, y = (pt.y - cy) * inv_w, z = (pt.z - cz) * inv_w;
       const float r2 = x * x + y * y + z * z;
-      // (x + iy)^|m|
-      float C = 1.0f, S = 0.0f;
-      for (int j = 0; j < am; ++j) {
+      float C = pt.w, S = 0.0f;   // q (x + iy)^m
+#pragma unroll
+      for (int m = 0; m <= P; ++m) {
+        float v1 = 1.0f, v2 = 0.0f;
+#pragma unroll
+        for (int n = m; n <= P; ++n) {
+          if (n == m + 1) {
+            v2 = v1;
+            v1 = (float)(2 * m + 1) * z * v1;
+          } else if (n > m + 1) {
+            const float v = ((float)(2 * n - 1) / (float)(n - m)) * z * v1 - ((float)(n + m - 1) / (float)(n - m)) * r2 * v2;
+            v2 = v1;
+            v1 = v;
+          }
+          float tc = v1 * C, ts = v1 * S;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            tc += __shfl_xor_sync(0xffffffffu, tc, o);
+            if (m > 0) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+          }
+          if (lane == 0) {
+            acc[warp][n * n + n + m] += (double)tc;
+            if (m > 0) acc[warp][n * n + n - m] += (double)ts;
+          }
+        }
         const float nC = x * C - y * S;
         S = x * S + y * C;
         C = nC;
       }
-      // V'_n^|m| by the regular recursion
-      float v1 = 1.0f, v2 = 0.0f;
-      for (int j = am + 1; j <= n; ++j) {
-        const float v = (j == am + 1) ? (float)(2 * am + 1) * z * v1
-                                      : ((float)(2 * j - 1) * z * v1 - (float)(j + am - 1) * r2 * v2) / (float)(j - am);
-        v2 = v1;
-        v1 = v;
-      }
-      const float T = (m > 0) ? C : (m < 0 ? S : 1.0f);
-      acc += (double)(p.w * v1 * T);
     }
-    acc *= t.fac[k];
   }
-  part[(size_t)item * nc + k] = acc;
+  __syncthreads();
+  for (int k = threadIdx.x; k < nc; k += kP2mThreads) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < kP2mThreads / 32; ++w2) sum += acc[w2][k];
+    part[(size_t)item * nc + k] = sum * (double)t.fac[k];
+  }
 }
 
 // M[cell][k] = sum over the cell's items (contiguous in Morton order) of part
@@ -274,7 +300,7 @@ __device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y
 }
 
 template <int P>
-__global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
+__global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
                                                             int n_ions, const int* __restrict__ tgt_start,
                                                             const int* __restrict__ tgt_order,
                                                             const float4* __restrict__ srcs,
@@ -283,16 +309,16 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const fl
                                                             const float* __restrict__ M, double* __restrict__ out,
                                                             int ld) {
   extern __shared__ __align__(16) float tree_smem[];
-  const int nc = (t.P + 1) * (t.P + 1);
-  const int nc4 = (nc + 3) & ~3;
-  float* sM = tree_smem;                  // one cell's multipole
-  float* srecip = tree_smem + nc4;        // 1/k, k = 0..P (padded)
-  float4* stile = reinterpret_cast<float4*>(srecip + ((t.P + 4) & ~3));   // direct-pair source tile
+  constexpr int nc = (P + 1) * (P + 1);
+  constexpr int nc4 = (nc + 3) & ~3;
+  float* sM = tree_smem;                  // kBatch cells' multipoles
+  float4* stile = reinterpret_cast<float4*>(sM + kBatch * nc4);   // direct-pair source tile
   int* sid = reinterpret_cast<int*>(stile + kTreeThreads);
+  int* slist = sid + kTreeThreads;        // compacted interaction list (<= 216)
+  int* swarp = slist + 216;               // per-warp counts
   const int G = blockIdx.x;                       // cell of level L-1
   const int t0 = tgt_start[G << 3], t1 = tgt_start[(G + 1) << 3];
   if (t1 <= t0) return;
-  for (int k = threadIdx.x; k <= t.P; k += blockDim.x) srecip[k] = k ? 1.0f / (float)k : 0.0f;
   int gx0, gy0, gz0;
   morton_decode(G, t.L - 1, &gx0, &gy0, &gz0);
   const int nsideL = 1 << t.L;
@@ -300,7 +326,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const fl
   for (int base = t0; base < t1; base += kTreeThreads) {
     const int slot = base + threadIdx.x;
     const bool active = slot < t1;
-    const int ti = active ? tgt_order[slot] : 0;
+    const int ti = active ? tgt_order[slot] : tgt_order[t0];
     const float4 p = tgt[ti];
     // this target's leaf (the first leaf of G whose range holds the slot)
     int leaf = G << 3;
@@ -317,31 +343,54 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const fl
       const int nside = 1 << l;
       const float w = t.D / (float)nside, inv_w = 1.0f / w;
       const int lshift = 3 * (t.L - l);
-      float fp = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
-      for (int j = 0; j < 216; ++j) {
-        const int ox = 2 * (px + (j % 3) - 1) + ((j / 27) & 1);
-        const int oy = 2 * (py + ((j / 3) % 3) - 1) + ((j / 54) & 1);
-        const int oz = 2 * (pz + ((j / 9) % 3) - 1) + ((j / 108) & 1);
-        if (ox < 0 || oy < 0 || oz < 0 || ox >= nside || oy >= nside || oz >= nside) continue;
-        if (l < t.L && abs(ox - cx) <= 1 && abs(oy - cy) <= 1 && abs(oz - cz) <= 1) continue;
-        const int code = morton(ox, oy, oz);
-        if (leaf_start[(code + 1) << lshift] == leaf_start[code << lshift]) continue;   // empty cell
-        __syncthreads();
-        const float* Mc = M + t.moff[l] + (size_t)code * nc;
-        for (int k = threadIdx.x; k < nc; k += blockDim.x) sM[k] = Mc[k];
-        __syncthreads();
-        const bool take = active && (l < t.L || abs(ox - lx) > 1 || abs(oy - ly) > 1 || abs(oz - lz) > 1);
-        if (take) {
-          const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
-          const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
-          const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
-          float a = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-          m2p_accumulate<P>(sM, dx, dy, dz, &a, &bx, &by, &bz);
-          fp += a;
-          fx += bx;
-          fy += by;
-          fz += bz;
+      // the list's non-empty cells, compacted in candidate order (ballot prefix)
+      int n_list = 0;
+      for (int r = 0; r < 216; r += kTreeThreads) {
+        const int j = r + threadIdx.x;
+        bool ok = false;
+        int code = 0;
+        if (j < 216) {
+          const int ox = 2 * (px + (j % 3) - 1) + ((j / 27) & 1);
+          const int oy = 2 * (py + ((j / 3) % 3) - 1) + ((j / 54) & 1);
+          const int oz = 2 * (pz + ((j / 9) % 3) - 1) + ((j / 108) & 1);
+          ok = !(ox < 0 || oy < 0 || oz < 0 || ox >= nside || oy >= nside || oz >= nside);
+          if (ok && l < t.L && abs(ox - cx) <= 1 && abs(oy - cy) <= 1 && abs(oz - cz) <= 1) ok = false;
+          if (ok) {
+            code = morton(ox, oy, oz);
+            ok = leaf_start[(code + 1) << lshift] != leaf_start[code << lshift];
+          }
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) swarp[wid] = __popc(bal);
+        __syncthreads();
+        int off = n_list;
+        for (int q2 = 0; q2 < wid; ++q2) off += swarp[q2];
+        if (ok) slist[off + __popc(bal & ((1u << lane) - 1u))] = code;
+        int tot = 0;
+        for (int q2 = 0; q2 < kTreeThreads / 32; ++q2) tot += swarp[q2];
+        n_list += tot;
+        __syncthreads();
+      }
+      float fp = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
+      for (int b0 = 0; b0 < n_list; b0 += kBatch) {
+        const int nb = min(kBatch, n_list - b0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nb * nc4; k += kTreeThreads) {
+          const int c = k / nc4, kk = k - c * nc4;
+          sM[k] = kk < nc ? M[t.moff[l] + (size_t)slist[b0 + c] * nc + kk] : 0.0f;
+        }
+        __syncthreads();
+        if (active)
+          for (int c = 0; c < nb; ++c) {
+            int ox, oy, oz;
+            morton_decode(slist[b0 + c], l, &ox, &oy, &oz);
+            if (l == t.L && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1) continue;
+            const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
+            const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
+            const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
+            m2p_accumulate<P>(sM + c * nc4, dx, dy, dz, &fp, &fx, &fy, &fz);
+          }
       }
       phi += (double)fp * (double)inv_w;
       gx += (double)fx * (double)(inv_w * inv_w);
@@ -369,11 +418,11 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const fl
         if (take)
           for (int k = 0; k < nb; ++k) {
             if (ti < n_ions && sid[k] == ti) continue;
-            const float4 s = stile[k];
-            const float dx = s.x - p.x, dy = s.y - p.y, dz = s.z - p.z;
+            const float4 sv = stile[k];
+            const float dx = sv.x - p.x, dy = sv.y - p.y, dz = sv.z - p.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
             const float ri = rsqrtf(r2);
-            const float qr = s.w * ri;
+            const float qr = sv.w * ri;
             const float qr3 = qr * ri * ri;
             fp += qr;
             fx += qr3 * dx;
@@ -398,7 +447,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_eval(TreeArgs t, const fl
 
 size_t tree_eval_smem(int P) {
   const int nc4 = ((P + 1) * (P + 1) + 3) & ~3;
-  return (size_t)(nc4 + ((P + 4) & ~3)) * 4 + kTreeThreads * 16 + kTreeThreads * 4;
+  return (size_t)kBatch * nc4 * 4 + kTreeThreads * 16 + kTreeThreads * 4 + 216 * 4 + (kTreeThreads / 32) * 4;
 }
 
 int tree_max_order() { return kMaxOrder; }
@@ -424,11 +473,20 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   k_tree_sort_bins<<<(nleaf + 255) / 256, 256, 0, s>>>(T.tgt_start, nleaf, T.tgt_order);
   k_tree_gather<<<grid, 256, 0, s>>>(T.src, T.src_order, 0, T.sc, T.src_sorted);
   // multipoles, level by level: items are cells of level il = max(l, L - 1)
-  const int p2m_threads = ((nc + 31) / 32) * 32;
   for (int l = 2; l <= t.L; ++l) {
     const int il = l >= t.L - 1 ? l : t.L - 1;
     const int items = 1 << (3 * il);
-    k_tree_p2m<<<items, p2m_threads, 0, s>>>(t, l, il, T.src_sorted, T.src_start, T.part);
+#define HSMA_TREE_P2M(PP) k_tree_p2m<PP><<<items, kP2mThreads, 0, s>>>(t, l, il, T.src_sorted, T.src_start, T.part)
+    switch (t.P) {
+      case 4: HSMA_TREE_P2M(4); break;
+      case 6: HSMA_TREE_P2M(6); break;
+      case 8: HSMA_TREE_P2M(8); break;
+      case 10: HSMA_TREE_P2M(10); break;
+      case 12: HSMA_TREE_P2M(12); break;
+      case 14: HSMA_TREE_P2M(14); break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef HSMA_TREE_P2M
     const int cells = 1 << (3 * l);
     const int per = items / cells;
     k_tree_m_reduce<<<(cells * nc + 255) / 256, 256, 0, s>>>(T.part, per, cells, nc, T.M + t.moff[l]);
