@@ -124,8 +124,9 @@ __global__ void k_tree_gather(const float4* __restrict__ src, const int* __restr
 // in Morton order), its sources expanded about the centre of its level-l
 // ancestor.  Each lane takes one source and walks all (n, m) by the regular
 // recursions (P a compile-time constant); every term is summed over the
-// warp's 32 sources by a fixed butterfly and added to the warp's FP64 row in
-// shared memory; the rows are added in warp order.  part[item * nc + k].
+// warp's 32 sources by a fixed butterfly and kept in a register of the lane
+// that owns it (k mod 32); the warps' rows are added in warp order in FP64.
+// part[item * nc + k].
 constexpr int kP2mThreads = 128;
 
 template <int P>
@@ -133,13 +134,15 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
                                                           const int* __restrict__ leaf_start,
                                                           double* __restrict__ part) {
   constexpr int nc = (P + 1) * (P + 1);
-  __shared__ double acc[kP2mThreads / 32][nc];
+  constexpr int nr = (nc + 31) / 32;    // terms owned per lane: k = lane + 32 r
+  __shared__ float acc[kP2mThreads / 32][nr * 32];
   const int item = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int shift = 3 * (t.L - il);
   const int s0 = leaf_start[item << shift], s1 = leaf_start[(item + 1) << shift];
-  for (int k = threadIdx.x; k < (kP2mThreads / 32) * nc; k += kP2mThreads) (&acc[0][0])[k] = 0.0;
-  __syncthreads();
+  float own[nr];
+#pragma unroll
+  for (int r = 0; r < nr; ++r) own[r] = 0.0f;
   if (s1 > s0) {
     int ix, iy, iz;
     {
@@ -173,15 +176,18 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
             v2 = v1;
             v1 = v;
           }
-          float tc = v1 * C, ts = v1 * S;
+          // warp sums by a fixed butterfly; the owner lane of term k keeps it
+          float tc = v1 * C;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            tc += __shfl_xor_sync(0xffffffffu, tc, o);
-            if (m > 0) ts += __shfl_xor_sync(0xffffffffu, ts, o);
-          }
-          if (lane == 0) {
-            acc[warp][n * n + n + m] += (double)tc;
-            if (m > 0) acc[warp][n * n + n - m] += (double)ts;
+          for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
+          const int kc = n * n + n + m;
+          own[kc >> 5] += (lane == (kc & 31)) ? tc : 0.0f;
+          if (m > 0) {
+            float ts = v1 * S;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+            const int ks = n * n + n - m;
+            own[ks >> 5] += (lane == (ks & 31)) ? ts : 0.0f;
           }
         }
         const float nC = x * C - y * S;
@@ -190,11 +196,13 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
       }
     }
   }
+#pragma unroll
+  for (int r = 0; r < nr; ++r) acc[warp][r * 32 + lane] = own[r];
   __syncthreads();
   for (int k = threadIdx.x; k < nc; k += kP2mThreads) {
     double sum = 0.0;
 #pragma unroll
-    for (int w2 = 0; w2 < kP2mThreads / 32; ++w2) sum += acc[w2][k];
+    for (int w2 = 0; w2 < kP2mThreads / 32; ++w2) sum += (double)acc[w2][k];
     part[(size_t)item * nc + k] = sum * (double)t.fac[k];
   }
 }
