@@ -309,30 +309,33 @@ __device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y
 
 template <int P>
 __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
-                                                            int n_ions, const int* __restrict__ tgt_start,
-                                                            const int* __restrict__ tgt_order,
-                                                            const float4* __restrict__ srcs,
-                                                            const int* __restrict__ src_order,
-                                                            const int* __restrict__ leaf_start,
-                                                            const float* __restrict__ M, double* __restrict__ out,
-                                                            int ld) {
+                                                               int n_ions, const int* __restrict__ tgt_start,
+                                                               const int* __restrict__ tgt_order,
+                                                               const float4* __restrict__ srcs,
+                                                               const int* __restrict__ src_order,
+                                                               const int* __restrict__ leaf_start,
+                                                               const float* __restrict__ M, double* __restrict__ out,
+                                                               int ld) {
+  // Warps work independently (no block barriers): warp w of the block takes
+  // G's targets w*32 + k*kTreeThreads + lane, compacts each level's list
+  // itself and stages multipoles in its own slice of shared memory.
   extern __shared__ __align__(16) float tree_smem[];
   constexpr int nc = (P + 1) * (P + 1);
   constexpr int nc4 = (nc + 3) & ~3;
-  float* sM = tree_smem;                  // kBatch cells' multipoles
-  float4* stile = reinterpret_cast<float4*>(sM + kBatch * nc4);   // direct-pair source tile
-  int* sid = reinterpret_cast<int*>(stile + kTreeThreads);
-  int* slist = sid + kTreeThreads;        // compacted interaction list (<= 216)
-  int* swarp = slist + 216;               // per-warp counts
+  constexpr int kWarps = kTreeThreads / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sM = tree_smem + (size_t)warp * kBatch * nc4;                        // kBatch multipoles
+  float4* stile = reinterpret_cast<float4*>(tree_smem + (size_t)kWarps * kBatch * nc4) + warp * 32;
+  int* sid = reinterpret_cast<int*>(reinterpret_cast<float4*>(tree_smem + (size_t)kWarps * kBatch * nc4) +
+                                    kTreeThreads) + warp * 32;
+  int* slist = sid + (kTreeThreads - warp * 32) + warp * 216;                  // compacted list, 216 per warp
   const int G = blockIdx.x;                       // cell of level L-1
   const int t0 = tgt_start[G << 3], t1 = tgt_start[(G + 1) << 3];
-  if (t1 <= t0) return;
   int gx0, gy0, gz0;
   morton_decode(G, t.L - 1, &gx0, &gy0, &gz0);
   const int nsideL = 1 << t.L;
-  __syncthreads();
-  for (int base = t0; base < t1; base += kTreeThreads) {
-    const int slot = base + threadIdx.x;
+  for (int base = t0 + warp * 32; base < t1; base += kTreeThreads) {
+    const int slot = base + lane;
     const bool active = slot < t1;
     const int ti = active ? tgt_order[slot] : tgt_order[t0];
     const float4 p = tgt[ti];
@@ -351,10 +354,10 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       const int nside = 1 << l;
       const float w = t.D / (float)nside, inv_w = 1.0f / w;
       const int lshift = 3 * (t.L - l);
-      // the list's non-empty cells, compacted in candidate order (ballot prefix)
+      // the list's non-empty cells, compacted in candidate order (warp ballot)
       int n_list = 0;
-      for (int r = 0; r < 216; r += kTreeThreads) {
-        const int j = r + threadIdx.x;
+      for (int r = 0; r < 216; r += 32) {
+        const int j = r + lane;
         bool ok = false;
         int code = 0;
         if (j < 216) {
@@ -369,26 +372,19 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
           }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) swarp[wid] = __popc(bal);
-        __syncthreads();
-        int off = n_list;
-        for (int q2 = 0; q2 < wid; ++q2) off += swarp[q2];
-        if (ok) slist[off + __popc(bal & ((1u << lane) - 1u))] = code;
-        int tot = 0;
-        for (int q2 = 0; q2 < kTreeThreads / 32; ++q2) tot += swarp[q2];
-        n_list += tot;
-        __syncthreads();
+        if (ok) slist[n_list + __popc(bal & ((1u << lane) - 1u))] = code;
+        n_list += __popc(bal);
       }
+      __syncwarp();
       float fp = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
       for (int b0 = 0; b0 < n_list; b0 += kBatch) {
         const int nb = min(kBatch, n_list - b0);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nb * nc4; k += kTreeThreads) {
+        __syncwarp();
+        for (int k = lane; k < nb * nc4; k += 32) {
           const int c = k / nc4, kk = k - c * nc4;
           sM[k] = kk < nc ? M[t.moff[l] + (size_t)slist[b0 + c] * nc + kk] : 0.0f;
         }
-        __syncthreads();
+        __syncwarp();
         if (active)
           for (int c = 0; c < nb; ++c) {
             int ox, oy, oz;
@@ -405,7 +401,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       gy += (double)fy * (double)(inv_w * inv_w);
       gz += (double)fz * (double)(inv_w * inv_w);
     }
-    // direct pairs: the 4 x 4 x 4 leaves around G, each thread its own 27
+    // direct pairs: the 4 x 4 x 4 leaves around G, each target its own 27
     // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is skipped
     for (int j = 0; j < 64; ++j) {
       const int ox = 2 * gx0 - 1 + (j & 3), oy = 2 * gy0 - 1 + ((j >> 2) & 3), oz = 2 * gz0 - 1 + (j >> 4);
@@ -414,15 +410,16 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       const int s0 = leaf_start[code], s1 = leaf_start[code + 1];
       if (s1 <= s0) continue;
       const bool take = active && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1;
+      if (!__any_sync(0xffffffffu, take)) continue;
       float fp = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-      for (int sb = s0; sb < s1; sb += kTreeThreads) {
-        __syncthreads();
-        if (sb + (int)threadIdx.x < s1) {
-          stile[threadIdx.x] = srcs[sb + threadIdx.x];
-          sid[threadIdx.x] = src_order[sb + threadIdx.x];
+      for (int sb = s0; sb < s1; sb += 32) {
+        __syncwarp();
+        if (sb + lane < s1) {
+          stile[lane] = srcs[sb + lane];
+          sid[lane] = src_order[sb + lane];
         }
-        __syncthreads();
-        const int nb = min(kTreeThreads, s1 - sb);
+        __syncwarp();
+        const int nb = min(32, s1 - sb);
         if (take)
           for (int k = 0; k < nb; ++k) {
             if (ti < n_ions && sid[k] == ti) continue;
@@ -455,7 +452,8 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
 
 size_t tree_eval_smem(int P) {
   const int nc4 = ((P + 1) * (P + 1) + 3) & ~3;
-  return (size_t)kBatch * nc4 * 4 + kTreeThreads * 16 + kTreeThreads * 4 + 216 * 4 + (kTreeThreads / 32) * 4;
+  const int warps = kTreeThreads / 32;
+  return (size_t)warps * kBatch * nc4 * 4 + kTreeThreads * 16 + kTreeThreads * 4 + (size_t)warps * 216 * 4;
 }
 
 int tree_max_order() { return kMaxOrder; }
