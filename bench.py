@@ -567,6 +567,8 @@ def main():
     ap.add_argument("--md-steps", type=int, default=200000, help="production steps of --md")
     ap.add_argument("--md-tdamp", type=float, default=0.01, help="thermostat damping time of --md")
     ap.add_argument("--md-eq", type=int, default=20000, help="equilibration steps of --md")
+    ap.add_argument("--near-tree", type=int, default=0, choices=[0, 1],
+                    help="1: tree evaluation of the near-field sums (option near_tree, order 10)")
     ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
                     help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
@@ -608,7 +610,7 @@ def main():
 
     x, q = workloads.electrolyte(c, seed=c.seed + 1000 * rank)
     N = c.N
-    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, timing=1, far_field=args.far_field)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, timing=1, far_field=args.far_field, near_tree=args.near_tree)
     stream = torch.cuda.current_stream(dev)
     P.hsma_set_stream(h.h, stream.cuda_stream)
     xd = torch.from_numpy(x).to(dev)
@@ -714,8 +716,14 @@ def main():
                            "frac": (pairs_near * FLOP_PER_PAIR / t_near / 1e12) / (2 * peak_instr)},
             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({mhz_src})",
             "near_ms": 1e3 * t_near, "lib_total_ms": float(np.mean(total_lib_ms))}
+    if args.near_tree:
+        # the tree does not sum the dense pairs: no pair-count roofline
+        roof = {"bound": "alu", "kernel": "k_tree_eval<10> (near field + check points)", "achieved": None,
+                "peak": peak_instr, "unit": "T FP32-pipe instr/s", "frac": None, "traffic": None,
+                "note": "tree evaluation; see profiles/k_tree_eval_hsma3d_n100000_p8_M2000_P10.md",
+                "near_ms": 1e3 * t_near, "lib_total_ms": float(np.mean(total_lib_ms))}
     tr = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr):
+    if os.path.exists(tr) and not args.near_tree:
         try:
             rec = json.load(open(tr))
             if (rec.get("pair_sources_sha1") == pair_sources_sha1()
@@ -732,6 +740,7 @@ def main():
                        "N_s": Ns, "n_check": n_check, "precision": "fp32-compute/fp64-accumulate",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
                        "far_field": "series (Eq. 5)" if args.far_field else "surface charges (Eq. 8)",
+                       "near_field": "tree, order 10" if args.near_tree else "direct sums",
                        "plan": plan},
             "pair_ints_per_s": pairs * ws / (ms_step / 1e3), "pairs_per_eval": pairs,
             "energy": energy, "roofline": roof,
@@ -754,7 +763,7 @@ def main():
     if not args.no_serve:
         line["serve"] = serve_bench(P)
     if not args.no_other_cases:
-        if not args.far_field:
+        if not args.far_field and not args.near_tree:
             line["far_field_series"] = far_series_compare(P, torch, stream, c, xd, qd, fd, h)
             e0 = np.zeros(1)
             P.hsma_eval_into(h.h, xd, qd, N, e0, fd)
