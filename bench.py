@@ -746,7 +746,7 @@ def main():
             "energy": energy, "roofline": roof,
             "e2e": {"value": ws / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": N * 32,
                     "d2h_bytes_per_step": N * 24 + 8},
-            "gpu_launches": 10 * args.steps, "clocks": clk.summary(), "fp64_path": fp64}
+            "gpu_launches": int(P.hsma_get_info(h.h, "kernels_per_eval")) * args.steps, "clocks": clk.summary(), "fp64_path": fp64}
     if not args.no_cpu_baseline:
         t_full, d = oracle_sample(c, x, q, 400)
         Fg = fd.cpu().numpy()[d["idx"]]

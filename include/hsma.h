@@ -181,7 +181,8 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
  * "far_chunks", "far_field", "tree_levels" (leaf level L of the tree, 0 when
- * off), "grid", "slots", "kernel", "tile_targets".
+ * off), "kernels_per_eval" (kernel launches of one evaluation), "grid",
+ * "slots", "kernel", "tile_targets".
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);

@@ -489,6 +489,11 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   rc = stage_assemble(h, N, forces_dev, pot_dev);
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[5], s);
+  // kernels this pipeline launches: prep 3, near 1 (tree: 10 + 2 per
+  // multipole level), chunk reduction 1 (not with the tree), fit 3, far 1,
+  // far reduction 1 (not with one far chunk), assembly 2
+  const bool far_one = h->far_series || h->chunks2 == 1;
+  h->kernels_per_eval = 3 + (h->near_tree ? 10 + 2 * (h->tree_L - 1) : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
   return HSMA_OK;
 }
 
@@ -824,6 +829,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "far_chunks") *value = h->far_series ? 1 : h->chunks2;
   else if (k == "far_field") *value = h->far_series;
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
+  else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;
   else if (k == "tile_targets") *value = pair_tile_targets(h->precision, h->precision ? h->tpt : 1);

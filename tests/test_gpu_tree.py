@@ -85,3 +85,17 @@ def test_tree_rejects_fp64_and_bad_order(P):
     with pytest.raises(P.HSMAError):
         h.set_option("tree_order", 40)
     h.close()
+
+
+@pytest.mark.parametrize("N,val", [(2, (1, -1)), (3, (2, -1)), (258, (1, -1))])
+def test_tree_tiny_and_ragged(P, N, val):
+    # leaf level 2 (the smallest tree): every leaf is within two of any other
+    L0 = 10.0 * (N / 1000) ** (1 / 3)
+    c = workloads.small_case(N, dims=3, box=(L0, L0, L0), p=4, M=200, valences=val, seed=N)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 4, 200), x, q)
+    E, F, pot, L = run(P, c, x, q, tree_order=10)
+    assert L == 2
+    scale = 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
+    assert abs(E - ref["energy"]) <= 1e-5 * scale
+    assert frms(F, ref["forces"]) <= 2e-5
