@@ -90,8 +90,11 @@ def case2_shape(N=8000, n_samp=48):
             "rel_force_rms_sampled": rel_rms(out["forces"], -q[idx, None] * ge), "sampled_ions": n_samp}
 
 
-def case3_shape(gam, margin, N=2000, n_samp=32):
-    c = workloads.small_case(N, dims=2, box=(20.0, 20.0, 10.0), p=8, M=1500, gammas=(gam, gam),
+def case3_shape(gam, margin, N=2000, n_samp=32, gam_bot=None):
+    """Slab of the case-3 shape; gam_bot (default gam) gives unequal
+    interfaces (image factors per Sec. 2.1, Eq. 4 with reading R7)."""
+    gb = gam if gam_bot is None else gam_bot
+    c = workloads.small_case(N, dims=2, box=(20.0, 20.0, 10.0), p=8, M=1500, gammas=(gam, gb),
                              G=80, seed=3)
     x, q = workloads.electrolyte(c, margin=margin)
     Lx, Ly, Lz = c.box
@@ -101,28 +104,49 @@ def case3_shape(gam, margin, N=2000, n_samp=32):
     ex = -np.ones(N, dtype=int)
     _, g = ewald2d_field(xc[idx], xc, q, Lx, Ly, rc, tol=1e-12,
                          exclude=np.arange(N)[idx])
-    for l in range(1, slab_lmax(gam, gam, Lx, Ly, Lz, eps=1e-12) + 1):
+    for l in range(1, slab_lmax(gam, gb, Lx, Ly, Lz, eps=1e-12) + 1):
         for sign in (+1, -1):
-            f = image_factor(l, sign, gam, gam)
+            f = image_factor(l, sign, gam, gb)
             if f == 0.0:
                 continue
             img = xc.copy()
             img[:, 2] = image_z(xc[:, 2], l, sign, Lz)
             _, gl = ewald2d_field(xc[idx], img, f * q, Lx, Ly, rc, tol=1e-12)
             g += gl
-    out = O.evaluate(O.make_setup(c.box, 2, 8, 1500, gam, gam, dtn_grid=80), x, q, targets=idx)
-    return {"case": f"2D 20x20x10, N = {N}, gamma = {gam}, wall margin {margin}, p = 8, M = 1500, G = 80",
+    out = O.evaluate(O.make_setup(c.box, 2, 8, 1500, gam, gb, dtn_grid=80), x, q, targets=idx)
+    return {"case": f"2D 20x20x10, N = {N}, gamma_top = {gam}, gamma_bot = {gb}, wall margin {margin}, "
+                    f"p = 8, M = 1500, G = 80",
             "rel_force_rms_sampled": rel_rms(out["forces"], -q[idx, None] * g), "sampled_ions": n_samp}
+
+
+def case1_variants():
+    """Case 1 under the options of the build: the unmasked near set, the
+    gradient-periodicity rows and the series far field, each against Ewald."""
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    L = c.box[0]
+    xc = (x - L * np.floor(x / L)) - 0.5 * L
+    Ee, _, ge = ewald3d(xc, q, c.box)
+    out = []
+    for label, kw, far in (("unmasked near set", dict(sphere_mask=False), "surface"),
+                           ("gradient rows", dict(grad_rows=True), "surface"),
+                           ("series far field", {}, "series")):
+        r = O.evaluate(O.make_setup(c.box, 3, c.p, c.M, **kw), x, q, far=far)
+        out.append({"case": f"{c.name}, {label}", "rel_energy": abs(r["energy"] - Ee) / abs(Ee),
+                    "rel_force_rms": rel_rms(r["forces"], -q[:, None] * ge)})
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
     a = ap.parse_args()
-    res = [case1(), case2_shape(N=4000 if a.quick else 8000)]
+    res = [case1(), *case1_variants(), case2_shape(N=4000 if a.quick else 8000)]
     for gam in (-0.95, 0.0, 0.95):
         for margin in (0.0, 0.5):
             res.append(case3_shape(gam, margin, N=800 if a.quick else 2000))
+    for gt, gb in ((0.95, -0.95), (-0.5, 0.8), (0.95, 0.0)):
+        res.append(case3_shape(gt, 0.5, N=800 if a.quick else 2000, gam_bot=gb))
     for r in res:
         print(json.dumps(r), flush=True)
 
