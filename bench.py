@@ -48,13 +48,15 @@ def peaks():
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.keep = path is not None
+        self.path = path or os.path.join(tempfile.gettempdir(), f"hsma_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -80,6 +82,8 @@ class Clocks:
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         try:
             rows = [l.split(",") for l in open(self.path) if l.strip()]
+            if not self.keep:
+                os.remove(self.path)
         except Exception:
             return out
         sm, mx, reasons = [], [], set()
@@ -560,6 +564,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other-cases", action="store_true")
     ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
+    ap.add_argument("--clocks-log", default=None,
+                    help="keep the nvidia-smi samples of the timed region in this CSV file")
     ap.add_argument("--record-traffic", default=None,
                     help="write profiles/traffic.json from this ncu CSV (near-field launch) and exit")
     ap.add_argument("--md", type=int, default=0, choices=[0, 1, 2, 3],
@@ -631,7 +637,7 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     near_ms, total_lib_ms = [], []
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_log) as clk:
         for i in range(args.steps):
             flush.fill_(float(i))              # evict L2 between steps (outside the events)
             ev[i][0].record(stream)
