@@ -324,6 +324,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
     if (rc) return rc;
   }
   h->plan_N = N;
+  h->plan_gen++;
   drop_graph(h);
   return HSMA_OK;
 }

@@ -31,6 +31,7 @@ struct hsma_md {
   double rdf_rmax = 5.0;
   int rdf_every = 0;
   cudaGraphExec_t g_step = nullptr, g_rdf = nullptr;
+  uint64_t plan_gen = 0;   // the electrostatics plan the loop was set up with
   std::string err;
   ~hsma_md();
 };
@@ -253,6 +254,7 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
     delete m;
     return frc;
   }
+  m->plan_gen = h->plan_gen;
   *out = m;
   return HSMA_OK;
 }
@@ -301,7 +303,8 @@ int hsma_md_run(hsma_md_t m, int64_t steps, double* thermo) {
   if (steps < 0 || steps > (int64_t)1 << 40) return md_fail(m, HSMA_ERR_ARG, "steps out of range");
   hsma_ctx* h = m->h;
   if (h->timing) return md_fail(m, HSMA_ERR_ARG, "the electrostatics handle has timing on");
-  if (h->geo_dirty || h->plan_N != m->N) return md_fail(m, HSMA_ERR_ARG, "electrostatics handle changed");
+  if (h->geo_dirty || h->plan_N != m->N || h->plan_gen != m->plan_gen)
+    return md_fail(m, HSMA_ERR_ARG, "the electrostatics handle was re-planned or changed");
   int rc = ensure_thermo(m, std::max<long long>(1, steps));
   if (rc) return rc;
   if (!m->g_step && (rc = capture(m, false, &m->g_step))) return rc;

@@ -124,3 +124,16 @@ def test_md_rejects_bad_arguments(P):
         P.MD(h2, x[:8] * 0.5, v[:8], q[:8], dt=0.01)    # box under 3 LJ cells a side
     h.close()
     h2.close()
+
+
+def test_md_refuses_a_replanned_handle(P):
+    x, v, q, box = system()
+    h = P.HSMA(box, 3, 6, 400, precision=1)
+    md = P.MD(h, x, v, q, dt=0.004)
+    md.run(2)
+    h.set_option("precision", 0)            # re-plans the handle's buffers and kernels
+    h.eval(x, q)
+    with pytest.raises(P.HSMAError):
+        md.run(1)
+    md.close()
+    h.close()
