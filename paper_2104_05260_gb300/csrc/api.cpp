@@ -203,18 +203,31 @@ void drop_graph(hsma_ctx* h) {
 static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   const Geometry& g = h->geo;
   const int P = h->tree_order;
-  const double per_leaf = h->ns_est / (32.0 * 0.52);
+  // images fill the sphere B (52 % of its cube) or, unmasked, the whole cube
+  const double per_leaf = h->ns_est / (32.0 * (g.par.sphere_mask ? 0.52 : 1.0));
   int L = (int)std::floor(std::log(std::max(per_leaf, 1.0)) / std::log(8.0));
   if (h->tree_leaf_level > 0) L = h->tree_leaf_level;
   L = std::max(2, std::min(6, L));
   const size_t nleaf = (size_t)1 << (3 * L);
   const int nc = (P + 1) * (P + 1);
+  // root cube: the sphere B, or, for the unmasked near set, every image of
+  // the shift table (sources must lie inside their cells for the expansions)
+  double half = g.Rs;
+  if (!g.par.sphere_mask) {
+    half = 0.0;
+    for (const Shift& sh : g.shifts) {
+      half = std::max(half, std::fabs(sh.sx) + 0.5 * g.par.box[0]);
+      half = std::max(half, std::fabs(sh.sy) + 0.5 * g.par.box[1]);
+      half = std::max(half, std::fabs(sh.zo) + 0.5 * g.par.box[2]);
+    }
+    half *= 1.0 + 1e-6;
+  }
   TreeArgs& t = h->tree_args;
   t.L = L;
   t.P = P;
-  t.Rs = (float)g.Rs;
-  t.D = (float)(2.0 * g.Rs);
-  t.inv_wL = (float)((double)(1 << L) / (2.0 * g.Rs));
+  t.Rs = (float)half;
+  t.D = (float)(2.0 * half);
+  t.inv_wL = (float)((double)(1 << L) / (2.0 * half));
   size_t off = 0;
   for (int l = 0; l < 8; ++l) {
     t.moff[l] = (int)off;

@@ -93,7 +93,7 @@ cudaError_t launch_far_series(int precision, const void* tgt, int N, const doubl
 // Tree evaluation of the near-field and check-point sums (tree.cu).
 struct TreeArgs {
   int L, P;              // leaf level (8^L leaves), expansion order
-  float Rs, D, inv_wL;   // root cube [-Rs, Rs]^3 of side D; 1 / leaf width
+  float Rs, D, inv_wL;   // root cube [-Rs, Rs]^3 of side D (Rs: its half-width); 1 / leaf width
   int moff[8];           // offset (floats) of level l's multipoles in M
   const float* norm;     // (P+1)^2: c_n0, sqrt(2) c_nm (2m-1)!! at n*(P+1) + m
   const float* fac;      // (P+1)^2: 4 pi/(2n+1) * norm^2 at k = n^2 + n + m

@@ -99,3 +99,13 @@ def test_tree_tiny_and_ragged(P, N, val):
     scale = 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
     assert abs(E - ref["energy"]) <= 1e-5 * scale
     assert frms(F, ref["forces"]) <= 2e-5
+
+
+def test_tree_with_the_unmasked_near_set(P):
+    # every image of the 27 cells is a source: the root cube must hold them all
+    c = workloads.small_case(2000, dims=3, box=(13.0, 13.0, 13.0), p=6, M=800, seed=19)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 6, 800, sphere_mask=False), x, q)
+    E, F, pot, L = run(P, c, x, q, tree_order=10, sphere_mask=0)
+    assert abs(E - ref["energy"]) <= 1e-5 * abs(ref["energy"])
+    assert frms(F, ref["forces"]) <= 2e-5
