@@ -26,6 +26,11 @@ thermostat but not its chain length or the degrees of freedom; a single
 thermostat and g = 3N - 3 are taken here.  With the thermostat off the step
 is plain velocity Verlet (NVE).
 
+Slabs (Sec. 4.3): with walls, the box is periodic in x and y only and the
+ions are kept in 0 < z < Lz by shifted-truncated LJ walls at z = 0 and
+z = Lz (energy 4 e_w [(s_w/d)^12 - (s_w/d)^6] + e_w for a distance d to the
+wall below 2^(1/6) s_w); positions wrap in x and y only.
+
 Everything is FP64 NumPy; the Coulomb forces come from a callable (the
 oracle's HSMA or Ewald sum).
 """
@@ -36,18 +41,19 @@ import numpy as np
 WCA_CUT = 2.0 ** (1.0 / 6.0)
 
 
-def wca(x, box, sigma=1.0, eps=1.0):
+def wca(x, box, sigma=1.0, eps=1.0, periodic=(True, True, True)):
     """Energy and forces of the shifted-truncated LJ repulsion, minimum image
-    in every periodic direction (3D), all pairs i < j."""
+    in the periodic directions, all pairs i < j."""
     x = np.asarray(x, dtype=np.float64)
     L = np.asarray(box, dtype=np.float64)
+    per = np.array(periodic, dtype=bool)
     n = len(x)
     F = np.zeros_like(x)
     U = 0.0
     rc2 = (WCA_CUT * sigma) ** 2
     for i in range(n - 1):
         d = x[i + 1:] - x[i]
-        d -= L * np.round(d / L)
+        d[:, per] -= L[per] * np.round(d[:, per] / L[per])
         r2 = np.sum(d * d, axis=1)
         m = r2 < rc2
         if not np.any(m):
@@ -62,10 +68,26 @@ def wca(x, box, sigma=1.0, eps=1.0):
     return U, F
 
 
-class State:
-    """Positions (wrapped into [0, L)), image counters, velocities, thermostat."""
+def walls(x, Lz, sigma_w=0.5, eps_w=1.0):
+    """Energy and forces of shifted-truncated LJ walls at z = 0 and z = Lz."""
+    z = np.asarray(x, dtype=np.float64)[:, 2]
+    F = np.zeros((len(z), 3))
+    U = 0.0
+    rc = WCA_CUT * sigma_w
+    for d, sign in ((z, 1.0), (Lz - z, -1.0)):     # distance to the wall, direction away from it
+        m = d < rc
+        s6 = (sigma_w / d[m]) ** 6
+        U += float(np.sum(4.0 * eps_w * (s6 * s6 - s6) + eps_w))
+        F[m, 2] += sign * 24.0 * eps_w * (2.0 * s6 * s6 - s6) / d[m]
+    return U, F
 
-    def __init__(self, x, v, q, box, mass=1.0):
+
+class State:
+    """Positions (wrapped into [0, L), in x and y only for a slab), image
+    counters, velocities, thermostat."""
+
+    def __init__(self, x, v, q, box, mass=1.0, slab=False):
+        self.slab = bool(slab)
         self.box = np.asarray(box, dtype=np.float64)
         self.x = np.array(x, dtype=np.float64)
         self.img = np.zeros(self.x.shape, dtype=np.int64)
@@ -83,12 +105,18 @@ class State:
         The quotient x / L can round across an integer; the two fix-ups put
         such a coordinate back inside."""
         k = np.floor(self.x / self.box)
+        if self.slab:
+            k[:, 2] = 0.0
         self.x -= k * self.box
         L = np.broadcast_to(self.box, self.x.shape)
         hi = self.x >= L
+        if self.slab:
+            hi[:, 2] = False
         self.x[hi] -= L[hi]
         k[hi] += 1
         lo = self.x < 0.0
+        if self.slab:
+            lo[:, 2] = False
         self.x[lo] += L[lo]
         k[lo] -= 1
         top = lo & (self.x >= L)
@@ -109,16 +137,22 @@ class Integrator:
     coulomb(x, q) -> (energy, forces) is the electrostatic solver; None leaves
     Coulomb out.  tdamp None means NVE."""
 
-    def __init__(self, coulomb, dt, kT=1.0, tdamp=None, sigma=1.0, eps=1.0):
+    def __init__(self, coulomb, dt, kT=1.0, tdamp=None, sigma=1.0, eps=1.0, wall_sigma=0.5, wall_eps=1.0):
         self.coulomb = coulomb
         self.dt = float(dt)
         self.kT = float(kT)
         self.tdamp = tdamp
         self.sigma = sigma
         self.eps = eps
+        self.wall_sigma = wall_sigma
+        self.wall_eps = wall_eps
 
     def forces(self, s):
-        U, F = wca(s.x, s.box, self.sigma, self.eps)
+        U, F = wca(s.x, s.box, self.sigma, self.eps, periodic=(True, True, not s.slab))
+        if s.slab:
+            Uw, Fw = walls(s.x, s.box[2], self.wall_sigma, self.wall_eps)
+            U += Uw
+            F = F + Fw
         Uc = 0.0
         if self.coulomb is not None:
             Uc, Fc = self.coulomb(s.x, s.q)

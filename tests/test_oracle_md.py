@@ -3,7 +3,9 @@ it does not itself compute: the WCA closed form and F = -grad U by finite
 differences, time reversibility and second-order energy conservation of
 velocity Verlet, the Nose-Hoover thermostat against an independent RK4
 solution of its scalar equations for an ideal gas, conservation of the
-extended energy, and the RDF counts against a brute-force double loop."""
+extended energy, the RDF counts against a brute-force double loop, and for
+the slab of Sec. 4.3 the LJ-wall closed form and gradient, reversibility and
+confinement."""
 import math
 
 import numpy as np
@@ -148,3 +150,41 @@ def test_rdf_counts_match_brute_force():
             if r < 3.0:
                 ref[int(r / 0.25)] += 1
     assert np.array_equal(h, ref)
+
+
+def test_walls_closed_form_and_gradient():
+    Lz = 6.0
+    for d in (0.3, 0.45, 0.5, md.WCA_CUT * 0.5 - 1e-9, 0.6):
+        x = np.array([[1.0, 1.0, d], [2.0, 2.0, 3.0]])
+        U, F = md.walls(x, Lz)
+        ref = 4 * ((0.5 / d) ** 12 - (0.5 / d) ** 6) + 1 if d < md.WCA_CUT * 0.5 else 0.0
+        assert abs(U - ref) < 1e-12 * max(1.0, abs(ref))
+        assert F[0, 2] >= 0.0                      # pushed away from the bottom wall
+    x = np.array([[1.0, 1.0, 0.4], [2.0, 2.0, Lz - 0.42]])
+    U, F = md.walls(x, Lz)
+    h = 1e-7
+    for i in range(2):
+        e = np.zeros_like(x); e[i, 2] = h
+        fd = -(md.walls(x + e, Lz)[0] - md.walls(x - e, Lz)[0]) / (2 * h)
+        assert abs(fd - F[i, 2]) < 1e-5 * max(1.0, abs(F[i, 2]))
+    assert F[1, 2] < 0.0
+
+
+def test_slab_nve_is_reversible_and_keeps_ions_inside():
+    rng = np.random.default_rng(6)
+    box = [6.0, 6.0, 4.0]
+    x = lattice(3, 4.0, 0.2, rng) + np.array([1.0, 1.0, 0.0])
+    x[:, 2] = 0.6 + (x[:, 2] / 4.0) * 2.8
+    n = len(x)
+    v = md.maxwell_velocities(n, 1.0, 1.0, rng)
+    s = md.State(x, v, np.zeros(n), box, slab=True)
+    it = md.Integrator(None, dt=0.002)
+    x0 = s.unwrapped().copy()
+    for _ in range(200):
+        it.step(s)
+        assert np.all((s.x[:, 2] > 0) & (s.x[:, 2] < box[2]))
+    s.v = -s.v
+    for _ in range(200):
+        it.step(s)
+    assert np.abs(s.unwrapped() - x0).max() < 1e-8
+    assert np.all(s.img[:, 2] == 0)
