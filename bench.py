@@ -519,6 +519,52 @@ def md_e1(P, valence=1, steps_eq=20000, steps_prod=200000, rdf_every=100, seed=1
             "g_ca": [round(float(v), 4) for v in g_ca]}
 
 
+def md_e3(P, valence=1, steps_eq=20000, steps_prod=200000, every=100, seed=13, bins=50):
+    """The confined electrolyte of Sec. 4.3 under the library's MD loop:
+    Lx = Ly = 100 sigma, Lz = 50 sigma, 218 anions and 218 (1:1) or 109 (2:1)
+    cations, WCA ions, LJ walls (eps kT, sigma 0.5) at the two interfaces,
+    gamma = 0.939 on both sides, Bjerrum length 3.5 sigma, dt = 0.005 tau,
+    Nose-Hoover with damping time 0.05 tau.  HSMA2D with lambda 1.6, p = 6
+    (the paper's parameter line), M = 600, G = 80, FP32 pairs.  Reports the
+    ion density across the slab (cations, anions, relative to the mean) and
+    the depletion next to the walls that the repulsive images cause."""
+    Lx, Lz = 100.0, 50.0
+    n_cat = {1: 218, 2: 109}[valence]
+    c = workloads.Case(f"e3_z{valence}", 2, (Lx, Lx, Lz), {valence: n_cat, -1: 218}, p=6, M=600, lam=1.6,
+                       gammas=(0.939, 0.939), dtn_grid=80, seed=seed)
+    x, q = workloads.electrolyte(c, min_dist=1.0, margin=1.0)
+    N = len(q)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    v = rng.normal(0.0, 1.0, (N, 3))
+    v -= v.mean(axis=0)
+    h = P.HSMA(c.box, 2, 6, 600, 0.939, 0.939, precision=1, coulomb_prefactor=3.5, dtn_grid=80)
+    md = P.MD(h, x, v, q, mass=1.0, dt=0.005, kT=1.0, tdamp=0.05, lj_sigma=1.0, lj_eps=1.0)
+    t0 = time.perf_counter()
+    md.run(steps_eq)
+    md.set_option("zhist_bins", bins)
+    md.set_option("rdf_every", every)
+    th = md.run(steps_prod)
+    dt_run = time.perf_counter() - t0
+    zh = md.get("zhist").reshape(2, bins)
+    samples = md.get("state")[4]
+    prof = zh / (samples * np.array([[n_cat], [218]]) / bins)    # density relative to the mean
+    edge = max(1, bins // 25)                                     # the outer 2 sigma on each side
+    mid = slice(bins // 2 - 5, bins // 2 + 5)
+    md.close()
+    h.close()
+    return {"system": f"Sec. 4.3 {'1:1' if valence == 1 else '2:1'} electrolyte between interfaces, gamma 0.939, "
+                      f"{Lx:g} x {Lx:g} x {Lz:g}, N = {N}, {steps_eq} + {steps_prod} steps",
+            "steps_per_s": (steps_eq + steps_prod) / dt_run,
+            "temperature_mean": float(np.mean(2 * th[:, 0] / (3 * N - 3))),
+            "cation_near_wall_over_middle": float(np.concatenate([prof[0, :edge], prof[0, -edge:]]).mean()
+                                                  / prof[0, mid].mean()),
+            "anion_near_wall_over_middle": float(np.concatenate([prof[1, :edge], prof[1, -edge:]]).mean()
+                                                 / prof[1, mid].mean()),
+            "z_bin_width": Lz / bins, "samples": int(samples),
+            "cation_profile": [round(float(v), 3) for v in prof[0]],
+            "anion_profile": [round(float(v), 3) for v in prof[1]]}
+
+
 def cores_used():
     return 1   # the oracle's pair sums are single-threaded NumPy
 
@@ -573,6 +619,8 @@ def main():
     ap.add_argument("--md-steps", type=int, default=200000, help="production steps of --md")
     ap.add_argument("--md-tdamp", type=float, default=0.01, help="thermostat damping time of --md")
     ap.add_argument("--md-eq", type=int, default=20000, help="equilibration steps of --md")
+    ap.add_argument("--md-slab", type=int, default=0, choices=[0, 1, 2],
+                    help="run the Sec. 4.3 confined-electrolyte MD with this cation valence and exit")
     ap.add_argument("--near-tree", type=int, default=0, choices=[0, 1],
                     help="1: tree evaluation of the near-field sums (option near_tree, order 10)")
     ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
@@ -605,6 +653,13 @@ def main():
         dist.barrier()
     import paper_2104_05260_gb300 as P
 
+    if args.md_slab:
+        if rank == 0:
+            print(json.dumps({"md_slab": md_e3(P, valence=args.md_slab, steps_eq=args.md_eq,
+                                               steps_prod=args.md_steps)}), flush=True)
+        if dist:
+            dist.barrier()
+        return
     if args.md:
         if rank == 0:
             print(json.dumps({"md_validation": md_e1(P, valence=args.md, steps_eq=args.md_eq,

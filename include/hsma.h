@@ -312,14 +312,18 @@ int hsma_server_step(hsma_t server);
 typedef struct hsma_md* hsma_md_t;
 
 /*
- * hsma_md_create -- start an MD loop around the 3D handle h (its box,
- * p, M, options and coulomb_prefactor, which is l_B kT in reduced units).
+ * hsma_md_create -- start an MD loop around the handle h (its box, p, M,
+ * options and coulomb_prefactor, which is l_B kT in reduced units).  With a
+ * 2D handle the loop is the confined electrolyte of Sec. 4.3: periodic in x
+ * and y, ions kept in 0 < z < Lz by shifted-truncated LJ walls at z = 0 and
+ * z = Lz (options wall_sigma 0.5, wall_eps 1.0).
  * x, v: N*3 positions and velocities; q: N charges (host or device).  Copies
  * them, wraps x into the box, computes the forces and takes the first
  * thermostat half step.  h must stay alive and must not be used for another
  * N or have its options changed while the loop exists.
- * Errors: HSMA_ERR_ARG (dims != 3, N < 2, a box side under 3 x 2^(1/6) sigma,
- * bad parameters), HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_NOMEM, HSMA_ERR_CUDA.
+ * Errors: HSMA_ERR_ARG (N < 2, a periodic box side under 3 x 2^(1/6) sigma,
+ * bad parameters), HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_OUT_OF_SLAB, HSMA_ERR_NOMEM,
+ * HSMA_ERR_CUDA.
  */
 int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, int64_t N,
                    double mass, double dt, double kT, double tdamp, double lj_sigma,
@@ -329,7 +333,10 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
  * hsma_md_set_option -- "rdf_every" (accumulate the RDF pair counts every
  * k-th step, 0 = never), "rdf_bins" (200), "rdf_rmax" (5.0, at most L/2)
  * (changing either clears the counts), "cell_capacity" (particles per LJ
- * cell, 8; a run that overflows it fails with HSMA_ERR_ARG).
+ * cell, 8; a run that overflows it fails with HSMA_ERR_ARG); slabs only:
+ * "wall_sigma", "wall_eps" (the LJ walls; the forces are recomputed),
+ * "zhist_bins" (100: the ion density histogram across the slab, taken with
+ * the RDF).
  */
 int hsma_md_set_option(hsma_md_t md, const char* key, double value);
 
@@ -337,15 +344,19 @@ int hsma_md_set_option(hsma_md_t md, const char* key, double value);
  * hsma_md_run -- advance `steps` steps and wait for them.  thermo (NULL or
  * steps*6 doubles, host or device) receives per step: kinetic energy, LJ
  * energy, Coulomb energy, xi, eta, and the conserved extended energy
- * K + U + Q xi^2/2 + g kT eta (K + U in NVE).
+ * K + U + Q xi^2/2 + g kT eta (K + U in NVE); the LJ column includes the
+ * wall energy of a slab.  A slab ion that leaves (0, Lz) fails the run with
+ * HSMA_ERR_OUT_OF_SLAB.
  */
 int hsma_md_run(hsma_md_t md, int64_t steps, double* thermo);
 
 /*
  * hsma_md_get -- copy state to the host: "x" (N*3, wrapped), "x_unwrapped",
  * "v", "forces" (LJ + Coulomb at the current positions), "rdf" (3*rdf_bins
- * pair counts: cation-anion, cation-cation, anion-anion), "state" (xi, eta,
- * last K, last U, RDF samples, velocity scale).  n is the capacity of out.
+ * pair counts: cation-anion, cation-cation, anion-anion; in a slab the
+ * minimum image is taken in x and y only), "zhist" (2*zhist_bins counts of
+ * cations then anions across 0 < z < Lz; slabs), "state" (xi, eta, last K,
+ * last U, RDF samples, velocity scale).  n is the capacity of out.
  */
 int hsma_md_get(hsma_md_t md, const char* name, double* out, int64_t n);
 

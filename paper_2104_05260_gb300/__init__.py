@@ -322,6 +322,8 @@ class MD:
         hsma_md_set_option(self.m, key, value)
         if key == "rdf_bins":
             self.rdf_bins = int(value)
+        if key == "zhist_bins":
+            self.zhist_bins = int(value)
 
     def run(self, steps):
         t = np.empty((int(steps), 6))
@@ -332,6 +334,8 @@ class MD:
         n = {"state": 6}.get(name)
         if name == "rdf":
             n = int(3 * self._rdf_bins())
+        if name == "zhist":
+            n = int(2 * getattr(self, "zhist_bins", 100))
         return hsma_md_get(self.m, name, n if n else 3 * self.N).reshape(
             (-1, 3) if name in ("x", "v", "x_unwrapped", "forces") else (-1,))
 

@@ -25,7 +25,10 @@ struct hsma_md {
   int cap = 8;
   int n_cells = 0;
   int nc[3] = {0, 0, 0};
-  DevBuf x, v, img, q, f_lj, f_c, blk_k, blk_u, sc, thermo, cells, rdf;
+  DevBuf x, v, img, q, f_lj, f_c, blk_k, blk_u, sc, thermo, cells, rdf, zhist;
+  int slab = 0;
+  double wall_sigma = 0.5, wall_eps = 1.0;
+  int zhist_bins = 100;
   long long thermo_cap = 0;
   int rdf_bins = 200;
   double rdf_rmax = 5.0;
@@ -39,7 +42,8 @@ struct hsma_md {
 hsma_md::~hsma_md() {
   if (g_step) cudaGraphExecDestroy(g_step);
   if (g_rdf) cudaGraphExecDestroy(g_rdf);
-  for (DevBuf* b : {&x, &v, &img, &q, &f_lj, &f_c, &blk_k, &blk_u, &sc, &thermo, &cells, &rdf}) b->release();
+  for (DevBuf* b : {&x, &v, &img, &q, &f_lj, &f_c, &blk_k, &blk_u, &sc, &thermo, &cells, &rdf, &zhist})
+    b->release();
 }
 
 static int md_fail(hsma_md* m, int code, const std::string& msg) {
@@ -91,6 +95,12 @@ static MdArgs md_args(hsma_md* m) {
   a.rdf = (unsigned long long*)m->rdf.p;
   a.rdf_bins = m->rdf_bins;
   a.rdf_rmax = m->rdf_rmax;
+  a.slab = m->slab;
+  a.wall_sigma = m->wall_sigma;
+  a.wall_eps = m->wall_eps;
+  a.wall_rc = std::pow(2.0, 1.0 / 6.0) * m->wall_sigma;
+  a.zhist = (unsigned long long*)m->zhist.p;
+  a.zhist_bins = m->zhist_bins;
   return a;
 }
 
@@ -152,7 +162,6 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
   if (!out) return HSMA_ERR_ARG;
   *out = nullptr;
   if (!h || h->is_server || !x || !v || !q) return HSMA_ERR_ARG;
-  if (h->gp.dims != 3) return HSMA_ERR_ARG;
   if (N < 2 || N > (int64_t)1 << 24) return HSMA_ERR_ARG;
   if (!(mass > 0) || !(dt > 0) || !(kT > 0) || !(lj_sigma > 0) || !(lj_eps >= 0) || !std::isfinite(tdamp))
     return HSMA_ERR_ARG;
@@ -166,13 +175,15 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
   m->tdamp = tdamp > 0 ? tdamp : 0.0;
   m->sigma = lj_sigma;
   m->eps = lj_eps;
+  m->slab = h->gp.dims == 2 ? 1 : 0;
   const double rc = std::pow(2.0, 1.0 / 6.0) * lj_sigma;
   for (int d = 0; d < 3; ++d) {
     m->L[d] = h->gp.box[d];
-    m->nc[d] = (int)std::floor(m->L[d] / rc);
-    if (m->nc[d] < 3) {
+    m->nc[d] = std::max(1, (int)std::floor(m->L[d] / rc));
+    // the 27-cell neighbour scheme needs 3 cells a side in periodic directions
+    if (m->nc[d] < 3 && !(m->slab && d == 2)) {
       delete m;
-      return HSMA_ERR_ARG;   // the 27-cell neighbour scheme needs 3 cells a side
+      return HSMA_ERR_ARG;
     }
   }
   m->n_cells = m->nc[0] * m->nc[1] * m->nc[2];
@@ -199,6 +210,7 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
     for (int d = 0; d < 3; ++d) {
       double& c = xh[3 * i + d];
       const double L = m->L[d];
+      if (m->slab && d == 2) continue;   // z stays inside (0, Lz): checked by the evaluation
       double w = std::floor(c / L);
       c -= w * L;
       if (c >= L) {
@@ -220,6 +232,7 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
       m->f_lj.ensure(n3 * 8) || m->f_c.ensure(n3 * 8) || m->blk_k.ensure((size_t)nb * 8) ||
       m->blk_u.ensure((size_t)hsma::md_lj_blocks((int)N) * 8) || m->sc.ensure(sizeof(MdScalars)) ||
       m->cells.ensure((size_t)m->n_cells * (1 + m->cap) * 4) || m->rdf.ensure((size_t)3 * m->rdf_bins * 8) ||
+      m->zhist.ensure((size_t)2 * m->zhist_bins * 8) ||
       ensure_thermo(m, 1)) {
     delete m;
     return HSMA_ERR_NOMEM;
@@ -235,6 +248,7 @@ int hsma_md_create(hsma_t h, const double* x, const double* v, const double* q, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->q.p, qh.data(), (size_t)N * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->sc.p, &init, sizeof(init), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->rdf.p, 0, (size_t)3 * m->rdf_bins * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->zhist.p, 0, (size_t)2 * m->zhist_bins * 8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -278,10 +292,38 @@ int hsma_md_set_option(hsma_md_t m, const char* key, double v) {
       m->rdf_rmax = v;
     }
     cudaError_t e = cudaMemsetAsync(m->rdf.p, 0, (size_t)3 * m->rdf_bins * 8, m->h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->zhist.p, 0, (size_t)2 * m->zhist_bins * 8, m->h->stream);
     MdScalars* d = (MdScalars*)m->sc.p;
     if (e == cudaSuccess) e = cudaMemsetAsync(&d->rdf_samples, 0, sizeof(long long), m->h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->h->stream);
     if (e != cudaSuccess) return md_cuda_fail(m, e, "rdf reset");
+    if (m->g_rdf) cudaGraphExecDestroy(m->g_rdf);
+    m->g_rdf = nullptr;
+    return HSMA_OK;
+  }
+  if (k == "wall_sigma" || k == "wall_eps") {
+    if (!m->slab) return md_fail(m, HSMA_ERR_ARG, k + " applies to slabs (dims 2) only");
+    if (!(v > 0) || !std::isfinite(v)) return md_fail(m, HSMA_ERR_ARG, k + " must be > 0");
+    if (k == "wall_sigma") m->wall_sigma = v;
+    else m->wall_eps = v;
+    if (m->g_step) cudaGraphExecDestroy(m->g_step);
+    if (m->g_rdf) cudaGraphExecDestroy(m->g_rdf);
+    m->g_step = m->g_rdf = nullptr;
+    // the forces of the current positions change with the walls
+    const MdArgs a = md_args(m);
+    int rc = enqueue_forces(m, a);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(m->h->stream);
+    if (e != cudaSuccess) return md_cuda_fail(m, e, "wall forces");
+    return HSMA_OK;
+  }
+  if (k == "zhist_bins") {
+    if (!(v >= 1) || v > 100000) return md_fail(m, HSMA_ERR_ARG, "zhist_bins must be in [1, 1e5]");
+    m->zhist_bins = (int)v;
+    if (m->zhist.ensure((size_t)2 * m->zhist_bins * 8)) return md_fail(m, HSMA_ERR_NOMEM, "zhist buffer");
+    cudaError_t e = cudaMemsetAsync(m->zhist.p, 0, (size_t)2 * m->zhist_bins * 8, m->h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->h->stream);
+    if (e != cudaSuccess) return md_cuda_fail(m, e, "zhist reset");
     if (m->g_rdf) cudaGraphExecDestroy(m->g_rdf);
     m->g_rdf = nullptr;
     return HSMA_OK;
@@ -324,8 +366,11 @@ int hsma_md_run(hsma_md_t m, int64_t steps, double* thermo) {
   if (e != cudaSuccess) return md_cuda_fail(m, e, "MD run");
   if (hs.flags & hsma::MD_FLAG_CELL_OVERFLOW)
     return md_fail(m, HSMA_ERR_ARG, "a cell held more particles than cell_capacity");
+  if (hs.flags & hsma::MD_FLAG_LEFT_SLAB)
+    return md_fail(m, HSMA_ERR_OUT_OF_SLAB, "an ion left the slab (0, Lz)");
   const hsma::DevScalars& r = *h->h_sc;
   if (r.flags & hsma::FLAG_NOT_NEUTRAL) return md_fail(m, HSMA_ERR_NOT_NEUTRAL, "system not neutral");
+  if (r.flags & hsma::FLAG_OUT_OF_SLAB) return md_fail(m, HSMA_ERR_OUT_OF_SLAB, "an ion left the slab (0, Lz)");
   return HSMA_OK;
 }
 
@@ -364,6 +409,15 @@ int hsma_md_get(hsma_md_t m, const char* name, double* out, int64_t n) {
     if (n < len) return md_fail(m, HSMA_ERR_ARG, "output too small");
     std::vector<unsigned long long> c((size_t)len);
     e = cudaMemcpy(c.data(), m->rdf.p, c.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return md_cuda_fail(m, e, "MD copy");
+    for (int64_t i = 0; i < len; ++i) out[i] = (double)c[i];
+    return HSMA_OK;
+  }
+  if (k == "zhist") {
+    const int64_t len = 2 * (int64_t)m->zhist_bins;
+    if (n < len) return md_fail(m, HSMA_ERR_ARG, "output too small");
+    std::vector<unsigned long long> c((size_t)len);
+    e = cudaMemcpy(c.data(), m->zhist.p, c.size() * 8, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return md_cuda_fail(m, e, "MD copy");
     for (int64_t i = 0; i < len; ++i) out[i] = (double)c[i];
     return HSMA_OK;

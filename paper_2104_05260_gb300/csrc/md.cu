@@ -40,6 +40,13 @@ __global__ void __launch_bounds__(kMdThreads) k_md_kick_drift(MdArgs a) {
     double v = a.v[k] * s + a.half_dt_m * (a.f_lj[k] + a.f_c[k]);
     double x = a.x[k] + a.dt * v;
     const double L = a.L[d];
+    if (a.slab && d == 2) {
+      // confined by the walls: no wrap; leaving (0, Lz) is an error
+      if (!(x > 0.0 && x < L)) atomicOr(&a.sc->flags, MD_FLAG_LEFT_SLAB);
+      a.v[k] = v;
+      a.x[k] = x;
+      continue;
+    }
     double w = floor(x / L);
     x -= w * L;
     // the quotient can round across an integer: bring x back into [0, L)
@@ -108,9 +115,14 @@ __global__ void __launch_bounds__(kMdThreads) k_md_lj(MdArgs a) {
     const int off[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
     int cc[3];
     double shift[3];
+    bool none = false;
     for (int d = 0; d < 3; ++d) {
       cc[d] = c0[d] + off[d];
       shift[d] = 0.0;
+      if (a.slab && d == 2) {
+        none = cc[d] < 0 || cc[d] >= a.nc[d];   // no cell beyond a wall
+        continue;
+      }
       if (cc[d] < 0) {
         cc[d] += a.nc[d];
         shift[d] = -a.L[d];
@@ -119,8 +131,8 @@ __global__ void __launch_bounds__(kMdThreads) k_md_lj(MdArgs a) {
         shift[d] = a.L[d];
       }
     }
-    const int c = (cc[2] * a.nc[1] + cc[1]) * a.nc[0] + cc[0];
-    const int n = min(a.cell_count[c], a.cap);
+    const int c = none ? 0 : (cc[2] * a.nc[1] + cc[1]) * a.nc[0] + cc[0];
+    const int n = none ? 0 : min(a.cell_count[c], a.cap);
     const int* l = a.cell_list + (size_t)c * a.cap;
     for (int k = 0; k < n; ++k) {
       const int j = l[k];
@@ -138,6 +150,17 @@ __global__ void __launch_bounds__(kMdThreads) k_md_lj(MdArgs a) {
         fy -= f * dy;
         fz -= f * dz;
       }
+    }
+    if (a.slab && lane == 0) {
+      // the two walls: distance d, force along the wall normal
+      const double dd[2] = {zi, a.L[2] - zi}, sgn[2] = {1.0, -1.0};
+      for (int wv = 0; wv < 2; ++wv)
+        if (dd[wv] < a.wall_rc) {
+          const double s2 = a.wall_sigma * a.wall_sigma / (dd[wv] * dd[wv]);
+          const double s6 = s2 * s2 * s2;
+          u += 4.0 * a.wall_eps * (s6 * s6 - s6) + a.wall_eps;
+          fz += sgn[wv] * 24.0 * a.wall_eps * (2.0 * s6 * s6 - s6) / dd[wv];
+        }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -257,7 +280,7 @@ __global__ void __launch_bounds__(kMdThreads) k_md_rdf(MdArgs a) {
     double dx = a.x[3 * (size_t)j] - xi, dy = a.x[3 * (size_t)j + 1] - yi, dz = a.x[3 * (size_t)j + 2] - zi;
     dx -= a.L[0] * rint(dx / a.L[0]);
     dy -= a.L[1] * rint(dy / a.L[1]);
-    dz -= a.L[2] * rint(dz / a.L[2]);
+    if (!a.slab) dz -= a.L[2] * rint(dz / a.L[2]);
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 < rmax2) {
       const int b = min(a.rdf_bins - 1, (int)(sqrt(r2) * scale));
@@ -268,6 +291,18 @@ __global__ void __launch_bounds__(kMdThreads) k_md_rdf(MdArgs a) {
 }
 
 __global__ void k_md_rdf_count(MdArgs a) { a.sc->rdf_samples += 1; }
+
+// ion density across the slab: counts of cations and anions in zhist_bins
+// bins over (0, Lz)
+__global__ void __launch_bounds__(kMdThreads) k_md_zhist(MdArgs a) {
+  const int i = blockIdx.x * kMdThreads + threadIdx.x;
+  if (i >= a.N) return;
+  const double qi = a.q[i];
+  if (qi == 0.0) return;
+  int b = (int)(a.x[3 * (size_t)i + 2] / a.L[2] * a.zhist_bins);
+  b = b < 0 ? 0 : (b >= a.zhist_bins ? a.zhist_bins - 1 : b);
+  atomicAdd(&a.zhist[(qi > 0.0 ? 0 : 1) * a.zhist_bins + b], 1ULL);
+}
 
 static int blocks(int n) { return (n + kMdThreads - 1) / kMdThreads; }
 
@@ -299,6 +334,7 @@ cudaError_t md_launch_start(const MdArgs& a, cudaStream_t s) {
 
 cudaError_t md_launch_rdf(const MdArgs& a, cudaStream_t s) {
   k_md_rdf<<<blocks(a.N), kMdThreads, 0, s>>>(a);
+  if (a.slab) k_md_zhist<<<blocks(a.N), kMdThreads, 0, s>>>(a);
   k_md_rdf_count<<<1, 1, 0, s>>>(a);
   return cudaGetLastError();
 }

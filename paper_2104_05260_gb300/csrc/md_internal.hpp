@@ -6,7 +6,7 @@
 
 namespace hsma {
 
-enum { MD_FLAG_CELL_OVERFLOW = 1 };
+enum { MD_FLAG_CELL_OVERFLOW = 1, MD_FLAG_LEFT_SLAB = 2 };
 constexpr int MD_THERMO_COLS = 6;   // K, U_LJ, U_coulomb, xi, eta, extended energy
 
 // Device-resident scalars of a run.
@@ -50,6 +50,11 @@ struct MdArgs {
   unsigned long long* rdf;   // 3 * rdf_bins
   int rdf_bins;
   double rdf_rmax;
+  // slab (Sec. 4.3): periodic in x, y; LJ walls at z = 0 and z = L[2]
+  int slab;
+  double wall_sigma, wall_eps, wall_rc;
+  unsigned long long* zhist;  // 2 * zhist_bins: cations, anions over (0, L[2])
+  int zhist_bins;
 };
 
 int md_blocks(int N);      // blocks of the per-particle kernels (blk_k entries)

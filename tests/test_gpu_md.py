@@ -6,6 +6,8 @@ reproducibility, NVE energy conservation and the RDF pair counts."""
 import numpy as np
 import pytest
 
+import workloads
+
 from oracle import hsma as O
 from oracle import md as OM
 
@@ -135,5 +137,58 @@ def test_md_refuses_a_replanned_handle(P):
     h.eval(x, q)
     with pytest.raises(P.HSMAError):
         md.run(1)
+    md.close()
+    h.close()
+
+
+def slab_system(n=120, box=(8.0, 8.0, 6.0), seed=5):
+    rng = np.random.default_rng(seed)
+    c = workloads.small_case(n, dims=2, box=box, seed=seed)
+    x, q = workloads.electrolyte(c, min_dist=0.9, margin=0.7)
+    v = OM.maxwell_velocities(n, 1.0, 1.0, rng)
+    return x, v, q, list(box)
+
+
+@pytest.mark.parametrize("tdamp", [0.05, 0.0])
+def test_slab_md_matches_oracle(P, tdamp):
+    # the confined electrolyte of Sec. 4.3: LJ walls, dielectric images (gamma 0.6)
+    x, v, q, box = slab_system()
+    lb, p, M, dt, steps, gam = 3.5, 6, 400, 0.004, 10, 0.6
+    h = P.HSMA(box, 2, p, M, gam, gam, precision=0, coulomb_prefactor=lb, dtn_grid=24)
+    md = P.MD(h, x, v, q, dt=dt, kT=1.0, tdamp=tdamp)
+    t = md.run(steps)
+    st = O.make_setup(box, 2, p, M, gam, gam, dtn_grid=24, prefactor=lb)
+
+    def coul(xx, qq):
+        out = O.evaluate(st, xx, qq)
+        return out["energy"], out["forces"]
+    it = OM.Integrator(coul, dt=dt, kT=1.0, tdamp=tdamp if tdamp > 0 else None)
+    s = OM.State(x, v, q, box, slab=True)
+    ref = []
+    for _ in range(steps):
+        it.step(s)
+        ref.append([s.kinetic(), s.U_lj, s.U_c, s.xi, s.eta, it.extended_energy(s)])
+    ref = np.array(ref)
+    scale = np.maximum(np.abs(ref).max(axis=0), 1.0)
+    assert np.all(np.abs(t - ref) <= 1e-9 * scale), np.abs(t - ref).max(axis=0)
+    assert np.abs(md.get("x_unwrapped") - s.unwrapped()).max() < 1e-10
+    assert np.abs(md.get("v") - s.v).max() < 1e-9
+    md.close()
+    h.close()
+
+
+def test_slab_density_histogram_counts_every_ion(P):
+    x, v, q, box = slab_system(seed=6)
+    h = P.HSMA(box, 2, 6, 400, 0.6, 0.6, precision=1, coulomb_prefactor=3.5, dtn_grid=24)
+    md = P.MD(h, x, v, q, dt=0.004, kT=1.0, tdamp=0.05)
+    md.set_option("zhist_bins", 12)
+    md.set_option("rdf_every", 5)
+    md.run(50)
+    zh = md.get("zhist").reshape(2, 12)
+    samples = int(md.get("state")[4])
+    assert samples == 10
+    assert zh[0].sum() == samples * np.sum(q > 0) and zh[1].sum() == samples * np.sum(q < 0)
+    xs = md.get("x")
+    assert np.all((xs[:, 2] > 0) & (xs[:, 2] < box[2]))
     md.close()
     h.close()
