@@ -759,6 +759,25 @@ def main():
                 "fp32_vs_fp64_rel_energy": abs(energy - float(e64[0])) / abs(float(e64[0])),
                 "fp32_vs_fp64_rel_force_rms": float(torch.sqrt((dF ** 2).sum() / (f64 ** 2).sum()))}
         h64.close()
+        # precision 2 (exact source-target differences) against the same FP64 result
+        h2 = P.HSMA(c.box, 3, c.p, c.M, precision=2)
+        P.hsma_set_stream(h2.h, stream.cuda_stream)
+        e2 = np.zeros(1)
+        f2 = torch.empty((N, 3), dtype=torch.float64, device=dev)
+        P.hsma_eval_into(h2.h, xd, qd, N, e2, f2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            P.hsma_eval_into(h2.h, xd, qd, N, e2, f2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dF2 = (f2 - f64).double()
+        fp64["precision2"] = {"evals_per_s": 5e3 / a.elapsed_time(b),
+                              "kernel": int(P.hsma_get_info(h2.h, "kernel")),
+                              "rel_energy_vs_fp64": abs(float(e2[0]) - float(e64[0])) / abs(float(e64[0])),
+                              "rel_force_rms_vs_fp64": float(torch.sqrt((dF2 ** 2).sum() / (f64 ** 2).sum()))}
+        h2.close()
 
     if rank != 0:
         if dist:

@@ -94,7 +94,12 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "n_monitor"         number of monitoring points N_m, >= (p+1)^2.
  *   "precision"         0 = FP64 pair arithmetic, 1 = FP32 pair arithmetic
  *                       with FP64-compensated accumulation (the paper's
- *                       eps_tol switch of Sec. 3.2 picks FP64 below 1e-6).
+ *                       eps_tol switch of Sec. 3.2 picks FP64 below 1e-6),
+ *                       2 = as 1 but with every source-target difference
+ *                       formed exactly: coordinates carried as FP32 hi + lo
+ *                       pairs, (hi_s - hi_t) + (lo_s - lo_t), so close pairs
+ *                       keep FP32 relative accuracy however large the box
+ *                       (about 1.2 x the cost of 1).
  *   "dtn_grid"          G, grid points per side on each 2D face (>= 4).
  *   "coulomb_prefactor" multiplies energy, forces and potential.
  *   "timing"            1 = record per-phase CUDA-event times (hsma_get_info).
@@ -104,8 +109,10 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       the near/check launch for a few kernel variants and
  *                       chunk counts and keep the fastest (cached per process
  *                       by N and check-point count); 0 = fixed heuristic.
- *   "targets_per_thread" kernel variant: 1, 2, 4 (scalar FP32) or 12, 14
- *                       (packed FP32x2, 2 or 4 targets); turns autotune off.
+ *   "targets_per_thread" kernel variant: 1, 2, 4 (scalar FP32), 12, 14
+ *                       (packed FP32x2, 2 or 4 targets), 24 (packed, sums in
+ *                       shared memory) or 32, 34 (exact differences, 2 or 4
+ *                       targets; precision 2); turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
  *   "sphere_mask"       1 (default) = the near set is the images inside the

@@ -111,7 +111,7 @@ hsma_ctx::~hsma_ctx() {
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
                     &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2, &d_tkey_s,
                     &d_tcnt_s, &d_tstart_s, &d_tcur_s, &d_tord_s, &d_tkey_t, &d_tcnt_t, &d_tstart_t, &d_tcur_t,
-                    &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac})
+                    &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac, &d_src32lo, &d_tgt32lo})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -295,12 +295,20 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
 
 int mask_words(const Geometry& g) { return std::max<int>(1, ((int)g.shifts.size() - 1 + 31) / 32); }
 
+// Pair-kernel variant code for the handle's precision: FP64 has one; the
+// exact-difference path (precision 2) runs the hi/lo variants 32 or 34.
+static int eff_tpt(const hsma_ctx* h) {
+  if (h->precision == 0) return 1;
+  if (h->precision == 2) return (h->tpt == 32 || h->tpt == 34) ? h->tpt : 34;
+  return h->tpt;
+}
+
 // Launch plan and buffers for N particles.
 int ensure_plan(hsma_ctx* h, int64_t N) {
   if (h->plan_N == N) return HSMA_OK;
   const Geometry& g = h->geo;
   const int prec = h->precision;
-  const int tpt = (prec == 0) ? 1 : h->tpt;
+  const int tpt = eff_tpt(h);
   const int tile = pair_tile_targets(prec, tpt);
   const int slots = pair_slots(prec, tpt);
   h->n_tgt1 = (int)N + g.n_check;
@@ -330,6 +338,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   else
     bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16) ||
           h->d_ioff.ensure(n * 4) || h->d_self.ensure(n * 32);
+  if (prec == 2) bad = bad || h->d_src32lo.ensure(simg * 16) || h->d_tgt32lo.ensure(nt * 16);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
   if (h->near_tree) {
     if (prec == 0) return fail(h, HSMA_ERR_ARG, "near_tree needs precision 1 (FP32 pair arithmetic)");
@@ -377,6 +386,8 @@ int stage_prep(hsma_ctx* h, int64_t N) {
   a.sc = (DevScalars*)h->d_sc.p;
   a.src32 = prec ? (float4*)h->d_src32.p : nullptr;
   a.tgt32 = prec ? (float4*)h->d_tgt32.p : nullptr;
+  a.src32lo = prec == 2 ? (float4*)h->d_src32lo.p : nullptr;
+  a.tgt32lo = prec == 2 ? (float4*)h->d_tgt32lo.p : nullptr;
   a.src64 = prec ? nullptr : (double4_32a*)h->d_src64.p;
   a.tgt64 = prec ? nullptr : (double4_32a*)h->d_tgt64.p;
   a.ioff = prec ? (int*)h->d_ioff.p : nullptr;
@@ -408,6 +419,8 @@ PairArgs near_args(hsma_ctx* h, int64_t N) {
   p1.ld = h->n_tgt1;
   p1.ioff = prec ? (const int*)h->d_ioff.p : nullptr;
   p1.icnt = prec ? (const int*)h->d_cnt.p : nullptr;
+  p1.src_lo = prec == 2 ? (const float4*)h->d_src32lo.p : nullptr;
+  p1.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;
   return p1;
 }
 
@@ -446,6 +459,7 @@ PairArgs far_args(hsma_ctx* h, int64_t N) {
   p2.n_chunks = h->chunks2;
   p2.part = (double*)h->d_fpart.p;
   p2.ld = (int)N;
+  p2.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;   // surface charges: no lo part
   return p2;
 }
 
@@ -473,7 +487,7 @@ int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) 
 // Enqueue one evaluation on h->stream; inputs already in d_x, d_q.
 int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   const int prec = h->precision;
-  const int tpt = (prec == 0) ? 1 : h->tpt;
+  const int tpt = eff_tpt(h);
   cudaStream_t s = h->stream;
   const bool tm = h->timing != 0;
   if (tm) cudaEventRecord(h->ev[0], s);
@@ -551,14 +565,15 @@ static int tune_near(hsma_ctx* h, int64_t N) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      if (prec) h->tpt = it->second.first;
+      if (prec) h->tpt = it->second.first;   // (the cache key holds the precision)
       h->tuned_chunks = std::max(1, it->second.second);
       h->tuned_N = N;
       h->plan_N = -1;
       return ensure_plan(h, N);
     }
   }
-  std::vector<int> tpts = prec ? std::vector<int>{12, 14, 24, 1} : std::vector<int>{1};
+  std::vector<int> tpts = prec == 2 ? std::vector<int>{32, 34}
+                         : prec ? std::vector<int>{12, 14, 24, 1} : std::vector<int>{1};
   struct Cand { int tpt, chunks; float ms; };
   std::vector<Cand> cands;
   int maxc = 1;
@@ -722,8 +737,9 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->gp.n_monitor = (int)v;
     h->geo_dirty = true;
   } else if (k == "precision") {
-    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "precision must be 0 or 1");
+    if (v != 0 && v != 1 && v != 2) return fail(h, HSMA_ERR_ARG, "precision must be 0, 1 or 2");
     h->precision = (int)v;
+    if (v == 1 && h->tpt >= 30) h->tpt = 12;   // back from the exact-difference variants
     h->tuned_N = -1;
     h->tuned_chunks = 0;
     h->plan_N = -1;
@@ -782,8 +798,9 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->tuned_chunks = 0;
     h->plan_N = -1;
   } else if (k == "targets_per_thread") {
-    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14 && v != 24)
-      return fail(h, HSMA_ERR_ARG, "targets_per_thread must be 1, 2, 4 (scalar), 12, 14 or 24 (packed)");
+    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14 && v != 24 && v != 32 && v != 34)
+      return fail(h, HSMA_ERR_ARG,
+                  "targets_per_thread must be 1, 2, 4 (scalar), 12, 14, 24 (packed) or 32, 34 (exact differences)");
     h->tpt = (int)v;
     h->autotune = 0;          // an explicit kernel choice turns tuning off
     h->tuned_N = -1;
@@ -839,14 +856,14 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "t_far_ms") *value = h->times[4];
   else if (k == "t_assemble_ms") *value = h->times[5];
   else if (k == "chunks") *value = h->chunks1;
-  else if (k == "kernel") *value = h->precision ? h->tpt : 0;
+  else if (k == "kernel") *value = h->precision ? eff_tpt(h) : 0;
   else if (k == "far_chunks") *value = h->far_series ? 1 : h->chunks2;
   else if (k == "far_field") *value = h->far_series;
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;
-  else if (k == "tile_targets") *value = pair_tile_targets(h->precision, h->precision ? h->tpt : 1);
+  else if (k == "tile_targets") *value = pair_tile_targets(h->precision, eff_tpt(h));
   else return fail(h, HSMA_ERR_ARG, "unknown info key " + k);
   return HSMA_OK;
 }

@@ -41,6 +41,8 @@ struct PrepArgs {
   double4_32a* src64;        // images: FP64 path, or NULL
   float4* tgt32;         // targets: N particles then n_check check points
   double4_32a* tgt64;
+  float4* src32lo;       // x - (float)x of the images (exact-difference path), or NULL
+  float4* tgt32lo;       // the same for the targets, or NULL
   int* ioff;             // N: first section-1 image of each ion, or NULL
   unsigned* mask;        // N x mwords: bit s-1 set when shift s puts the ion's image in B
   int mwords;            // ceil((n_shift - 1) / 32)
@@ -64,6 +66,11 @@ struct PairArgs {
   // [ioff[t], ioff[t] + icnt[t]); those terms are added in FP64 elsewhere.
   const int* ioff = nullptr;
   const int* icnt = nullptr;
+  // exact-difference variants: the FP32 rounding remainders x - (float)x of
+  // the sources and targets (null = zero), so that x_s - x_t is formed as
+  // (hi_s - hi_t) + (lo_s - lo_t)
+  const float4* src_lo = nullptr;
+  const float4* tgt_lo = nullptr;
 };
 
 struct PairPlan {

@@ -203,6 +203,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
         a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
         a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
       }
+      if (a.src32lo) {
+        const float4 lo = make_float4((float)(xc - (double)(float)xc), (float)(yc - (double)(float)yc),
+                                      (float)(zc - (double)(float)zc), 0.f);
+        a.src32lo[j] = lo;
+        a.tgt32lo[j] = lo;
+      }
       if (a.src64) {
         a.src64[j] = make_double4_32a(xc, yc, zc, qj);
         a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
@@ -222,6 +228,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
         const int k = o + __popc(m & ((1u << lane) - 1u));
         const double qs = sh[4] * qj;
         if (a.src32) a.src32[k] = make_float4((float)px, (float)py, (float)pz, (float)qs);
+        if (a.src32lo)
+          a.src32lo[k] = make_float4((float)(px - (double)(float)px), (float)(py - (double)(float)py),
+                                     (float)(pz - (double)(float)pz), 0.f);
         if (a.src64) a.src64[k] = make_double4_32a(px, py, pz, qs);
         if (a.self) {
           const double dx = px - xc, dy = py - yc, dz = pz - zc;
@@ -256,6 +265,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
     const double* cp = a.check_pts + 3 * (size_t)t;
     const double c0 = a.cscale * cp[0], c1 = a.cscale * cp[1], c2 = a.cscale * cp[2];
     if (a.tgt32) a.tgt32[a.N + t] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
+    if (a.tgt32lo)
+      a.tgt32lo[a.N + t] = make_float4((float)(c0 - (double)(float)c0), (float)(c1 - (double)(float)c1),
+                                       (float)(c2 - (double)(float)c2), 0.f);
     if (a.tgt64) a.tgt64[a.N + t] = make_double4_32a(c0, c1, c2, 0.0);
   }
 }

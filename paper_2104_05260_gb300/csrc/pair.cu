@@ -426,6 +426,156 @@ __device__ __forceinline__ void pair_item_f32x2s(const PairArgs& a, int item, fl
   }
 }
 
+// Exact-difference variant (precision 2): each coordinate is carried as an
+// FP32 pair hi + lo (lo = x - (float)x, written by the prep in FP64), and the
+// difference of a source and a target is (hi_s - hi_t) + (lo_s - lo_t).  For
+// close pairs hi_s - hi_t is exact, so the difference has FP32 relative
+// accuracy however large the coordinates; the rest of the arithmetic is that
+// of k_pair_f32x2.  A null lo array stands for zeros (surface charges).
+template <int NP>
+__device__ __forceinline__ void pair_item_f32x2x(const PairArgs& a, int item, float4* sh) {
+  const float4* __restrict__ tgt = (const float4*)a.tgt;
+  const float4* __restrict__ src = (const float4*)a.src;
+  constexpr int TPT = 2 * NP;
+  const int ns = a.sc ? a.sc->Ns : a.n_src;
+  int per = (ns + a.n_chunks - 1) / a.n_chunks;
+  per = (per + kTile32 - 1) / kTile32 * kTile32;
+  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  const int t0 = tile * kPairThreads * TPT;
+  float2 nx[NP], ny[NP], nz[NP], mx[NP], my[NP], mz[NP];   // -hi, -lo of the targets
+  float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+    const int tb = ta + kPairThreads;
+    const float4 va = (ta < a.n_tgt) ? tgt[ta] : make_float4(kFar, kFar, kFar, 0.f);
+    const float4 vb = (tb < a.n_tgt) ? tgt[tb] : make_float4(kFar, kFar, kFar, 0.f);
+    const float4 la = (a.tgt_lo && ta < a.n_tgt) ? a.tgt_lo[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 lb = (a.tgt_lo && tb < a.n_tgt) ? a.tgt_lo[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    nx[k] = make_float2(-va.x, -vb.x);
+    ny[k] = make_float2(-va.y, -vb.y);
+    nz[k] = make_float2(-va.z, -vb.z);
+    mx[k] = make_float2(-la.x, -lb.x);
+    my[k] = make_float2(-la.y, -lb.y);
+    mz[k] = make_float2(-la.z, -lb.z);
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) hp[k] = lp[k] = hx[k] = lx[k] = hy[k] = ly[k] = hz[k] = lz[k] = 0.f;
+  int so[TPT], sc[TPT];   // own section-1 image range of each ion target
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    const int t = t0 + threadIdx.x + k * kPairThreads;
+    const bool ion = a.ioff && t < a.n_diag;
+    so[k] = ion ? a.ioff[t] : 0;
+    sc[k] = ion ? a.icnt[t] : 0;
+  }
+  int lo1 = 0, hi1 = 0;
+  own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
+  const int s0 = chunk * per;
+  const int s1 = min(ns, s0 + per);
+  for (int sb = s0; sb < s1; sb += kTile32) {
+    const int n = min(kTile32, s1 - sb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kPairThreads) {
+      const float4 v = src[sb + i];
+      const float4 l = a.src_lo ? a.src_lo[sb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sh[4 * i] = make_float4(v.x, v.x, v.y, v.y);
+      sh[4 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
+      sh[4 * i + 2] = make_float4(l.x, l.x, l.y, l.y);
+      sh[4 * i + 3] = make_float4(l.z, l.z, 0.f, 0.f);
+    }
+    __syncthreads();
+    float2 p[NP], gx[NP], gy[NP], gz[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) p[k] = gx[k] = gy[k] = gz[k] = make_float2(0.f, 0.f);
+    // tiles that hold no identity or own image of these targets skip the checks
+    const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
+                      (sb < hi1 && lo1 < sb + n);
+    if (!diag) {
+#pragma unroll kUnroll
+      for (int i = 0; i < n; ++i) {
+        const float4 A = sh[4 * i], B = sh[4 * i + 1], Cl = sh[4 * i + 2], Dl = sh[4 * i + 3];
+        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+        const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+        const float2 tx = make_float2(Cl.x, Cl.y), ty = make_float2(Cl.z, Cl.w), tz = make_float2(Dl.x, Dl.y);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float2 dx = __fadd2_rn(__fadd2_rn(sx, nx[k]), __fadd2_rn(tx, mx[k]));
+          const float2 dy = __fadd2_rn(__fadd2_rn(sy, ny[k]), __fadd2_rn(ty, my[k]));
+          const float2 dz = __fadd2_rn(__fadd2_rn(sz, nz[k]), __fadd2_rn(tz, mz[k]));
+          float2 r2 = __fmul2_rn(dx, dx);
+          r2 = __ffma2_rn(dy, dy, r2);
+          r2 = __ffma2_rn(dz, dz, r2);
+          const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+          const float2 qi = __fmul2_rn(sq, inv);
+          p[k] = __fadd2_rn(p[k], qi);
+          const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+          gx[k] = __ffma2_rn(q3, dx, gx[k]);
+          gy[k] = __ffma2_rn(q3, dy, gy[k]);
+          gz[k] = __ffma2_rn(q3, dz, gz[k]);
+        }
+      }
+    } else
+    for (int i = 0; i < n; ++i) {
+      const float4 A = sh[4 * i], B = sh[4 * i + 1], Cl = sh[4 * i + 2], Dl = sh[4 * i + 3];
+      const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+      const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+      const float2 tx = make_float2(Cl.x, Cl.y), ty = make_float2(Cl.z, Cl.w), tz = make_float2(Dl.x, Dl.y);
+      const int sidx = sb + i;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+        const int tb = ta + kPairThreads;
+        const float2 dx = __fadd2_rn(__fadd2_rn(sx, nx[k]), __fadd2_rn(tx, mx[k]));
+        const float2 dy = __fadd2_rn(__fadd2_rn(sy, ny[k]), __fadd2_rn(ty, my[k]));
+        const float2 dz = __fadd2_rn(__fadd2_rn(sz, nz[k]), __fadd2_rn(tz, mz[k]));
+        float2 r2 = __fmul2_rn(dx, dx);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dz, dz, r2);
+        // an ion skips its identity image and its own shifted images
+        const bool owna = (sidx == ta && ta < a.n_diag) || (unsigned)(sidx - so[2 * k]) < (unsigned)sc[2 * k];
+        const bool ownb = (sidx == tb && tb < a.n_diag) || (unsigned)(sidx - so[2 * k + 1]) < (unsigned)sc[2 * k + 1];
+        const float2 inv = make_float2(owna ? 0.f : rsqrtf(r2.x), ownb ? 0.f : rsqrtf(r2.y));
+        const float2 qi = __fmul2_rn(sq, inv);
+        p[k] = __fadd2_rn(p[k], qi);
+        const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+        gx[k] = __ffma2_rn(q3, dx, gx[k]);
+        gy[k] = __ffma2_rn(q3, dy, gy[k]);
+        gz[k] = __ffma2_rn(q3, dz, gz[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      two_sum_add(hp[2 * k], lp[2 * k], p[k].x);
+      two_sum_add(hp[2 * k + 1], lp[2 * k + 1], p[k].y);
+      two_sum_add(hx[2 * k], lx[2 * k], gx[k].x);
+      two_sum_add(hx[2 * k + 1], lx[2 * k + 1], gx[k].y);
+      two_sum_add(hy[2 * k], ly[2 * k], gy[k].x);
+      two_sum_add(hy[2 * k + 1], ly[2 * k + 1], gy[k].y);
+      two_sum_add(hz[2 * k], lz[2 * k], gz[k].x);
+      two_sum_add(hz[2 * k + 1], lz[2 * k + 1], gz[k].y);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    const int t = t0 + threadIdx.x + k * kPairThreads;
+    if (t < a.n_tgt) {
+      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+      o[0] = (double)hp[k] + (double)lp[k];
+      o[(size_t)a.ld] = (double)hx[k] + (double)lx[k];
+      o[2 * (size_t)a.ld] = (double)hy[k] + (double)ly[k];
+      o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads) k_pair_f32x2x(PairArgs a) {
+  __shared__ float4 sh[4 * kTile32];
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2x<NP>(a, item, sh);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2s(PairArgs a) {
   __shared__ float4 sh[2 * kTile32];
@@ -530,7 +680,7 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
 // 24 = packed, 4 targets, compensated sums in shared memory.
 int pair_tile_targets(int precision, int tpt) {
   if (precision == 0) return kPairThreads;
-  return kPairThreads * (tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);
+  return kPairThreads * (tpt > 30 ? tpt - 30 : tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);
 }
 
 static const void* pair_fn(int precision, int tpt) {
@@ -541,6 +691,8 @@ static const void* pair_fn(int precision, int tpt) {
     case 12: return (const void*)k_pair_f32x2<1>;
     case 14: return (const void*)k_pair_f32x2<2>;
     case 24: return (const void*)k_pair_f32x2s<2>;
+    case 32: return (const void*)k_pair_f32x2x<1>;
+    case 34: return (const void*)k_pair_f32x2x<2>;
     default: return (const void*)k_pair_f32<4>;
   }
 }
@@ -563,6 +715,8 @@ cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream
   else if (tpt == 12) k_pair_f32x2<1><<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 14) k_pair_f32x2<2><<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 24) k_pair_f32x2s<2><<<grid, kPairThreads, kAccBytes2, s>>>(a);
+  else if (tpt == 32) k_pair_f32x2x<1><<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 34) k_pair_f32x2x<2><<<grid, kPairThreads, 0, s>>>(a);
   else k_pair_f32<4><<<grid, kPairThreads, 0, s>>>(a);
   return cudaGetLastError();
 }

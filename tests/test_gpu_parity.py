@@ -15,8 +15,10 @@ from oracle import hsma as O
 
 pytestmark = pytest.mark.gpu
 
-E_TOL = {0: 1e-6, 1: 1e-5}
-F_TOL = {0: 1e-6, 1: 2e-5}      # relative RMS of the per-ion forces
+# precision 2 is an FP32-compute path (exact differences): the FP32 bounds;
+# its gain at large coordinates is checked at the bench size below
+E_TOL = {0: 1e-6, 1: 1e-5, 2: 1e-5}
+F_TOL = {0: 1e-6, 1: 2e-5, 2: 2e-5}      # relative RMS of the per-ion forces
 
 
 @pytest.fixture(scope="module")
@@ -76,14 +78,14 @@ def check_full(P, c, x, q, prec, st=None, **opt):
     return E, ref
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_cfg1_full(P, prec):
     c = workloads.case(1)                          # N = 1000, L = 10, p = 6, M = 800
     x, q = workloads.electrolyte(c)
     check_full(P, c, x, q, prec)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("N,val", [(2, (1, -1)), (3, (2, -1)), (258, (1, -1)), (1001, (2, -1)),
                                    (2050, (3, -1))])
 def test_ragged_and_tiny_sizes(P, prec, N, val):
@@ -117,7 +119,7 @@ def test_literal_sphere_radius_125_cells(P, prec):
     check_full(P, c, x, q, prec, st=st, **{"lambda": 2.6, "n_monitor": 200})
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.0, 0.0), (0.95, 0.95), (0.6, 0.0)])
 def test_2d_small(P, prec, gam):
     c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam,
@@ -127,7 +129,7 @@ def test_2d_small(P, prec, gam):
     # FP32 path sums every ion's own images in FP64, so only FP32 pairs of two
     # different ions that are both that close limit it.
     x, q = workloads.electrolyte(c)
-    d = 1e-6 if prec == 0 else 1e-3
+    d = 1e-3 if prec == 1 else 1e-6
     x[0, 2] = d                          # bottom wall
     x[1, 2] = 10.0 - d                   # top wall
     check_full(P, c, x, q, prec, dtn_grid=24)
@@ -150,6 +152,25 @@ def test_unmasked_near_set_2d(P, prec):
     x, q = workloads.electrolyte(c, margin=1e-3)
     st = O.make_setup(c.box, 2, c.p, c.M, 0.5, -0.3, lam=c.lam, dtn_grid=24, sphere_mask=False)
     check_full(P, c, x, q, prec, st=st, dtn_grid=24, sphere_mask=0)
+
+
+def test_exact_differences_close_the_fp32_gap_at_bench_size(P):
+    # precision 2 against the FP64 path at N = 1e5: the close-pair force error
+    # of plain FP32 (coordinates rounded at |x| ~ 50) is gone
+    c = workloads.case(2)
+    x, q = workloads.electrolyte(c)
+    res = {}
+    for prec in (0, 1, 2):
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=prec)
+        E, F, _ = h.eval(x, q)
+        res[prec] = (E, F)
+        h.close()
+    e1, e2 = (rel(res[k][0], res[0][0]) for k in (1, 2))
+    f1, f2 = (frms(res[k][1], res[0][1]) for k in (1, 2))
+    # forces: the close-pair error goes; the energy (which nearly cancels:
+    # E = -2384 for 1e5 ions) keeps the FP32 bound
+    assert f2 <= 2e-6 and e2 <= 1e-5, (f2, e2)
+    assert f2 < 0.1 * f1
 
 
 def test_errors_are_reported(P):
