@@ -167,7 +167,7 @@ def oracle_sample(c, x, q, n_targets, seed=99, n_check=None, st=None):
                         t_targets=t3 - t2, Ns=len(iq))
 
 
-def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None):
+def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None, precision=1):
     """Served workload: independent HSMA3D requests, Poisson arrivals.
 
     Requests: neutral +-1 electrolytes at density 0.1, N log-uniform in
@@ -199,7 +199,7 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
             h.close()
         return res
 
-    r32 = one_at_a_time(1, sample)
+    r32 = one_at_a_time(precision, sample)
     r64 = one_at_a_time(0, sample)
     # the sample is stratified by N: scale its mean to the whole stream
     t32 = np.mean([r32[i][0] for i in sample])
@@ -207,7 +207,7 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     rate = 0.8 / t32
     arrivals = workloads.poisson_arrivals(n_req, rate, seed=seed)
 
-    server = P.hsma_server_create(slots, budget, 1)
+    server = P.hsma_server_create(slots, budget, precision)
     for p in (6, 8, 10):                       # build the three unit geometries, untimed
         c, x, q = next(r for r in reqs if r[0].p == p)
         t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
@@ -250,11 +250,12 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     df = [math.sqrt(np.mean(np.sum((out[i][1] - r64[i][2]) ** 2, 1)) / np.mean(np.sum(r64[i][2] ** 2, 1)))
           for i in sample]
     return {"workload": f"{n_req} requests, N log-uniform [1e3, 5e4], p in {{6,8,10}}, M = 4p^2+400, "
-                        f"rho = 0.1, Poisson arrivals at {rate:.1f}/s (0.8 x one-at-a-time FP32 capacity)",
-            "slots": slots, "budget_bytes": budget,
+                        f"rho = 0.1, Poisson arrivals at {rate:.1f}/s (0.8 x the one-at-a-time capacity "
+                        f"at precision {precision})",
+            "precision": precision, "slots": slots, "budget_bytes": budget,
             "evals_per_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_N": float(np.mean([c.N for c, _, _ in reqs])),
-            "one_at_a_time_fp64_evals_per_s": 1.0 / t64, "one_at_a_time_fp32_evals_per_s": 1.0 / t32,
+            "one_at_a_time_fp64_evals_per_s": 1.0 / t64, "one_at_a_time_evals_per_s": 1.0 / t32,
             "served_vs_fp64": (n_req / span) * t64,
             "sample": f"{n_sample} requests stratified by N, timed one at a time",
             "max_rel_energy_err_vs_fp64": float(max(de)),
@@ -842,6 +843,7 @@ def main():
             "rel_energy_vs_fp64_gpu": fp64["fp32_vs_fp64_rel_energy"] if fp64 else None}
     if not args.no_serve:
         line["serve"] = serve_bench(P)
+        line["serve_precision2"] = serve_bench(P, precision=2)
     if not args.no_other_cases:
         if not args.far_field and not args.near_tree:
             line["far_field_series"] = far_series_compare(P, torch, stream, c, xd, qd, fd, h)

@@ -275,7 +275,7 @@ const char* hsma_last_error(hsma_t h);
  *
  * hsma_server_create -- a request loop with at most `slots` requests on the
  * device at once and `budget_bytes` of device memory for their state.
- * precision as for hsma_set_option.  Requests that arrive while others run
+ * precision as for hsma_set_option (0, 1 or 2).  Requests that arrive while others run
  * are admitted as slots and memory free up; their pair sums share launches.
  * Each request's result is identical to an evaluation of it alone.
  */

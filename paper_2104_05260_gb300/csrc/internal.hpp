@@ -87,10 +87,10 @@ cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream
 int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
 // One launch over several packed-FP32 pair sums (descs and start in device
 // memory; start has n_desc + 1 entries, start[n_desc] = total items).
-cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
+cudaError_t launch_pair_ragged(int precision, const PairArgs* descs, const int* start, int n_desc, int grid,
                                cudaStream_t s);
-int pair_ragged_slots();
-int pair_ragged_variant();   // kernel code the ragged launch runs (plan tiles with it)
+int pair_ragged_slots(int precision);
+int pair_ragged_variant(int precision);   // kernel code the ragged launch runs (plan tiles with it)
 // Far field as the fitted series itself (no surface charges): out[c*N + i],
 // c = phi, grad; norm[n*(p+1) + m] = c_n0 (m = 0), sqrt(2) c_nm (2m-1)!! (m > 0)
 // with c_nm the orthonormal harmonic normalisation; A as the fit writes it.

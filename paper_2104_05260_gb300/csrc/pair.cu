@@ -612,20 +612,36 @@ __global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged(const PairArgs*
   }
 }
 
-int pair_ragged_variant() { return 12; }
+// The same ragged launch for precision 2 (exact differences), 512-target tiles.
+__global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged_x(const PairArgs* __restrict__ descs,
+                                                                  const int* __restrict__ start,
+                                                                  int n_desc) {
+  __shared__ float4 sh[4 * kTile32];
+  const int total = start[n_desc];
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int d = 0;
+    while (d + 1 < n_desc && start[d + 1] <= item) ++d;
+    const PairArgs a = descs[d];
+    pair_item_f32x2x<1>(a, item - start[d], sh);
+  }
+}
 
-cudaError_t launch_pair_ragged(const PairArgs* descs, const int* start, int n_desc, int grid,
+int pair_ragged_variant(int precision) { return precision == 2 ? 32 : 12; }
+
+cudaError_t launch_pair_ragged(int precision, const PairArgs* descs, const int* start, int n_desc, int grid,
                                cudaStream_t s) {
   if (grid < 1) grid = 1;
-  k_pair_ragged<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
+  if (precision == 2) k_pair_ragged_x<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
+  else k_pair_ragged<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
   return cudaGetLastError();
 }
 
-int pair_ragged_slots() {
+int pair_ragged_slots(int precision) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged, kPairThreads, 0);
+  if (precision == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged_x, kPairThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged, kPairThreads, 0);
   return sms * (per < 1 ? 1 : per);
 }
 

@@ -104,7 +104,7 @@ static void free_request(Request* r) {
 // inputs and per-ion arrays, images in B, targets, partial sums, outputs.
 static size_t request_bytes(int64_t N, const double box[3], int p, int M, int precision) {
   const double ns = 27.0 * (double)N;   // every image of the 27 cells, the most B can hold
-  const double img = precision ? 16.0 : 32.0;
+  const double img = precision == 1 ? 16.0 : 32.0;   // FP32 (x, y, z, q); FP64 or hi + lo
   const double nck = 4.0 * (p + 1) * (p + 1);
   const double chunks = 64.0;   // generous bound on source chunks per tile
   return (size_t)(ns * img + (N + nck) * (img + 32.0 * chunks) + N * 200.0 + (double)M * 64);
@@ -234,7 +234,7 @@ static int launch_batch(Server* s, BatchBuf& bb) {
         int rc = stage_fit(s->slots[r->slot].ctx, r->N);
         if (rc) return rc;
       }
-    if (s->precision == 1) {
+    if (s->precision >= 1) {
       PairArgs* d = bb.h_desc + phase * (int)s->slots.size();
       int* start = bb.h_start + phase * ((int)s->slots.size() + 1);
       int items = 0;
@@ -250,7 +250,8 @@ static int launch_batch(Server* s, BatchBuf& bb) {
       int* ds = (int*)bb.d_start.p + phase * ((int)s->slots.size() + 1);
       cudaError_t e = cudaMemcpyAsync(dd, d, sizeof(PairArgs) * n, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ds, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess) e = launch_pair_ragged(dd, ds, n, std::min(items, s->ragged_slots), st);
+      if (e == cudaSuccess)
+        e = launch_pair_ragged(s->precision, dd, ds, n, std::min(items, s->ragged_slots), st);
       if (e != cudaSuccess) return HSMA_ERR_CUDA;
     } else {
       for (Request* r : bb.reqs) {
@@ -367,7 +368,7 @@ extern "C" {
 int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* out) {
   if (!out) return HSMA_ERR_ARG;
   *out = nullptr;
-  if (slots < 1 || slots > 64 || !(budget_bytes > 0) || (precision != 0 && precision != 1))
+  if (slots < 1 || slots > 64 || !(budget_bytes > 0) || precision < 0 || precision > 2)
     return HSMA_ERR_ARG;
   hsma_ctx* h = new (std::nothrow) hsma_ctx();
   if (!h) return HSMA_ERR_NOMEM;
@@ -378,14 +379,14 @@ int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* ou
   s->budget = budget_bytes;
   int rc = HSMA_OK;
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) rc = HSMA_ERR_CUDA;
-  if (rc == HSMA_OK) s->ragged_slots = pair_ragged_slots();
+  if (rc == HSMA_OK) s->ragged_slots = pair_ragged_slots(precision);
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
     if (rc != HSMA_OK) break;
     sl.ctx = new hsma_ctx();
     sl.ctx->precision = precision;
     sl.ctx->autotune = 0;                      // a request's plan depends only on the request
-    if (precision) sl.ctx->tpt = pair_ragged_variant();
+    if (precision) sl.ctx->tpt = pair_ragged_variant(precision);
     rc = hsma_ctx_init(sl.ctx);
     if (rc == HSMA_OK) {
       cudaStreamDestroy(sl.ctx->stream);
