@@ -632,7 +632,7 @@ def main():
         print(json.dumps(record_traffic(
             args.record_traffic, "k_pair_f32x2s<2> near field + check points", "hsma3d_n100000_rho0.1_p8_M2000",
             46, "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                "--clock-control none -k regex:k_pair -s 23 -c 1 --csv --log-file near_traffic.csv "
+                "--clock-control none -k regex:k_pair -s 33 -c 1 --csv --log-file near_traffic.csv "
                 "python bench.py --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --no-serve "
                 "--no-other-cases")))
         return
