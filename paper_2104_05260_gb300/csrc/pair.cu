@@ -576,6 +576,149 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32x2x(PairArgs a) {
   for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2x<NP>(a, item, sh);
 }
 
+// Exact differences (as in pair_item_f32x2x) with the compensated sums in
+// shared memory (as in pair_item_f32x2s), for a lower register count.
+template <int NP>
+__device__ __forceinline__ void pair_item_f32x2xs(const PairArgs& a, int item, float4* sh, float* acc) {
+  const float4* __restrict__ tgt = (const float4*)a.tgt;
+  const float4* __restrict__ src = (const float4*)a.src;
+  constexpr int TPT = 2 * NP;
+  const int ns = a.sc ? a.sc->Ns : a.n_src;
+  int per = (ns + a.n_chunks - 1) / a.n_chunks;
+  per = (per + kTile32 - 1) / kTile32 * kTile32;
+  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  const int t0 = tile * kPairThreads * TPT;
+  float2 nx[NP], ny[NP], nz[NP], mx[NP], my[NP], mz[NP];   // -hi, -lo of the targets
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+    const int tb = ta + kPairThreads;
+    const float4 va = (ta < a.n_tgt) ? tgt[ta] : make_float4(kFar, kFar, kFar, 0.f);
+    const float4 vb = (tb < a.n_tgt) ? tgt[tb] : make_float4(kFar, kFar, kFar, 0.f);
+    const float4 la = (a.tgt_lo && ta < a.n_tgt) ? a.tgt_lo[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 lb = (a.tgt_lo && tb < a.n_tgt) ? a.tgt_lo[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    nx[k] = make_float2(-va.x, -vb.x);
+    ny[k] = make_float2(-va.y, -vb.y);
+    nz[k] = make_float2(-va.z, -vb.z);
+    mx[k] = make_float2(-la.x, -lb.x);
+    my[k] = make_float2(-la.y, -lb.y);
+    mz[k] = make_float2(-la.z, -lb.z);
+  }
+  // acc[(8*k + c) * kPairThreads + tid]: c = 2*component + (0 hi, 1 lo), target slot k
+#pragma unroll
+  for (int r = 0; r < 8 * TPT; ++r) acc[r * kPairThreads + threadIdx.x] = 0.f;
+  int lo1 = 0, hi1 = 0;
+  own_range(a, t0, kPairThreads * TPT, &lo1, &hi1);
+  const int s0 = chunk * per;
+  const int s1 = min(ns, s0 + per);
+  for (int sb = s0; sb < s1; sb += kTile32) {
+    const int n = min(kTile32, s1 - sb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kPairThreads) {
+      const float4 v = src[sb + i];
+      const float4 l = a.src_lo ? a.src_lo[sb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sh[4 * i] = make_float4(v.x, v.x, v.y, v.y);
+      sh[4 * i + 1] = make_float4(v.z, v.z, v.w, v.w);
+      sh[4 * i + 2] = make_float4(l.x, l.x, l.y, l.y);
+      sh[4 * i + 3] = make_float4(l.z, l.z, 0.f, 0.f);
+    }
+    __syncthreads();
+    float2 p[NP], gx[NP], gy[NP], gz[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) p[k] = gx[k] = gy[k] = gz[k] = make_float2(0.f, 0.f);
+    const bool diag = ((sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads * TPT) && (t0 < sb + n)) ||
+                      (sb < hi1 && lo1 < sb + n);
+    if (!diag) {
+#pragma unroll kUnroll
+      for (int i = 0; i < n; ++i) {
+        const float4 A = sh[4 * i], B = sh[4 * i + 1], Cl = sh[4 * i + 2], Dl = sh[4 * i + 3];
+        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+        const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+        const float2 tx = make_float2(Cl.x, Cl.y), ty = make_float2(Cl.z, Cl.w), tz = make_float2(Dl.x, Dl.y);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const float2 dx = __fadd2_rn(__fadd2_rn(sx, nx[k]), __fadd2_rn(tx, mx[k]));
+          const float2 dy = __fadd2_rn(__fadd2_rn(sy, ny[k]), __fadd2_rn(ty, my[k]));
+          const float2 dz = __fadd2_rn(__fadd2_rn(sz, nz[k]), __fadd2_rn(tz, mz[k]));
+          float2 r2 = __fmul2_rn(dx, dx);
+          r2 = __ffma2_rn(dy, dy, r2);
+          r2 = __ffma2_rn(dz, dz, r2);
+          const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+          const float2 qi = __fmul2_rn(sq, inv);
+          p[k] = __fadd2_rn(p[k], qi);
+          const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+          gx[k] = __ffma2_rn(q3, dx, gx[k]);
+          gy[k] = __ffma2_rn(q3, dy, gy[k]);
+          gz[k] = __ffma2_rn(q3, dz, gz[k]);
+        }
+      }
+    } else {
+      for (int i = 0; i < n; ++i) {
+        const float4 A = sh[4 * i], B = sh[4 * i + 1], Cl = sh[4 * i + 2], Dl = sh[4 * i + 3];
+        const float2 sx = make_float2(A.x, A.y), sy = make_float2(A.z, A.w);
+        const float2 sz = make_float2(B.x, B.y), sq = make_float2(B.z, B.w);
+        const float2 tx = make_float2(Cl.x, Cl.y), ty = make_float2(Cl.z, Cl.w), tz = make_float2(Dl.x, Dl.y);
+        const int sidx = sb + i;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const int ta = t0 + threadIdx.x + (2 * k) * kPairThreads;
+          const int tb = ta + kPairThreads;
+          const bool ia = a.ioff && ta < a.n_diag, ib = a.ioff && tb < a.n_diag;
+          const int soa = ia ? a.ioff[ta] : 0, sca = ia ? a.icnt[ta] : 0;
+          const int sob = ib ? a.ioff[tb] : 0, scb = ib ? a.icnt[tb] : 0;
+          const float2 dx = __fadd2_rn(__fadd2_rn(sx, nx[k]), __fadd2_rn(tx, mx[k]));
+          const float2 dy = __fadd2_rn(__fadd2_rn(sy, ny[k]), __fadd2_rn(ty, my[k]));
+          const float2 dz = __fadd2_rn(__fadd2_rn(sz, nz[k]), __fadd2_rn(tz, mz[k]));
+          float2 r2 = __fmul2_rn(dx, dx);
+          r2 = __ffma2_rn(dy, dy, r2);
+          r2 = __ffma2_rn(dz, dz, r2);
+          // an ion skips its identity image and its own shifted images
+          const bool owna = (sidx == ta && ta < a.n_diag) || (unsigned)(sidx - soa) < (unsigned)sca;
+          const bool ownb = (sidx == tb && tb < a.n_diag) || (unsigned)(sidx - sob) < (unsigned)scb;
+          const float2 inv = make_float2(owna ? 0.f : rsqrtf(r2.x), ownb ? 0.f : rsqrtf(r2.y));
+          const float2 qi = __fmul2_rn(sq, inv);
+          p[k] = __fadd2_rn(p[k], qi);
+          const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+          gx[k] = __ffma2_rn(q3, dx, gx[k]);
+          gy[k] = __ffma2_rn(q3, dy, gy[k]);
+          gz[k] = __ffma2_rn(q3, dz, gz[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      smem_two_sum(acc, 2 * k, 0, p[k].x);
+      smem_two_sum(acc, 2 * k + 1, 0, p[k].y);
+      smem_two_sum(acc, 2 * k, 1, gx[k].x);
+      smem_two_sum(acc, 2 * k + 1, 1, gx[k].y);
+      smem_two_sum(acc, 2 * k, 2, gy[k].x);
+      smem_two_sum(acc, 2 * k + 1, 2, gy[k].y);
+      smem_two_sum(acc, 2 * k, 3, gz[k].x);
+      smem_two_sum(acc, 2 * k + 1, 3, gz[k].y);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    const int t = t0 + threadIdx.x + k * kPairThreads;
+    if (t < a.n_tgt) {
+      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+#pragma unroll
+      for (int comp = 0; comp < 4; ++comp) {
+        const float* hp = acc + ((8 * k + 2 * comp) * kPairThreads + threadIdx.x);
+        o[comp * (size_t)a.ld] = (double)hp[0] + (double)hp[kPairThreads];
+      }
+    }
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2xs(PairArgs a) {
+  __shared__ float4 sh[4 * kTile32];
+  extern __shared__ float acc[];   // 8 * 2NP * kPairThreads floats
+  const int items = a.n_tiles * a.n_chunks;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2xs<NP>(a, item, sh, acc);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2s(PairArgs a) {
   __shared__ float4 sh[2 * kTile32];
@@ -693,10 +836,12 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
 
 // Kernel variants of the FP32 path, by code: 1, 2, 4 = scalar FP32 with that
 // many targets per thread; 12, 14 = packed FP32x2 with 2 or 4 targets;
-// 24 = packed, 4 targets, compensated sums in shared memory.
+// 24 = packed, 4 targets, compensated sums in shared memory; 32, 34 = packed
+// exact differences with 2 or 4 targets; 44 = exact differences, 4 targets,
+// compensated sums in shared memory.
 int pair_tile_targets(int precision, int tpt) {
   if (precision == 0) return kPairThreads;
-  return kPairThreads * (tpt > 30 ? tpt - 30 : tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);
+  return kPairThreads * (tpt > 40 ? tpt - 40 : tpt > 30 ? tpt - 30 : tpt > 20 ? tpt - 20 : tpt > 10 ? tpt - 10 : tpt);
 }
 
 static const void* pair_fn(int precision, int tpt) {
@@ -709,6 +854,7 @@ static const void* pair_fn(int precision, int tpt) {
     case 24: return (const void*)k_pair_f32x2s<2>;
     case 32: return (const void*)k_pair_f32x2x<1>;
     case 34: return (const void*)k_pair_f32x2x<2>;
+    case 44: return (const void*)k_pair_f32x2xs<2>;
     default: return (const void*)k_pair_f32<4>;
   }
 }
@@ -718,7 +864,7 @@ int pair_slots(int precision, int tpt) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fn(precision, tpt), kPairThreads,
-                                                tpt == 24 ? kAccBytes2 : 0);
+                                                (tpt == 24 || tpt == 44) ? kAccBytes2 : 0);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -733,6 +879,7 @@ cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream
   else if (tpt == 24) k_pair_f32x2s<2><<<grid, kPairThreads, kAccBytes2, s>>>(a);
   else if (tpt == 32) k_pair_f32x2x<1><<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 34) k_pair_f32x2x<2><<<grid, kPairThreads, 0, s>>>(a);
+  else if (tpt == 44) k_pair_f32x2xs<2><<<grid, kPairThreads, kAccBytes2, s>>>(a);
   else k_pair_f32<4><<<grid, kPairThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
