@@ -112,7 +112,8 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "targets_per_thread" kernel variant: 1, 2, 4 (scalar FP32), 12, 14
  *                       (packed FP32x2, 2 or 4 targets), 24 (packed, sums in
  *                       shared memory) or 32, 34 (exact differences, 2 or 4
- *                       targets; precision 2); turns autotune off.
+ *                       targets), 44 (exact differences, 4 targets, sums in
+ *                       shared memory) for precision 2; turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
  *   "sphere_mask"       1 (default) = the near set is the images inside the
@@ -127,6 +128,15 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       too, weighted by grad_weight * R_c.  Not in the
  *                       paper's fit; 0 (default) = the paper's rows only.
  *   "grad_weight"       weight of those rows in units of R_c (> 0; 0.1).
+ *   "surface_rule"      quadrature of the surface charges on the sphere B
+ *                       (Sec. 2.2, third step): 0 (default) = M golden-spiral
+ *                       points with equal weights; 1 = the Fibonacci lattice
+ *                       rule of Sec. 3.2 with F = M and F_w the Fibonacci
+ *                       number before it (M must be a Fibonacci number >= 13,
+ *                       else HSMA_ERR_ARG), lattice (j + 1/2)/F, (j F_w mod F)/F
+ *                       mapped to the sphere through a degree-5 periodising
+ *                       map, with the map's Jacobian as the weights; it
+ *                       converges as M^-6.
  *   "near_tree"         1 = evaluate the near-field and check-point sums by a
  *                       tree (the paper's O(N) path, which it runs through an
  *                       FMM library): images binned into a uniform octree over
@@ -223,12 +233,14 @@ int hsma_get_array(hsma_t h, const char* name, double* out, int64_t n);
  *   "sizes"          [n_check, nv, nA, rank, n_shift, Rc, Rs, Rs2].
  * lam <= 0, n_monitor <= 0 or G <= 0 select the defaults; grad_weight > 0
  * adds the gradient-periodicity rows with that weight (option grad_rows),
- * <= 0 leaves them out.  n is the capacity of out in doubles.
+ * <= 0 leaves them out; surface_rule is the option of that name.  n is the
+ * capacity of out in doubles.
  * Errors: HSMA_ERR_ARG, HSMA_ERR_NUMERIC.
  */
 int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
                         double gamma_bot, double lam, int n_monitor, int G,
-                        double grad_weight, const char* name, double* out, int64_t n);
+                        double grad_weight, int surface_rule, const char* name, double* out,
+                        int64_t n);
 
 /*
  * hsma_pair_sum_static -- the direct pair sum (the kernel behind the near

@@ -48,12 +48,12 @@ notes of the repository):
     first upper image reflects across the top interface).  See ``ewald``.
  R8 Neutrality: |sum q| > 1e-10 sum |q| is an error; otherwise the residual is
     removed as q_i -= sum q / N.
- R2b Unmasked near set (optional): every image of every shift of the table is
+ R12 Unmasked near set (optional): every image of every shift of the table is
     near, whether inside B or not (3D: the full 27 cells at lambda <= sqrt 3).
     The far sources then start at 1.5 cells from the centre, so the series of
     Eq. 5 converges faster inside the circumsphere, at about 4.5 times the
     near-field cost.  The fit and the surface map are unchanged.
- R9 Gradient-periodicity rows (optional, off by default; not in the paper's
+ R13 Gradient-periodicity rows (optional, off by default; not in the paper's
     fit): for every periodic row of R4/R5 three more rows, one per Cartesian
     component d, require the field to be periodic as well:
         w_g sum A [d_d b(r_c) - d_d b(w(r_c))] = w_g [d_d Phi_B(w(r_c)) - d_d Phi_B(r_c)]
@@ -61,6 +61,17 @@ notes of the repository):
     potential units like those of R4).  They are appended after all other rows;
     the raw check vector gains d_x, d_y, d_z Phi_B at the 2 N_m monitoring
     points and wraps.
+ R18 Fibonacci lattice surface rule (optional, surface_rule=1; Sec. 3.2 names
+    the rule by two adjacent Fibonacci numbers F_w < F and claims N_o^-6
+    convergence): M = F points, F_w the Fibonacci number before F.  The
+    rank-1 lattice u_j = (j + 1/2)/F, s_j = (j F_w mod F)/F on the unit
+    square is mapped to the sphere by theta = pi psi(u), phi = 2 pi s, with
+    the periodising map psi(u) = u^3 (10 - 15 u + 6 u^2), psi'(u) =
+    30 u^2 (1 - u)^2.  The weight of point j is the Jacobian over F,
+        w_j = 2 pi^2 psi'(u_j) sin(theta_j) / F   (unit sphere),
+    and R6 becomes Q_j = sum A_nm (2n+1) R_s^(n+1) w_j / (4 pi) Y_nm(yhat_j).
+    The integrand's periodic extension in u has its first jump in the fifth
+    derivative, so the rule converges as F^-6 on smooth integrands.
 
 Coordinates at the API: 3D box [0,Lx)x[0,Ly)x[0,Lz) (positions are wrapped);
 2D slab [0,Lx)x[0,Ly)x(0,Lz) (x, y wrapped; z must be inside).  Internally
@@ -77,7 +88,7 @@ from .ewald import image_factor
 GOLDEN = (1.0 + math.sqrt(5.0)) / 2.0
 NEUTRAL_TOL = 1e-10
 SVD_RCOND = 1e-13
-GRAD_WEIGHT = 0.1        # R9: w_g / R_c
+GRAD_WEIGHT = 0.1        # R13: w_g / R_c
 
 
 class OracleError(ValueError):
@@ -87,6 +98,30 @@ class OracleError(ValueError):
 def rnd_half_away(x):
     """Round half away from zero (R4)."""
     return np.sign(x) * np.floor(np.abs(x) + 0.5)
+
+
+def fibonacci_pair(M):
+    """(F_w, F) with F = M for a Fibonacci number M >= 13 (R18), else None."""
+    a, b = 8, 13
+    while b < M:
+        a, b = b, a + b
+    return (a, b) if b == M else None
+
+
+def fibonacci_lattice(M, radius):
+    """Fibonacci lattice rule on the sphere (R18): M points of the radius and
+    their weights on the unit sphere (summing to 4 pi up to O(M^-6))."""
+    Fw, F = fibonacci_pair(M)
+    j = np.arange(F, dtype=np.int64)
+    u = (j + 0.5) / F
+    s = ((j * Fw) % F) / F
+    psi = u ** 3 * (10.0 - 15.0 * u + 6.0 * u * u)
+    dpsi = 30.0 * u * u * (1.0 - u) ** 2
+    th = math.pi * psi
+    ph = 2.0 * math.pi * s
+    y = radius * np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=-1)
+    w = 2.0 * math.pi ** 2 * dpsi * np.sin(th) / F
+    return y, w
 
 
 def golden_spiral(n, radius):
@@ -125,9 +160,11 @@ class Setup:
     ysurf: np.ndarray = field(default=None)    # (M, 3) surface points
     rank: int = 0
     sing: np.ndarray = field(default=None)
-    grad_rows: bool = False                    # R9
+    grad_rows: bool = False                    # R13
     grad_weight: float = 0.0
-    sphere_mask: bool = True                   # R2 (False: R2b)
+    sphere_mask: bool = True                   # R2 (False: R12)
+    surface_rule: int = 0                      # R3 (1: R18)
+    wsurf: np.ndarray = field(default=None)    # (M,) R18 weights on the unit sphere
 
 
 def shift_table(dims, box, Rs, gamma_top=0.0, gamma_bot=0.0):
@@ -185,10 +222,11 @@ def face_grid(box, G):
 
 def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
                n_monitor=None, dtn_grid=80, prefactor=1.0, grad_rows=False,
-               grad_weight=GRAD_WEIGHT, sphere_mask=True):
+               grad_weight=GRAD_WEIGHT, sphere_mask=True, surface_rule=0):
     """Geometry-only preparation: sphere, shifts, check points, fit, map.
-    grad_rows adds the gradient-periodicity rows of R9; sphere_mask=False
-    takes the unmasked near set of R2b."""
+    grad_rows adds the gradient-periodicity rows of R13; sphere_mask=False
+    takes the unmasked near set of R12; surface_rule=1 the Fibonacci lattice
+    rule of R18 (M must be a Fibonacci number >= 13)."""
     box = tuple(float(b) for b in box)
     if dims not in (2, 3):
         raise OracleError("dims must be 2 or 3")
@@ -196,6 +234,8 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
         raise OracleError("need p >= 1 and M >= (p+1)^2")
     if abs(gamma_top) > 1 or abs(gamma_bot) > 1:
         raise OracleError("|gamma| must be <= 1")
+    if surface_rule not in (0, 1) or (surface_rule == 1 and fibonacci_pair(M) is None):
+        raise OracleError("surface_rule 1 needs M to be a Fibonacci number >= 13")
     if lam is None:
         lam = 1.3 if dims == 3 else 1.6
     if n_monitor is None:
@@ -208,6 +248,7 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
     st.grad_rows = bool(grad_rows)
     st.grad_weight = float(grad_weight)
     st.sphere_mask = bool(sphere_mask)
+    st.surface_rule = int(surface_rule)
     st.Rc = 0.5 * math.sqrt((Lx * Lx + Ly * Ly) + Lz * Lz)
     st.Rs = st.lam * st.Rc
     st.Rs2 = st.Rs * st.Rs
@@ -248,7 +289,7 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
         D = np.vstack(blocks)
     n_base_rows = D.shape[0]
     if st.grad_rows:
-        # R9: one row per kept monitoring point and component, component-major
+        # R13: one row per kept monitoring point and component, component-major
         wg = st.grad_weight * st.Rc
         Gm = H.solid_grad(p, mon, st.Rc)[:, 1:, :]
         Gw = H.solid_grad(p, wrap, st.Rc)[:, 1:, :]
@@ -299,12 +340,20 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
         assert P.shape[1] == nv0 + 6 * nm
     st.P = P
 
-    # surface map (R6): Q_m = sum_nm A_nm (2n+1) R_s^(n+1) / M Y_nm(yhat_m)
-    st.ysurf = golden_spiral(M, st.Rs)
-    Y = H.solid(p, st.ysurf, st.Rs)       # (r/R_s)^n Y_nm = Y_nm at r = R_s
-    nfac = np.array([(2 * n + 1) * st.Rs ** (n + 1) / (M * st.Rc ** n)
-                     for n in range(p + 1) for _ in range(2 * n + 1)])
-    st.W = (Y * nfac[None, :])[:, 1:]
+    if st.surface_rule == 0:
+        # surface map (R6): Q_m = sum_nm A_nm (2n+1) R_s^(n+1) / M Y_nm(yhat_m)
+        st.ysurf = golden_spiral(M, st.Rs)
+        Y = H.solid(p, st.ysurf, st.Rs)       # (r/R_s)^n Y_nm = Y_nm at r = R_s
+        nfac = np.array([(2 * n + 1) * st.Rs ** (n + 1) / (M * st.Rc ** n)
+                         for n in range(p + 1) for _ in range(2 * n + 1)])
+        st.W = (Y * nfac[None, :])[:, 1:]
+    else:
+        # R18: Q_j = sum_nm A_nm (2n+1) R_s^(n+1) w_j / (4 pi) Y_nm(yhat_j)
+        st.ysurf, st.wsurf = fibonacci_lattice(M, st.Rs)
+        Y = H.solid(p, st.ysurf, st.Rs)
+        nfac = np.array([(2 * n + 1) * st.Rs ** (n + 1) / (4.0 * math.pi * st.Rc ** n)
+                         for n in range(p + 1) for _ in range(2 * n + 1)])
+        st.W = (Y * nfac[None, :] * st.wsurf[:, None])[:, 1:]
     return st
 
 
@@ -335,7 +384,7 @@ def prepare_inputs(st, x, q):
 
 
 def near_set(st, xc, q):
-    """Images inside B (step 1, R2), or every image of the table (R2b):
+    """Images inside B (step 1, R2), or every image of the table (R12):
     positions, charges, source index, shift index."""
     pos, chg, src, sid = [], [], [], []
     for s, (sx, sy, zs, zo, f) in enumerate(st.shifts):

@@ -137,11 +137,30 @@ def case1_variants():
     return out
 
 
+def surface_rules():
+    """Case 1 positions at p = 10 under the two surface rules (R3, R18), at
+    the default sphere (lambda = 1.3) and the literal one (lambda = 2.6)."""
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    L = c.box[0]
+    xc = (x - L * np.floor(x / L)) - 0.5 * L
+    Ee, _, ge = ewald3d(xc, q, c.box)
+    out = []
+    for lam, runs in ((1.3, ((0, 800), (1, 987))), (2.6, ((0, 800), (0, 2584), (1, 610), (1, 2584)))):
+        for rule, M in runs:
+            r = O.evaluate(O.make_setup(c.box, 3, 10, M, lam=lam, surface_rule=rule), x, q)
+            name = "golden spiral" if rule == 0 else "Fibonacci lattice"
+            out.append({"case": f"{c.name} positions, p = 10, lambda = {lam}, {name}, M = {M}",
+                        "rel_energy": abs(r["energy"] - Ee) / abs(Ee),
+                        "rel_force_rms": rel_rms(r["forces"], -q[:, None] * ge)})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true")
     a = ap.parse_args()
-    res = [case1(), *case1_variants(), case2_shape(N=4000 if a.quick else 8000)]
+    res = [case1(), *case1_variants(), *surface_rules(), case2_shape(N=4000 if a.quick else 8000)]
     for gam in (-0.95, 0.0, 0.95):
         for margin in (0.0, 0.5):
             res.append(case3_shape(gam, margin, N=800 if a.quick else 2000))

@@ -41,7 +41,7 @@ SIGNATURES = {
     "hsma_submit": (_I, [_P, _P, _P, _L, ctypes.POINTER(_D), _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "hsma_poll": (_I, [_P, ctypes.c_uint64, _P, _P]),
     "hsma_server_step": (_I, [_P]),
-    "hsma_geometry_array": (_I, [ctypes.POINTER(_D), _I, _I, _I, _D, _D, _D, _I, _I, _D,
+    "hsma_geometry_array": (_I, [ctypes.POINTER(_D), _I, _I, _I, _D, _D, _D, _I, _I, _D, _I,
                                  ctypes.c_char_p, _P, _L]),
     "hsma_pair_sum_static": (_I, [_P, _L, _P, _L, _P, _I, _P]),
     "hsma_md_create": (_I, [_P, _P, _P, _P, _L, _D, _D, _D, _D, _D, _D, ctypes.POINTER(_P)]),
@@ -210,12 +210,13 @@ def hsma_server_step(server):
 
 
 def hsma_geometry_array(box, dims, p, M, name, n, gamma_top=0.0, gamma_bot=0.0, lam=0.0,
-                        n_monitor=0, G=0, grad_weight=0.0):
+                        n_monitor=0, G=0, grad_weight=0.0, surface_rule=0):
     """Host-only geometry array (no GPU); see include/hsma.h."""
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     out = np.empty(int(n), dtype=np.float64)
     rc = lib().hsma_geometry_array(b, int(dims), int(p), int(M), float(gamma_top), float(gamma_bot),
-                                   float(lam), int(n_monitor), int(G), float(grad_weight), name.encode(),
+                                   float(lam), int(n_monitor), int(G), float(grad_weight),
+                                   int(surface_rule), name.encode(),
                                    ctypes.c_void_p(out.ctypes.data), int(n))
     if rc != HSMA_OK:
         raise HSMAError(rc, "hsma_geometry_array(" + name + ") failed")

@@ -296,10 +296,10 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
 int mask_words(const Geometry& g) { return std::max<int>(1, ((int)g.shifts.size() - 1 + 31) / 32); }
 
 // Pair-kernel variant code for the handle's precision: FP64 has one; the
-// exact-difference path (precision 2) runs the hi/lo variants 32 or 34.
+// exact-difference path (precision 2) runs the hi/lo variants 32, 34 or 44.
 static int eff_tpt(const hsma_ctx* h) {
   if (h->precision == 0) return 1;
-  if (h->precision == 2) return (h->tpt == 32 || h->tpt == 34) ? h->tpt : 34;
+  if (h->precision == 2) return (h->tpt == 32 || h->tpt == 34 || h->tpt == 44) ? h->tpt : 34;
   return h->tpt;
 }
 
@@ -572,7 +572,7 @@ static int tune_near(hsma_ctx* h, int64_t N) {
       return ensure_plan(h, N);
     }
   }
-  std::vector<int> tpts = prec == 2 ? std::vector<int>{32, 34}
+  std::vector<int> tpts = prec == 2 ? std::vector<int>{32, 34, 44}
                          : prec ? std::vector<int>{12, 14, 24, 1} : std::vector<int>{1};
   struct Cand { int tpt, chunks; float ms; };
   std::vector<Cand> cands;
@@ -766,6 +766,12 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     if (!(v > 0) || !std::isfinite(v)) return fail(h, HSMA_ERR_ARG, "grad_weight must be > 0");
     h->gp.grad_weight = v;
     h->geo_dirty = true;
+  } else if (k == "surface_rule") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "surface_rule must be 0 or 1");
+    if (v == 1 && fibonacci_before(h->gp.M) == 0)
+      return fail(h, HSMA_ERR_ARG, "surface_rule 1 needs M to be a Fibonacci number >= 13");
+    h->gp.surface_rule = (int)v;
+    h->geo_dirty = true;
   } else if (k == "near_tree") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "near_tree must be 0 or 1");
     h->near_tree = (int)v;
@@ -798,9 +804,9 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->tuned_chunks = 0;
     h->plan_N = -1;
   } else if (k == "targets_per_thread") {
-    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14 && v != 24 && v != 32 && v != 34)
+    if (v != 1 && v != 2 && v != 4 && v != 12 && v != 14 && v != 24 && v != 32 && v != 34 && v != 44)
       return fail(h, HSMA_ERR_ARG,
-                  "targets_per_thread must be 1, 2, 4 (scalar), 12, 14, 24 (packed) or 32, 34 (exact differences)");
+                  "targets_per_thread must be 1, 2, 4 (scalar), 12, 14, 24 (packed) or 32, 34, 44 (exact differences)");
     h->tpt = (int)v;
     h->autotune = 0;          // an explicit kernel choice turns tuning off
     h->tuned_N = -1;
@@ -910,7 +916,8 @@ const char* hsma_last_error(hsma_t h) {
 
 extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
                                    double gamma_bot, double lam, int n_monitor, int G,
-                                   double grad_weight, const char* name, double* out, int64_t n) {
+                                   double grad_weight, int surface_rule, const char* name, double* out,
+                                   int64_t n) {
   if (!box || !name || !out) return HSMA_ERR_ARG;
   if (dims != 2 && dims != 3) return HSMA_ERR_ARG;
   GeoParams gp;
@@ -925,6 +932,7 @@ extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, 
   gp.G = G > 0 ? G : 80;
   gp.grad_rows = grad_weight > 0 ? 1 : 0;
   if (grad_weight > 0) gp.grad_weight = grad_weight;
+  gp.surface_rule = surface_rule;
   Geometry g;
   std::string err;
   const int rc = build_geometry(gp, &g, &err);

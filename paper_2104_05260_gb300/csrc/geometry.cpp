@@ -14,6 +14,13 @@
 //    discrete DtN map, rows weighted by R_c / G (Sec. 2.2, second step).
 //  * Surface charges: Q_m = sum A_nm (2n+1) R_s^(n+1) / M Y_nm(y_m/R_s) on M
 //    spherical-Fibonacci points of radius R_s (Sec. 2.2, third step).
+//    Option: the Fibonacci lattice rule named in Sec. 3.2 by two adjacent
+//    Fibonacci numbers F_w < F (M = F): the lattice u_j = (j + 1/2)/F,
+//    s_j = (j F_w mod F)/F is mapped to theta = pi psi(u), phi = 2 pi s with
+//    psi(u) = u^3 (10 - 15u + 6u^2); weight w_j = 2 pi^2 psi'(u_j)
+//    sin(theta_j) / F, and 1/M above becomes w_j / (4 pi).  The periodic
+//    extension of the integrand in u then jumps first in its fifth
+//    derivative, hence the F^-6 convergence the paper states.
 //  * Image factors of Sec. 2.1, Eq. 4 with the first upper image carrying
 //    gamma_top (reflection across the top interface).
 #include "geometry.hpp"
@@ -252,6 +259,36 @@ static void fibonacci_sphere(int n, double R, std::vector<double>* out) {
   }
 }
 
+int fibonacci_before(int M) {
+  long a = 8, b = 13;
+  while (b < M) {
+    const long c = a + b;
+    a = b;
+    b = c;
+  }
+  return b == M ? (int)a : 0;
+}
+
+// Points of the Fibonacci lattice rule (radius R) and their weights on the
+// unit sphere; M must be a Fibonacci number >= 13.
+static void fibonacci_lattice(int M, double R, std::vector<double>* out, std::vector<double>* w) {
+  const long Fw = fibonacci_before(M);
+  out->resize((size_t)M * 3);
+  w->resize(M);
+  for (int j = 0; j < M; ++j) {
+    const double u = (j + 0.5) / M;
+    const double s = (double)(((long)j * Fw) % M) / M;
+    const double psi = u * u * u * (10.0 - 15.0 * u + 6.0 * u * u);
+    const double dpsi = 30.0 * u * u * (1.0 - u) * (1.0 - u);
+    const double th = kPi * psi, ph = 2.0 * kPi * s;
+    const double st = std::sin(th);
+    (*out)[3 * j + 0] = R * st * std::cos(ph);
+    (*out)[3 * j + 1] = R * st * std::sin(ph);
+    (*out)[3 * j + 2] = R * std::cos(th);
+    (*w)[j] = 2.0 * kPi * kPi * dpsi * st / M;
+  }
+}
+
 // Periodic discrete DtN map on a G x G grid (x-major): F^-1 diag(|h|) F with
 // h = 2 pi (j'/Lx, k'/Ly), j' the signed frequency.  Direct separable DFT.
 struct DtN {
@@ -380,6 +417,9 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
   if (gp.dims == 2 && gp.G < 4) { *err = "dtn_grid must be >= 4"; return HSMA_ERR_ARG; }
   if (gp.grad_rows && !(gp.grad_weight > 0.0 && std::isfinite(gp.grad_weight))) {
     *err = "grad_weight must be > 0"; return HSMA_ERR_ARG;
+  }
+  if (gp.surface_rule != 0 && (gp.surface_rule != 1 || fibonacci_before(M) == 0)) {
+    *err = "surface_rule 1 needs M to be a Fibonacci number >= 13"; return HSMA_ERR_ARG;
   }
   g->par = gp;
   sphere_radius(gp.box, gp.lam, &g->Rc, &g->Rs, &g->Rs2);
@@ -518,16 +558,24 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
       }
   }
   // surface points and W
-  fibonacci_sphere(M, Rs, &g->ysurf);
   g->W.assign((size_t)M * nA, 0.0);
-  std::vector<double> fac(nb);
-  for (int n = 0; n <= p; ++n)
-    for (int m = -n; m <= n; ++m)
-      fac[n * n + n + m] = (2 * n + 1) * std::pow(Rs, n + 1) / ((double)M * std::pow(Rc, n));
-  std::vector<double> ys(nb);
+  std::vector<double> fac(nb), ys(nb), wq;
+  if (gp.surface_rule == 0) {
+    fibonacci_sphere(M, Rs, &g->ysurf);
+    for (int n = 0; n <= p; ++n)
+      for (int m = -n; m <= n; ++m)
+        fac[n * n + n + m] = (2 * n + 1) * std::pow(Rs, n + 1) / ((double)M * std::pow(Rc, n));
+  } else {
+    fibonacci_lattice(M, Rs, &g->ysurf, &wq);
+    for (int n = 0; n <= p; ++n)
+      for (int m = -n; m <= n; ++m)
+        fac[n * n + n + m] = (2 * n + 1) * std::pow(Rs, n + 1) / (4.0 * kPi * std::pow(Rc, n));
+  }
   for (int m = 0; m < M; ++m) {
     solid_basis(p, g->ysurf[3 * m], g->ysurf[3 * m + 1], g->ysurf[3 * m + 2], Rs, ys.data(), nullptr);
-    for (int k = 1; k < nb; ++k) g->W[(size_t)m * nA + k - 1] = fac[k] * ys[k];
+    const double wm = gp.surface_rule == 0 ? 1.0 : wq[m];
+    for (int k = 1; k < nb; ++k)
+      g->W[(size_t)m * nA + k - 1] = gp.surface_rule == 0 ? fac[k] * ys[k] : (fac[k] * ys[k]) * wm;
   }
   return HSMA_OK;
 }

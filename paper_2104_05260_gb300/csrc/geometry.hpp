@@ -29,7 +29,12 @@ struct GeoParams {
   int sphere_mask = 1;       // 0: every image of the shift table is near
   int grad_rows = 0;         // gradient-periodicity rows appended to the fit
   double grad_weight = 0.1;  // their weight, in units of R_c
+  int surface_rule = 0;      // 0: golden-spiral points, equal weights; 1: Fibonacci lattice rule
 };
+
+// The Fibonacci number before M when M is a Fibonacci number >= 13 (the
+// lattice rule's F_w for F = M), else 0.
+int fibonacci_before(int M);
 
 struct Geometry {
   GeoParams par;

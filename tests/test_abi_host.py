@@ -107,6 +107,28 @@ def test_geometry_gradient_rows_match_oracle(P, dims):
     assert np.abs(To[:, -6 * st.n_mon:]).max() > 1e-3 * np.abs(To).max()
 
 
+@pytest.mark.parametrize("dims,M", [(3, 987), (2, 610)])
+def test_geometry_fibonacci_lattice_matches_oracle(P, dims, M):
+    # the surface rule of Sec. 3.2 (F_w/F lattice): points and the weighted map
+    from oracle import hsma
+    box = (10.0, 10.0, 10.0) if dims == 3 else (20.0, 20.0, 10.0)
+    p, G = 6, 16
+    st = hsma.make_setup(box, dims, p, M, 0.4, -0.2, dtn_grid=G, surface_rule=1)
+    kw = dict(gamma_top=0.4, gamma_bot=-0.2, G=G, surface_rule=1)
+    sz = sizes(P, box, dims, p, M, **kw)
+    ys = P.hsma_geometry_array(box, dims, p, M, "surface_points", 3 * M, **kw).reshape(-1, 3)
+    assert np.allclose(ys, st.ysurf, rtol=0, atol=1e-12)
+    T = P.hsma_geometry_array(box, dims, p, M, "T", M * sz["nv"], **kw).reshape(M, sz["nv"])
+    To = st.W @ st.P
+    assert np.abs(T - To).max() < 1e-8 * np.abs(To).max()
+    # a different map from the golden-spiral rule at the same M
+    T0 = P.hsma_geometry_array(box, dims, p, M, "T", M * sz["nv"], gamma_top=0.4, gamma_bot=-0.2,
+                               G=G).reshape(M, sz["nv"])
+    assert np.abs(T - T0).max() > 1e-2 * np.abs(To).max()
+    with pytest.raises(P.HSMAError):
+        P.hsma_geometry_array(box, dims, p, M + 1, "sizes", 8, surface_rule=1)   # not Fibonacci
+
+
 def test_geometry_rejects_bad_arguments(P):
     with pytest.raises(P.HSMAError):
         P.hsma_geometry_array((10, 10, 10), 3, 6, 10, "sizes", 8)       # M < (p+1)^2

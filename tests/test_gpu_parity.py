@@ -154,6 +154,47 @@ def test_unmasked_near_set_2d(P, prec):
     check_full(P, c, x, q, prec, st=st, dtn_grid=24, sphere_mask=0)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [3, 2])
+def test_fibonacci_lattice_surface_rule(P, prec, dims):
+    # option surface_rule = 1: the F_w/F lattice rule of Sec. 3.2 (M = F)
+    import dataclasses
+    if dims == 3:
+        c = dataclasses.replace(workloads.case(1), M=987)
+        x, q = workloads.electrolyte(c)
+        st = O.make_setup(c.box, 3, c.p, c.M, lam=c.lam, surface_rule=1)
+        check_full(P, c, x, q, prec, st=st, surface_rule=1)
+    else:
+        c = workloads.small_case(300, dims=2, box=(20.0, 20.0, 10.0), p=6, M=610, gammas=(0.5, -0.3),
+                                 G=24, seed=19)
+        x, q = workloads.electrolyte(c, margin=1e-3)
+        st = O.make_setup(c.box, 2, c.p, c.M, 0.5, -0.3, lam=c.lam, dtn_grid=24, surface_rule=1)
+        check_full(P, c, x, q, prec, st=st, dtn_grid=24, surface_rule=1)
+
+
+def test_fibonacci_lattice_at_the_literal_sphere_against_ewald(P):
+    # the literal sphere (lambda = 2.6) at P = 10 on the FP64 path: with the
+    # lattice rule the result lies within 1e-6 of the Ewald sum
+    from oracle.ewald import ewald3d
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    L = c.box[0]
+    xc = (x - L * np.floor(x / L)) - 0.5 * L
+    Ee, _, ge = ewald3d(xc, q, c.box)
+    h = P.HSMA(c.box, 3, 10, 610, precision=0, surface_rule=1, **{"lambda": 2.6})
+    E, F, _ = h.eval(x, q)
+    h.close()
+    assert rel(E, Ee) < 1e-6
+    assert frms(F, -q[:, None] * ge) < 1e-6
+
+
+def test_surface_rule_rejects_a_non_fibonacci_count(P):
+    h = P.HSMA((10.0, 10.0, 10.0), 3, 6, 800)
+    with pytest.raises(P.HSMAError):
+        h.set_option("surface_rule", 1)
+    h.close()
+
+
 def test_exact_differences_close_the_fp32_gap_at_bench_size(P):
     # precision 2 against the FP64 path at N = 1e5: the close-pair force error
     # of plain FP32 (coordinates rounded at |x| ~ 50) is gone
@@ -314,3 +355,22 @@ def test_kernel_variants_graphs_and_tuning_agree(P):
     E, F, _ = h.eval(x, q)
     h.close()
     assert rel(E, ref[0]) <= 1e-12 and frms(F, ref[1]) <= 1e-12
+
+
+def test_exact_difference_variants_agree(P):
+    # the three exact-difference kernels (2 or 4 targets per thread, sums in
+    # registers or in shared memory) form the same differences and sum the
+    # same pair terms in the same order, so with a fixed chunk count they
+    # agree bitwise, with and without graph replay
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    ref = None
+    for tpt in (32, 34, 44):
+        for graphs in (0, 1):
+            h = P.HSMA(c.box, 3, c.p, c.M, precision=2, targets_per_thread=tpt, chunks=8, graphs=graphs)
+            E, F, pot = h.eval(x, q, potential=True)
+            assert h.info("kernel") == tpt
+            h.close()
+            if ref is None:
+                ref = (E, F, pot)
+            assert E == ref[0] and np.array_equal(F, ref[1]) and np.array_equal(pot, ref[2]), (tpt, graphs)

@@ -306,7 +306,7 @@ def test_fit_recovers_the_series_of_a_periodic_field(dims, grad_rows):
 
 
 def test_gradient_rows_keep_rank_and_accuracy():
-    # the gradient-periodicity rows (R9) add information: full rank, a better
+    # the gradient-periodicity rows (R13) add information: full rank, a better
     # conditioned fit, and an Ewald error no worse than the value rows alone
     L = 10.0 * (0.3) ** (1 / 3)
     x, q = system3d(300, L, 21)
@@ -324,7 +324,7 @@ def test_gradient_rows_keep_rank_and_accuracy():
 
 @pytest.mark.parametrize("dims", [3, 2])
 def test_unmasked_near_set_counts_and_is_more_accurate(dims):
-    # R2b: every image of the shift table is near, so N_s = N x (table rows);
+    # R12: every image of the shift table is near, so N_s = N x (table rows);
     # the far sources start further out and the series converges faster, so
     # the error against the plain sums drops at equal p
     if dims == 3:
