@@ -152,6 +152,12 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "tree_leaf_level"   leaf level L of the tree (8^L leaves over the root
  *                       cube), 2..6; 0 (default) = about 32 images per
  *                       occupied leaf.
+ *   "tree_parts"        1..8 (default 2): each 32-target task of the tree
+ *                       evaluation is split into this many work items (every
+ *                       tree_parts-th batch of each interaction list), which
+ *                       a persistent kernel takes from a queue; the items'
+ *                       partial sums are added in a fixed order, so the
+ *                       result depends on this value but not on scheduling.
  *   "far_field"         0 (default) = the far field from the M surface charges
  *                       (Eq. 8, the paper's choice); 1 = the fitted series of
  *                       Eq. 5 itself, sum over n >= 1 of A_nm (r/R_c)^n Y_nm,

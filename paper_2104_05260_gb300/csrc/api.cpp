@@ -252,7 +252,7 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
                    h->d_tcnt_s.ensure(nleaf * 4) || h->d_tcur_s.ensure(nleaf * 4) ||
                    h->d_tstart_s.ensure((nleaf + 1) * 4) || h->d_tkey_t.ensure(nt * 4) ||
                    h->d_tord_t.ensure(nt * 4) || h->d_tcnt_t.ensure(nleaf * 4) || h->d_tcur_t.ensure(nleaf * 4) ||
-                   h->d_tstart_t.ensure((nleaf + 1) * 4) || h->d_tpart.ensure(nleaf * nc * 8) ||
+                   h->d_tstart_t.ensure((nleaf + 1) * 4) || h->d_tpart.ensure(std::max(nleaf * nc, (size_t)h->tree_parts * 4 * nt) * 8) ||
                    h->d_tM.ensure(off * 4) || h->d_tnorm.ensure((size_t)nc * 4) || h->d_tfac.ensure((size_t)nc * 4);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "tree buffers");
   cudaError_t e = cudaMemcpy(h->d_tnorm.p, norm.data(), (size_t)nc * 4, cudaMemcpyHostToDevice);
@@ -288,6 +288,8 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
   T.M = (float*)h->d_tM.p;
   T.out = (double*)h->d_red1.p;
   T.ld = h->n_tgt1;
+  T.parts = h->tree_parts;
+  T.out_parts = (double*)h->d_tpart.p;     // the P2M partials are consumed before the evaluation
   cudaError_t e = launch_tree(T, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "tree launch");
   return HSMA_OK;
@@ -517,11 +519,12 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   rc = stage_assemble(h, N, forces_dev, pot_dev);
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[5], s);
-  // kernels this pipeline launches: prep 3, near 1 (tree: 10 + 2 per
-  // multipole level), chunk reduction 1 (not with the tree), fit 3, far 1,
-  // far reduction 1 (not with one far chunk), assembly 2
+  // kernels this pipeline launches: prep 3; near 1 and its chunk reduction
+  // 1, or the tree's 9 binning kernels, 2 per multipole level, task count and
+  // scan, evaluation and part reduction; fit 3; far 1; far reduction 1 (not
+  // with one far chunk); assembly 2
   const bool far_one = h->far_series || h->chunks2 == 1;
-  h->kernels_per_eval = 3 + (h->near_tree ? 10 + 2 * (h->tree_L - 1) : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
+  h->kernels_per_eval = 3 + (h->near_tree ? 13 + 2 * (h->tree_L - 1) : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
   return HSMA_OK;
 }
 
@@ -780,6 +783,10 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     if (!(v >= 4) || v > tree_max_order() || std::fmod(v, 2.0) != 0.0)
       return fail(h, HSMA_ERR_ARG, "tree_order must be one of 4, 6, 8, 10, 12, 14");
     h->tree_order = (int)v;
+    h->plan_N = -1;
+  } else if (k == "tree_parts") {
+    if (!(v >= 1) || v > 8 || std::floor(v) != v) return fail(h, HSMA_ERR_ARG, "tree_parts must be in [1, 8]");
+    h->tree_parts = (int)v;
     h->plan_N = -1;
   } else if (k == "tree_leaf_level") {
     if (!(v >= 0) || v > 6 || v == 1) return fail(h, HSMA_ERR_ARG, "tree_leaf_level must be 0 (automatic) or in [2, 6]");

@@ -118,10 +118,13 @@ struct TreeLaunch {
   float* M;              // multipoles of levels 2..L
   double* out;           // out[c*ld + t], c = phi, grad (one chunk's layout)
   int ld;
+  int parts;             // items per task of the evaluation (each a partial sum)
+  double* out_parts;     // parts * 4 * ld partials, summed into out in part order
 };
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
 size_t tree_eval_smem(int P);
 int tree_max_order();
+int tree_sm_count();
 
 // Sum a pair launch's per-chunk partials (rows 0..n_rows of leading
 // dimension ld) into out[c*ld + r], the layout of a single chunk; fixed order.

@@ -219,13 +219,13 @@ __global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_c
 }
 
 // ---------------------------------------------------------------- M2P + P2P
-// One block per cell G of level L-1 (its 8 leaves' targets, in index order
-// within each leaf, kTreeThreads at a time).  For levels l < L the
-// interaction list depends only on G's ancestor, so each listed cell's
-// multipole is staged once in shared memory for all of G's targets.  At the
-// leaf level the list is the children of G's neighbours; a thread skips the
-// leaves adjacent to its own.  Direct pairs come from the 4 x 4 x 4 leaves
-// around G, each thread taking those adjacent to its own leaf.
+// One warp per work item: up to 32 targets of one cell G of level L-1 (in
+// index order within each leaf) and one part of their lists.  For levels
+// l < L the interaction list depends only on G's ancestor, so each listed
+// cell's multipole is staged once in shared memory for the warp's targets.
+// At the leaf level the list is the children of G's neighbours; a lane skips
+// the leaves adjacent to its own.  Direct pairs come from the 4 x 4 x 4
+// leaves around G, each lane taking those adjacent to its own leaf.
 //
 // Multipoles hold 4 pi/(2n+1) norm^2 sum q V'T, so the evaluation multiplies
 // by the irregular polynomial U'T alone; 1/(n-m) comes from a table.
@@ -307,6 +307,17 @@ __device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y
   *z = iz;
 }
 
+// Work items of the evaluation: a task is up to 32 consecutive targets of one
+// cell G of level L-1 (task_start[G] .. task_start[G+1]); each task is split
+// into S parts, part s taking every S-th batch of each level's interaction
+// list and every S-th of the 64 direct-pair leaves.  An item (task, part) is
+// computed the same way whichever warp takes it, and writes its own partial
+// out[(s*4 + c)*ld + t]; the parts are summed afterwards in fixed order.
+__global__ void k_tree_tasks(const int* __restrict__ tgt_start, int n_cells, int* __restrict__ count) {
+  const int G = blockIdx.x * blockDim.x + threadIdx.x;
+  if (G < n_cells) count[G] = (tgt_start[(G + 1) << 3] - tgt_start[G << 3] + 31) >> 5;
+}
+
 template <int P>
 __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
                                                                int n_ions, const int* __restrict__ tgt_start,
@@ -314,11 +325,13 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
                                                                const float4* __restrict__ srcs,
                                                                const int* __restrict__ src_order,
                                                                const int* __restrict__ leaf_start,
-                                                               const float* __restrict__ M, double* __restrict__ out,
-                                                               int ld) {
-  // Warps work independently (no block barriers): warp w of the block takes
-  // G's targets w*32 + k*kTreeThreads + lane, compacts each level's list
-  // itself and stages multipoles in its own slice of shared memory.
+                                                               const float* __restrict__ M,
+                                                               const int* __restrict__ task_start, int n_cells,
+                                                               int S, int* __restrict__ queue,
+                                                               double* __restrict__ out, int ld) {
+  // Persistent warps, no block barriers: each warp takes the next item from
+  // the queue, compacts each level's list itself and stages multipoles in its
+  // own slice of shared memory.
   extern __shared__ __align__(16) float tree_smem[];
   constexpr int nc = (P + 1) * (P + 1);
   constexpr int nc4 = (nc + 3) & ~3;
@@ -329,12 +342,26 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
   int* sid = reinterpret_cast<int*>(reinterpret_cast<float4*>(tree_smem + (size_t)kWarps * kBatch * nc4) +
                                     kTreeThreads) + warp * 32;
   int* slist = sid + (kTreeThreads - warp * 32) + warp * 216;                  // compacted list, 216 per warp
-  const int G = blockIdx.x;                       // cell of level L-1
-  const int t0 = tgt_start[G << 3], t1 = tgt_start[(G + 1) << 3];
-  int gx0, gy0, gz0;
-  morton_decode(G, t.L - 1, &gx0, &gy0, &gz0);
   const int nsideL = 1 << t.L;
-  for (int base = t0 + warp * 32; base < t1; base += kTreeThreads) {
+  const int n_items = S * task_start[n_cells];
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const int task = item / S, part = item - task * S;
+    // G: the last cell whose first task is <= task
+    int lo = 0, hi = n_cells;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (task_start[mid] <= task) lo = mid;
+      else hi = mid - 1;
+    }
+    const int G = lo;                              // cell of level L-1
+    const int t0 = tgt_start[G << 3], t1 = tgt_start[(G + 1) << 3];
+    const int base = t0 + (task - task_start[G]) * 32;
+    int gx0, gy0, gz0;
+    morton_decode(G, t.L - 1, &gx0, &gy0, &gz0);
     const int slot = base + lane;
     const bool active = slot < t1;
     const int ti = active ? tgt_order[slot] : tgt_order[t0];
@@ -377,7 +404,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       }
       __syncwarp();
       float fp = 0.0f, fx = 0.0f, fy = 0.0f, fz = 0.0f;
-      for (int b0 = 0; b0 < n_list; b0 += kBatch) {
+      for (int b0 = part * kBatch; b0 < n_list; b0 += S * kBatch) {
         const int nb = min(kBatch, n_list - b0);
         __syncwarp();
         for (int k = lane; k < nb * nc4; k += 32) {
@@ -403,7 +430,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
     }
     // direct pairs: the 4 x 4 x 4 leaves around G, each target its own 27
     // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is skipped
-    for (int j = 0; j < 64; ++j) {
+    for (int j = part; j < 64; j += S) {
       const int ox = 2 * gx0 - 1 + (j & 3), oy = 2 * gy0 - 1 + ((j >> 2) & 3), oz = 2 * gz0 - 1 + (j >> 4);
       if (ox < 0 || oy < 0 || oz < 0 || ox >= nsideL || oy >= nsideL || oz >= nsideL) continue;
       const int code = morton(ox, oy, oz);
@@ -442,10 +469,11 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
     }
     if (active) {
       // as the pair kernels: phi and its gradient with respect to the target
-      out[ti] = phi;
-      out[(size_t)ld + ti] = gx;
-      out[2 * (size_t)ld + ti] = gy;
-      out[3 * (size_t)ld + ti] = gz;
+      double* o = out + (size_t)part * 4 * ld;
+      o[ti] = phi;
+      o[(size_t)ld + ti] = gx;
+      o[2 * (size_t)ld + ti] = gy;
+      o[3 * (size_t)ld + ti] = gz;
     }
   }
 }
@@ -457,6 +485,17 @@ size_t tree_eval_smem(int P) {
 }
 
 int tree_max_order() { return kMaxOrder; }
+
+int tree_sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 1;
+  }
+  return sms;
+}
 
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   const TreeArgs& t = T.t;
@@ -497,10 +536,21 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
     const int per = items / cells;
     k_tree_m_reduce<<<(cells * nc + 255) / 256, 256, 0, s>>>(T.part, per, cells, nc, T.M + t.moff[l]);
   }
+  // tasks per cell of level L-1 (the cursors are free again after the fills)
+  const int n_cells = nleaf / 8;
+  int* task_count = T.src_cursor;
+  int* task_start = T.tgt_cursor;
+  int* queue = T.tgt_count;
+  k_tree_tasks<<<(n_cells + 255) / 256, 256, 0, s>>>(T.tgt_start, n_cells, task_count);
+  k_tree_scan<<<1, 1024, 0, s>>>(task_count, n_cells, task_start);
+  e = cudaMemsetAsync(queue, 0, 4, s);
+  if (e != cudaSuccess) return e;
   const size_t sm = tree_eval_smem(t.P);
-#define HSMA_TREE_EVAL(PP)                                                                                  \
-  k_tree_eval<PP><<<nleaf / 8, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order, T.src_sorted, \
-                                                      T.src_order, T.src_start, T.M, T.out, T.ld)
+  const int eval_grid = 5 * tree_sm_count();
+#define HSMA_TREE_EVAL(PP)                                                                                \
+  k_tree_eval<PP><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order,        \
+                                                      T.src_sorted, T.src_order, T.src_start, T.M, task_start, \
+                                                      n_cells, T.parts, queue, T.out_parts, T.ld)
   switch (t.P) {
     case 4: HSMA_TREE_EVAL(4); break;
     case 6: HSMA_TREE_EVAL(6); break;
@@ -511,7 +561,9 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
 #undef HSMA_TREE_EVAL
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_chunks(T.out_parts, T.parts, T.ld, T.n_tgt, T.out, s);
 }
 
 }  // namespace hsma

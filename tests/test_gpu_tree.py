@@ -109,3 +109,24 @@ def test_tree_with_the_unmasked_near_set(P):
     E, F, pot, L = run(P, c, x, q, tree_order=10, sphere_mask=0)
     assert abs(E - ref["energy"]) <= 1e-5 * abs(ref["energy"])
     assert frms(F, ref["forces"]) <= 2e-5
+
+
+def test_tree_parts_agree_and_each_is_repeatable(P):
+    # the evaluation's work items split each task's lists into tree_parts
+    # parts; a split changes only the FP32 summation order, and whichever
+    # warp takes an item computes it the same way
+    c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
+    x, q = workloads.electrolyte(c)
+    ref = None
+    for parts in (1, 2, 3, 4, 8):
+        E1, F1, _, _ = run(P, c, x, q, tree_parts=parts)
+        E2, F2, _, _ = run(P, c, x, q, tree_parts=parts)
+        assert E1 == E2 and np.array_equal(F1, F2), parts
+        if ref is None:
+            ref = (E1, F1)
+        assert abs(E1 - ref[0]) <= 1e-6 * abs(ref[0]) and frms(F1, ref[1]) <= 1e-6, parts
+    h = P.HSMA(c.box, 3, c.p, c.M, near_tree=1)
+    for bad in (0, 9, 2.5):
+        with pytest.raises(P.HSMAError):
+            h.set_option("tree_parts", bad)
+    h.close()
