@@ -152,6 +152,11 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "tree_leaf_level"   leaf level L of the tree (8^L leaves over the root
  *                       cube), 2..6; 0 (default) = about 32 images per
  *                       occupied leaf.
+ *   "guard_selftest"    1 = overwrite one byte of the guard band of this
+ *                       handle's position buffer (inside its allocation, so
+ *                       an in-bounds write), 0 = restore it; lets a test see
+ *                       "guard_violations" count it.  Needs an evaluation
+ *                       first, else HSMA_ERR_ARG.
  *   "tree_parts"        1..8 (default 2): each 32-target task of the tree
  *                       evaluation is split into this many work items (every
  *                       tree_parts-th batch of each interaction list), which
@@ -205,7 +210,12 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
  * "far_chunks", "far_field", "tree_levels" (leaf level L of the tree, 0 when
  * off), "kernels_per_eval" (kernel launches of one evaluation), "grid",
- * "slots", "kernel", "tile_targets".
+ * "slots", "kernel", "tile_targets", "guard_violations" (process-wide: how
+ * many device buffers of this library, live or already freed, have had the
+ * 256-byte guard band behind their end overwritten; every buffer is
+ * allocated with such a band holding a fixed pattern, compared when the
+ * buffer is freed and, for live buffers, when this key is read; waits for
+ * the device first).
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);

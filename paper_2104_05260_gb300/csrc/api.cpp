@@ -22,25 +22,93 @@ using hsma::DevBuf;
 
 namespace hsma {
 
+// Guard bands (a bounds check that needs no sanitizer): every device buffer
+// is allocated kGuardBytes longer than asked and the tail is filled with
+// kGuardByte.  The live buffers are kept in a process-wide table; a buffer's
+// tail is compared with the pattern when it is freed and, for all live
+// buffers, when the info key "guard_violations" is read.  A kernel that wrote
+// past the end of its buffer shows up as a changed tail.
+namespace {
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+std::mutex g_guard_mu;
+std::map<void*, size_t>& guard_table() {
+  static std::map<void*, size_t>* t = new std::map<void*, size_t>();   // outlives static destructors
+  return *t;
+}
+int64_t g_guard_bad_freed = 0;
+
+// 1 if the tail of the buffer at p (n bytes asked) differs from the pattern
+int guard_changed(void* p, size_t n) {
+  unsigned char buf[kGuardBytes];
+  if (cudaMemcpy(buf, (char*)p + n, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;   // no context left (process exit): nothing to compare
+  }
+  for (size_t i = 0; i < kGuardBytes; ++i)
+    if (buf[i] != kGuardByte) return 1;
+  return 0;
+}
+}  // namespace
+
 int DevBuf::ensure(size_t bytes) {
   if (bytes <= n) return 0;
-  if (p) cudaFree(p);
-  p = nullptr;
-  n = 0;
+  release();
   if (bytes == 0) return 0;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (cudaMalloc(&p, bytes + kGuardBytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
     return -1;
   }
+  if (cudaMemset((char*)p + bytes, kGuardByte, kGuardBytes) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p);
+    p = nullptr;
+    return -1;
+  }
   n = bytes;
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  guard_table()[p] = n;
   return 0;
 }
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    // the buffer's last users may still be running on a non-blocking stream
+    if (cudaDeviceSynchronize() != cudaSuccess) cudaGetLastError();
+    const int bad = guard_changed(p, n);
+    {
+      std::lock_guard<std::mutex> lk(g_guard_mu);
+      guard_table().erase(p);
+      g_guard_bad_freed += bad;
+    }
+    cudaFree(p);
+  }
   p = nullptr;
   n = 0;
+}
+
+// Buffers, live or freed, whose guard band has been written.
+int64_t guard_violations() {
+  if (cudaDeviceSynchronize() != cudaSuccess) cudaGetLastError();
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  int64_t bad = g_guard_bad_freed;
+  for (const auto& e : guard_table()) bad += guard_changed(e.first, e.second);
+  return bad;
+}
+
+// Write one byte into (value 1) or restore (value 0) the guard band of the
+// buffer at p, n bytes long: it lies inside the allocation, so this is an
+// ordinary in-bounds write.  It exists so that a test can see the check work.
+int guard_selftest(void* p, size_t n, int value) {
+  if (!p) return -1;
+  if (cudaMemset((char*)p + n, value ? 0x00 : kGuardByte, 1) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return 0;
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -775,6 +843,10 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
       return fail(h, HSMA_ERR_ARG, "surface_rule 1 needs M to be a Fibonacci number >= 13");
     h->gp.surface_rule = (int)v;
     h->geo_dirty = true;
+  } else if (k == "guard_selftest") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "guard_selftest must be 0 or 1");
+    if (guard_selftest(h->d_x.p, h->d_x.n, (int)v))
+      return fail(h, HSMA_ERR_ARG, "guard_selftest needs an evaluation first");
   } else if (k == "near_tree") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "near_tree must be 0 or 1");
     h->near_tree = (int)v;
@@ -874,6 +946,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "far_field") *value = h->far_series;
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
+  else if (k == "guard_violations") *value = (double)guard_violations();
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;
   else if (k == "tile_targets") *value = pair_tile_targets(h->precision, eff_tpt(h));

@@ -22,6 +22,8 @@ struct DevBuf {
 struct Server;  // request loop state (serve.cpp)
 
 bool is_device_ptr(const void* ptr);
+int64_t guard_violations();
+int guard_selftest(void* p, size_t n, int value);
 double estimate_images(const Geometry& g, int64_t N);
 int choose_chunks(int tiles, int slots, double n_src, int min_len);
 

@@ -236,6 +236,29 @@ def test_errors_are_reported(P):
     h.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_degenerate_inputs(P, prec):
+    # no particles: an argument error, and the handle stays usable
+    h = P.HSMA((10.0, 10.0, 10.0), 3, 4, 200, precision=prec)
+    with pytest.raises(P.HSMAError) as e:
+        h.eval(np.zeros((0, 3)), np.zeros(0))
+    assert e.value.code == -1
+    # uncharged particles (one alone, or many): energy, forces and potential
+    # are exactly zero, with no division by zero for the lone particle
+    rng = np.random.default_rng(3)
+    for n in (1, 37):
+        x = rng.uniform(0.0, 10.0, (n, 3))
+        E, F, pot = h.eval(x, np.zeros(n), potential=True)
+        assert E == 0.0 and np.all(F == 0.0) and np.all(pot == 0.0)
+    # and a charged system afterwards still matches the oracle
+    c = workloads.small_case(64, dims=3, box=(10.0, 10.0, 10.0), p=4, M=200, seed=64)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 4, 200), x, q)
+    E, F, _ = h.eval(x, q)
+    h.close()
+    assert rel(E, ref["energy"]) <= E_TOL[prec] and frms(F, ref["forces"]) <= F_TOL[prec]
+
+
 def test_repeatable_bitwise(P):
     c = workloads.case(1)
     x, q = workloads.electrolyte(c)
