@@ -59,6 +59,14 @@ def test_exponential_integral_and_convergence_rate():
     assert err[233] < err[89] * (89 / 233) ** 6
 
 
+def test_harmonic_products_are_integrated_exactly():
+    # int Y_nm Y_n'm' dS = delta for the real orthonormal harmonics (n, n' <= 8)
+    y, w = O.fibonacci_lattice(987, 1.0)
+    Y = H.solid(8, y, 1.0)
+    G = (Y * w[:, None]).T @ Y
+    assert np.abs(G - np.eye(len(G))).max() < 1e-12
+
+
 def test_single_layer_identity():
     # int Y_nm(yhat) / |yhat - r| dS = 4 pi / (2n+1) |r|^n Y_nm(rhat) for |r| < 1,
     # the identity behind the surface charges
