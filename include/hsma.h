@@ -157,7 +157,7 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       an in-bounds write), 0 = restore it; lets a test see
  *                       "guard_violations" count it.  Needs an evaluation
  *                       first, else HSMA_ERR_ARG.
- *   "tree_parts"        1..8 (default 2): each 32-target task of the tree
+ *   "tree_parts"        1..8 (default 4): each 32-target task of the tree
  *                       evaluation is split into this many work items (every
  *                       tree_parts-th batch of each interaction list), which
  *                       a persistent kernel takes from a queue; the items'

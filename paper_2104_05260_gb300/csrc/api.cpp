@@ -312,7 +312,11 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
         for (int k = 2 * m - 1; k > 1; k -= 2) c *= k;
       }
       norm[nn * (P + 1) + m] = (float)c;
-      const double f = 4.0 * 3.14159265358979323846 / (2 * nn + 1) * c * c;   // the evaluation has no norm
+      // the evaluation has no norm; its recursion variable is U_nm / K_nm with
+      // K_nm = prod_{k=m+1..nn} (2k-1)/(k-m), so the stored multipole carries K_nm
+      double K = 1.0;
+      for (int k = m + 1; k <= nn; ++k) K *= (2.0 * k - 1.0) / (double)(k - m);
+      const double f = 4.0 * 3.14159265358979323846 / (2 * nn + 1) * c * c * K;
       fac[nn * nn + nn + m] = (float)f;
       fac[nn * nn + nn - m] = (float)f;
     }

@@ -232,18 +232,30 @@ __global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_c
 template <int P>
 __device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, float x, float y, float z, float* phi,
                                                float* gx, float* gy, float* gz) {
-  // P is a compile-time constant: both loops unroll, the recursion
-  // coefficients fold, and the independent m-chains interleave
+  // P is a compile-time constant: both loops unroll and the recursion
+  // coefficients fold.  A term is u(r^2, z) (C_m Mc + S_m Ms) with
+  // C_m + i S_m = (x + iy)^m, so its gradient is
+  //   2 (x, y, z) du/dr^2 (...) + (0, 0, du/dz|r^2) (...) + u (d/dx, d/dy)(...),
+  // and d/dx (x + iy)^m = m (x + iy)^(m-1), d/dy = i m (x + iy)^(m-1).
+  // Along each m-chain the terms are summed against Mc and Ms separately and
+  // the powers of x + iy are applied once per chain.
+  // The chain variable is v_n = U_n / K_nm with K_nm = prod_{k=m+1..n}
+  // (2k-1)/(k-m), which makes the z-term coefficient of the three-term
+  // recursion 1:  v_n = z rho v_(n-1) - c_nm rho v_(n-2),
+  // c_nm = (n+m-1)(n-m-1) / ((2n-1)(2n-3)).  K_nm is folded into the stored
+  // multipoles (the fac table), so the sums below see U_n M_nm unchanged.
   const float r2 = x * x + y * y + z * z;
   const float rho = 1.0f / r2;
   const float rinv = rsqrtf(r2);
-  float C = 1.0f, S = 0.0f, Cx = 0.0f, Cy = 0.0f, Sx = 0.0f, Sy = 0.0f;
+  const float zr = z * rho;
+  float C = 1.0f, S = 0.0f, C1 = 0.0f, S1 = 0.0f;   // (x + iy)^m and (x + iy)^(m-1)
   float um = rinv;   // r^-(2m+1) for m = 0
-  float p = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+  float p = 0.f, sq = 0.f, sz = 0.f, sx = 0.f, sy = 0.f;
 #pragma unroll
   for (int m = 0; m <= P; ++m) {
-    float u1 = um, z1 = 0.0f, q1 = -((float)m + 0.5f) * rho * um;   // U, dU/dz, dU/d(r^2)
+    float u1 = um, z1 = 0.0f, q1 = -((float)m + 0.5f) * rho * um;   // v, dv/dz, dv/d(r^2)
     float u2 = 0.0f, z2 = 0.0f, q2 = 0.0f;
+    float uc = 0.f, us = 0.f, qc = 0.f, qs = 0.f, zc = 0.f, zs = 0.f;
 #pragma unroll
     for (int n = m; n <= P; ++n) {
       float u, uz, uq;
@@ -251,48 +263,50 @@ __device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, flo
         u = u1; uz = z1; uq = q1;
       } else {
         if (n == m + 1) {
-          const float a = (float)(2 * m + 1) * rho;
-          u = a * z * u1;
-          uz = a * (u1 + z * z1);
-          uq = a * z * q1 - u * rho;
+          u = zr * u1;
+          uz = rho * u1;                 // dv_m/dz = 0
+          uq = zr * q1 - rho * u;
         } else {
-          const float a = ((float)(2 * n - 1) / (float)(n - m)) * rho;
-          const float b = ((float)(n + m - 1) / (float)(n - m)) * rho;
-          u = a * z * u1 - b * u2;
-          uz = a * (u1 + z * z1) - b * z2;
-          uq = a * z * q1 - b * q2 - u * rho;
+          const float b = ((float)((n + m - 1) * (n - m - 1)) / (float)((2 * n - 1) * (2 * n - 3))) * rho;
+          u = zr * u1 - b * u2;
+          uz = rho * (u1 + z * z1) - b * z2;
+          uq = zr * q1 - b * q2 - rho * u;
         }
         u2 = u1; z2 = z1; q2 = q1;
         u1 = u; z1 = uz; q1 = uq;
       }
-      const float Ux = 2.0f * x * uq, Uy = 2.0f * y * uq, Uz = uz + 2.0f * z * uq;
       const int base = n * n + n;
-      if (m == 0) {
-        const float a0 = Mc[base];
-        p += a0 * u;
-        ax += a0 * Ux;
-        ay += a0 * Uy;
-        az += a0 * Uz;
-      } else {
-        const float ac = Mc[base + m], as = Mc[base - m];
-        const float wv = ac * C + as * S;
-        const float wx = ac * Cx + as * Sx, wy = ac * Cy + as * Sy;
-        p += u * wv;
-        ax += Ux * wv + u * wx;
-        ay += Uy * wv + u * wy;
-        az += Uz * wv;
+      const float ac = Mc[base + m];
+      uc += u * ac;
+      qc += uq * ac;
+      zc += uz * ac;
+      if (m > 0) {
+        const float as = Mc[base - m];
+        us += u * as;
+        qs += uq * as;
+        zs += uz * as;
       }
     }
+    if (m == 0) {
+      p += uc;
+      sq += qc;
+      sz += zc;
+    } else {
+      p += C * uc + S * us;
+      sq += C * qc + S * qs;
+      sz += C * zc + S * zs;
+      sx += (float)m * (C1 * uc + S1 * us);
+      sy += (float)m * (C1 * us - S1 * uc);
+    }
+    C1 = C; S1 = S;
     const float nC = x * C - y * S, nS = x * S + y * C;
-    const float nCx = C + x * Cx - y * Sx, nSx = S + x * Sx + y * Cx;
-    const float nCy = x * Cy - S - y * Sy, nSy = x * Sy + C + y * Cy;
-    C = nC; S = nS; Cx = nCx; Sx = nSx; Cy = nCy; Sy = nSy;
+    C = nC; S = nS;
     um *= rho;
   }
   *phi += p;
-  *gx += ax;
-  *gy += ay;
-  *gz += az;
+  *gx += 2.0f * x * sq + sx;
+  *gy += 2.0f * y * sq + sy;
+  *gz += 2.0f * z * sq + sz;
 }
 
 __device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y, int* z) {
