@@ -63,27 +63,46 @@ __global__ void k_tree_bin(const float4* __restrict__ pts, int n_fixed, const De
   }
 }
 
-// exclusive scan of count[0..n) into start[0..n], one block
+// exclusive scan of count[0..n) into start[0..n], one block: warp w takes a
+// contiguous range and reads it 32 entries at a time (coalesced), with warp
+// shuffles for the running prefix; a second pass writes the offsets
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(1024) k_tree_scan(const int* __restrict__ count, int n, int* __restrict__ start) {
-  __shared__ int sh[1024];
-  const int per = (n + 1023) / 1024;
-  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+  __shared__ int wsum[32];
+  __shared__ int total;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per_warp = ((n + 31) / 32 + 31) / 32 * 32;
+  const int b0 = min(n, warp * per_warp), b1 = min(n, b0 + per_warp);
   int s = 0;
-  for (int b = b0; b < b1; ++b) s += count[b];
-  sh[threadIdx.x] = s;
+  for (int b = b0 + lane; b < b1; b += 32) s += count[b];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (lane == 0) wsum[warp] = s;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int v = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
-    __syncthreads();
-    sh[threadIdx.x] += v;
-    __syncthreads();
+  if (warp == 0) {
+    const int v = wsum[lane];
+    const int incl = warp_incl_scan(v, lane);
+    wsum[lane] = incl - v;
+    if (lane == 31) total = incl;
   }
-  int run = sh[threadIdx.x] - s;
-  for (int b = b0; b < b1; ++b) {
-    start[b] = run;
-    run += count[b];
+  __syncthreads();
+  int carry = wsum[warp];
+  for (int b = b0; b < b1; b += 32) {
+    const int i = b + lane;
+    const int v = i < b1 ? count[i] : 0;
+    const int incl = warp_incl_scan(v, lane);
+    if (i < b1) start[i] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if (threadIdx.x == 1023) start[n] = sh[1023];
+  if (threadIdx.x == 0) start[n] = total;
 }
 
 __global__ void k_tree_fill(int n_fixed, const DevScalars* sc, const int* __restrict__ key,
@@ -95,20 +114,54 @@ __global__ void k_tree_fill(int n_fixed, const DevScalars* sc, const int* __rest
   }
 }
 
-// each bin's entries in increasing index order (deterministic sums)
+// each bin's entries in increasing index order (deterministic sums): one
+// warp per bin; the entries (distinct indices) are ranked by counting the
+// smaller ones, up to kSortPer per lane in registers, then written in place.
+// Larger bins (never seen at the planned leaf sizes) fall back to an
+// insertion sort by one lane.
+constexpr int kSortPer = 8;
+
 __global__ void k_tree_sort_bins(const int* __restrict__ start, int n_bins, int* __restrict__ order) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n_bins) return;
-  int* l = order + start[b];
-  const int n = start[b + 1] - start[b];
-  for (int k = 1; k < n; ++k) {
-    const int v = l[k];
-    int j = k - 1;
-    while (j >= 0 && l[j] > v) {
-      l[j + 1] = l[j];
-      --j;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < n_bins; b += warps) {
+    int* l = order + start[b];
+    const int n = start[b + 1] - start[b];
+    if (n <= 1) continue;
+    if (n <= 32 * kSortPer) {
+      int v[kSortPer], rank[kSortPer];
+#pragma unroll
+      for (int t = 0; t < kSortPer; ++t) {
+        const int i = t * 32 + lane;
+        v[t] = i < n ? l[i] : 0x7fffffff;
+        rank[t] = 0;
+      }
+#pragma unroll
+      for (int t2 = 0; t2 < kSortPer; ++t2) {
+        if (t2 * 32 >= n) break;
+        for (int j = 0; j < 32; ++j) {
+          const int o = __shfl_sync(0xffffffffu, v[t2], j);
+#pragma unroll
+          for (int t = 0; t < kSortPer; ++t) rank[t] += (o < v[t]) ? 1 : 0;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kSortPer; ++t)
+        if (t * 32 + lane < n) l[rank[t]] = v[t];
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int k = 1; k < n; ++k) {
+        const int x = l[k];
+        int j = k - 1;
+        while (j >= 0 && l[j] > x) {
+          l[j + 1] = l[j];
+          --j;
+        }
+        l[j + 1] = x;
+      }
     }
-    l[j + 1] = v;
+    __syncwarp();
   }
 }
 
@@ -528,8 +581,8 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   k_tree_scan<<<1, 1024, 0, s>>>(T.tgt_count, nleaf, T.tgt_start);
   k_tree_fill<<<grid, 256, 0, s>>>(0, T.sc, T.src_key, T.src_start, T.src_cursor, T.src_order);
   k_tree_fill<<<grid, 256, 0, s>>>(T.n_tgt, nullptr, T.tgt_key, T.tgt_start, T.tgt_cursor, T.tgt_order);
-  k_tree_sort_bins<<<(nleaf + 255) / 256, 256, 0, s>>>(T.src_start, nleaf, T.src_order);
-  k_tree_sort_bins<<<(nleaf + 255) / 256, 256, 0, s>>>(T.tgt_start, nleaf, T.tgt_order);
+  k_tree_sort_bins<<<grid, 256, 0, s>>>(T.src_start, nleaf, T.src_order);
+  k_tree_sort_bins<<<grid, 256, 0, s>>>(T.tgt_start, nleaf, T.tgt_order);
   k_tree_gather<<<grid, 256, 0, s>>>(T.src, T.src_order, 0, T.sc, T.src_sorted);
   // multipoles, level by level: items are cells of level il = max(l, L - 1)
   for (int l = 2; l <= t.L; ++l) {
