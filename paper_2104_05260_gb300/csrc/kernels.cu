@@ -180,10 +180,29 @@ __global__ void __launch_bounds__(kScanThreads) k_prep_scan(PrepArgs a, int nblk
   }
 }
 
+// Own-image terms of the shifts that do not reflect (zs = 1): the image
+// lies exactly (sx, sy, zo) from its ion, so 1/|d| and d/|d|^3 depend on the
+// shift alone and are formed once per block (FP64).
+constexpr int kSelfTable = 256;
+
 __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
   __shared__ int sh_off[kIonsPerBlock];
+  __shared__ double sh_self[4][kSelfTable];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * kIonsPerBlock + w;
+  if (a.self)
+    for (int t = threadIdx.x + 1; t < min(a.n_shift, kSelfTable); t += kPrepThreads) {
+      const double* sh = a.shifts + 5 * t;
+      if (sh[2] == 1.0) {
+        const double dx = sh[0], dy = sh[1], dz = sh[3];
+        const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
+        const double inv3 = inv * inv * inv;
+        sh_self[0][t] = inv;
+        sh_self[1][t] = inv3 * dx;
+        sh_self[2][t] = inv3 * dy;
+        sh_self[3][t] = inv3 * dz;
+      }
+    }
   if (threadIdx.x == 0) {
     int o = a.blk[blockIdx.x];
     for (int k = 0; k < kIonsPerBlock; ++k) {   // exclusive prefix over the block's ions
@@ -233,14 +252,21 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
                                      (float)(pz - (double)(float)pz), 0.f);
         if (a.src64) a.src64[k] = make_double4_32a(px, py, pz, qs);
         if (a.self) {
-          const double dx = px - xc, dy = py - yc, dz = pz - zc;
-          const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
-          const double qi = qs * inv;
-          const double q3 = qi * inv * inv;
-          sp += qi;
-          sgx += q3 * dx;
-          sgy += q3 * dy;
-          sgz += q3 * dz;
+          if (sh[2] == 1.0 && s < kSelfTable) {
+            sp += qs * sh_self[0][s];
+            sgx += qs * sh_self[1][s];
+            sgy += qs * sh_self[2][s];
+            sgz += qs * sh_self[3][s];
+          } else {
+            const double dx = px - xc, dy = py - yc, dz = pz - zc;
+            const double inv = rsqrt(dx * dx + dy * dy + dz * dz);
+            const double qi = qs * inv;
+            const double q3 = qi * inv * inv;
+            sp += qi;
+            sgx += q3 * dx;
+            sgy += q3 * dy;
+            sgz += q3 * dz;
+          }
         }
       }
       o += __popc(m);
