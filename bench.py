@@ -175,7 +175,8 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     is 0.8 x the one-at-a-time FP32 capacity measured here on a sample of the
     same requests.  Reports served evals/s, p50/p99 latency (completion -
     arrival, host clock) and the one-at-a-time FP64 and FP32 forms on a
-    stratified sample, extrapolated to the whole stream.
+    stratified sample, extrapolated to the whole stream; then the served
+    capacity, with all requests submitted at once.
     """
     shapes = workloads.serving_stream(n_req, seed=seed)
     reqs = []
@@ -216,6 +217,7 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     tickets = [None] * n_req
     done_t = np.zeros(n_req)
     out = [None] * n_req
+    fbuf = [np.empty((c.N, 3)) for c, _, _ in reqs]      # result buffers, allocated once
     nxt = 0
     pending = set()
     t_start = time.perf_counter()
@@ -227,7 +229,7 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
             pending.add(nxt)
             nxt += 1
         for i in list(pending):
-            r = P.hsma_poll(server, tickets[i], reqs[i][0].N)
+            r = P.hsma_poll(server, tickets[i], reqs[i][0].N, out=fbuf[i])
             if r is not None:
                 done_t[i] = time.perf_counter() - t_start
                 out[i] = r
@@ -237,6 +239,22 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     P.hsma_destroy(server)
     lat = (done_t - arrivals) * 1e3
     span = done_t.max() - arrivals[0]
+
+    # served capacity: the same requests all submitted at once (saturated queue)
+    server = P.hsma_server_create(slots, budget, precision)
+    for p in (6, 8, 10):                       # unit geometries, untimed
+        c, x, q = next(r for r in reqs if r[0].p == p)
+        t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
+        while P.hsma_poll(server, t, c.N) is None:
+            pass
+    t_sat = time.perf_counter()
+    sat_tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
+    # collect in submission order: each poll also advances the server
+    for i in range(n_req):
+        while P.hsma_poll(server, sat_tickets[i], reqs[i][0].N, out=fbuf[i]) is None:
+            pass
+    sat_span = time.perf_counter() - t_sat
+    P.hsma_destroy(server)
     de = [abs(out[i][0] - r64[i][1]) / abs(r64[i][1]) for i in sample]
     # the same error against the energy scale 1/2 sum |q_i Phi_i| (|E| itself can
     # nearly cancel in a random neutral configuration)
@@ -257,6 +275,9 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
             "p99_ms": float(np.percentile(lat, 99)), "mean_N": float(np.mean([c.N for c, _, _ in reqs])),
             "one_at_a_time_fp64_evals_per_s": 1.0 / t64, "one_at_a_time_evals_per_s": 1.0 / t32,
             "served_vs_fp64": (n_req / span) * t64,
+            "saturated_evals_per_s": n_req / sat_span,
+            "saturated_vs_one_at_a_time": (n_req / sat_span) * t32,
+            "saturated_vs_fp64": (n_req / sat_span) * t64,
             "sample": f"{n_sample} requests stratified by N, timed one at a time",
             "max_rel_energy_err_vs_fp64": float(max(de)),
             "median_rel_energy_err_vs_fp64": float(np.median(de)),

@@ -193,10 +193,13 @@ def hsma_submit(server, x, q, box, p, M):
     return t.value
 
 
-def hsma_poll(server, ticket, N):
-    """Returns None while pending, else (energy, forces)."""
+def hsma_poll(server, ticket, N, out=None):
+    """Returns None while pending, else (energy, forces).  out, an (N, 3)
+    float64 array, receives the forces; without it one is allocated."""
     e = ctypes.c_double()
-    f = np.empty((N, 3), dtype=np.float64)
+    f = out if out is not None else np.empty((N, 3), dtype=np.float64)
+    if f.shape != (N, 3) or f.dtype != np.float64 or not f.flags.c_contiguous:
+        raise ValueError("out must be a contiguous float64 array of shape (N, 3)")
     rc = lib().hsma_poll(server, ctypes.c_uint64(ticket), ctypes.cast(ctypes.byref(e), ctypes.c_void_p),
                          ctypes.c_void_p(f.ctypes.data))
     if rc == HSMA_PENDING:
