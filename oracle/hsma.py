@@ -40,7 +40,9 @@ notes of the repository):
     with dn the outward normal derivative, g that face's gamma and Lambda_G the
     periodic discrete DtN map (2D DFT, multiply by |h|, inverse DFT).  These
     rows are weighted by R_c / G (a grid-size-independent surface average in
-    potential units).
+    potential units).  Parity unpinned for these DtN rows: the paper's own
+    discretisation (the 2D-dilation formula) is not available, so only the
+    end result of HSMA2D is pinned, against the Ewald2D image series.
  R6 Surface charges: the single layer sigma = sum A_nm (2n+1) R_s^(n-1)/(4 pi) Y_nm
     reproduces sum A_nm r^n Y_nm inside B (Laplace expansion of 1/|r - y|), so
     Q_m = sum A_nm (2n+1) R_s^(n+1) / M Y_nm(y_m / R_s).
