@@ -328,9 +328,10 @@ def other_cases(P, torch, dev, stream):
             h.close()
         if 0 in energies:
             rec["fp32_vs_fp64_rel_energy"] = abs(energies[1] - energies[0]) / abs(energies[0])
-        if c.dims == 3 and c.N >= 100000:
+        if c.dims == 2 or c.N >= 100000:
             # the tree evaluation of the near field (option near_tree) beside it
-            h = P.HSMA(c.box, c.dims, c.p, c.M, precision=1, near_tree=1)
+            h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=1, near_tree=1,
+                       dtn_grid=c.dtn_grid)
             P.hsma_set_stream(h.h, stream.cuda_stream)
             e = np.zeros(1)
             ft = torch.empty_like(fd)
@@ -345,6 +346,10 @@ def other_cases(P, torch, dev, stream):
             rec["tree_fp32_evals_per_s"] = 1e3 * max(3, n32) / a.elapsed_time(b)
             rec["tree_levels"] = int(P.hsma_get_info(h.h, "tree_levels"))
             rec["tree_vs_dense_rel_energy"] = abs(float(e[0]) - energies[1]) / abs(energies[1])
+            # fd holds the forces of the last dense run (FP64 where it ran, else FP32)
+            ref = "fp64" if 0 in energies else "fp32"
+            rec["tree_vs_" + ref + "_rel_force_rms"] = float(
+                torch.sqrt(((ft - fd) ** 2).sum(1).mean() / (fd ** 2).sum(1).mean()).item())
             h.close()
         out[c.name] = rec
     return out

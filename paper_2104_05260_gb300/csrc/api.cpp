@@ -179,7 +179,8 @@ hsma_ctx::~hsma_ctx() {
                     &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
                     &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2, &d_tkey_s,
                     &d_tcnt_s, &d_tstart_s, &d_tcur_s, &d_tord_s, &d_tkey_t, &d_tcnt_t, &d_tstart_t, &d_tcur_t,
-                    &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac, &d_src32lo, &d_tgt32lo})
+                    &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac, &d_src32lo, &d_tgt32lo,
+                    &d_imgshift})
     b->release();
   if (gexec) cudaGraphExecDestroy(gexec);
   if (h_sc) cudaFreeHost(h_sc);
@@ -321,6 +322,7 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
       fac[nn * nn + nn - m] = (float)f;
     }
   const bool bad = h->d_tkey_s.ensure(simg * 4) || h->d_tord_s.ensure(simg * 4) || h->d_tsrc.ensure(simg * 16) ||
+                   h->d_imgshift.ensure(simg * 4) ||
                    h->d_tcnt_s.ensure(nleaf * 4) || h->d_tcur_s.ensure(nleaf * 4) ||
                    h->d_tstart_s.ensure((nleaf + 1) * 4) || h->d_tkey_t.ensure(nt * 4) ||
                    h->d_tord_t.ensure(nt * 4) || h->d_tcnt_t.ensure(nleaf * 4) || h->d_tcur_t.ensure(nleaf * 4) ||
@@ -362,6 +364,12 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
   T.ld = h->n_tgt1;
   T.parts = h->tree_parts;
   T.out_parts = (double*)h->d_tpart.p;     // the P2M partials are consumed before the evaluation
+  T.xc = (const double*)h->d_xc.p;
+  T.q = (const double*)h->d_q.p;
+  T.shifts = (const double*)h->d_shifts.p;
+  T.ioff = (const int*)h->d_ioff.p;
+  T.icnt = (const int*)h->d_cnt.p;
+  T.img_shift = (const int*)h->d_imgshift.p;
   cudaError_t e = launch_tree(T, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "tree launch");
   return HSMA_OK;
@@ -470,6 +478,8 @@ int stage_prep(hsma_ctx* h, int64_t N) {
   // FP32 path: each ion's own shifted images are summed in FP64 by the prep
   // kernels and skipped by the FP32 pair kernel
   a.self = prec ? (double*)h->d_self.p : nullptr;
+  // the tree sums an ion's own images in FP64 from their shift indices
+  a.img_shift = (prec && h->near_tree) ? (int*)h->d_imgshift.p : nullptr;
   const int nblk = (int)((N + 255) / 256);
   cudaError_t e = launch_prep(a, nblk, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "prep launch");

@@ -49,7 +49,8 @@ struct hsma_ctx {
   hsma::DevBuf d_x, d_q, d_xc, d_cnt, d_blk, d_blkq, d_blkaq, d_src32, d_src64, d_tgt32, d_tgt64,
       d_part, d_fpart, d_forces, d_pot, d_grad, d_blke, d_sc, d_ioff, d_self, d_mask,
       d_red1, d_red2,  // chunk-reduced partials of the near/check and far launches
-      d_src32lo, d_tgt32lo;  // FP32 rounding remainders of images and targets (precision 2)
+      d_src32lo, d_tgt32lo,  // FP32 rounding remainders of images and targets (precision 2)
+      d_imgshift;            // shift index of each section-1 image (tree evaluation)
   hsma::DevScalars* h_sc = nullptr;  // pinned
   cudaEvent_t ev[kEvents] = {};
   double times[6] = {0, 0, 0, 0, 0, 0};

@@ -47,6 +47,7 @@ struct PrepArgs {
   unsigned* mask;        // N x mwords: bit s-1 set when shift s puts the ion's image in B
   int mwords;            // ceil((n_shift - 1) / 32)
   double* self;          // 4 x N: FP64 sums over each ion's own images, or NULL
+  int* img_shift;        // Ns - N: shift index of each section-1 image, or NULL
 };
 
 // One generic pair-sum launch: targets x sources -> per-chunk partial sums of
@@ -120,6 +121,13 @@ struct TreeLaunch {
   int ld;
   int parts;             // items per task of the evaluation (each a partial sum)
   double* out_parts;     // parts * 4 * ld partials, summed into out in part order
+  // own images of the ion targets, summed in FP64 by the direct pairs
+  const double* xc;      // n_ions*3 box-centred FP64 positions
+  const double* q;       // n_ions charges (neutral residual: sc->qcorr)
+  const double* shifts;  // n_shift*5 (sx, sy, zs, zo, f)
+  const int* ioff;       // n_ions: first section-1 image of each ion
+  const int* icnt;       // n_ions: its number of section-1 images
+  const int* img_shift;  // section-1 image (index - n_ions) -> shift index
 };
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
 size_t tree_eval_smem(int P);

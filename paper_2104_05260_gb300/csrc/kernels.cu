@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
         const double py = __dadd_rn(yc, sh[1]);
         const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
         const int k = o + __popc(m & ((1u << lane) - 1u));
+        if (a.img_shift) a.img_shift[k - a.N] = s;
         const double qs = sh[4] * qj;
         if (a.src32) a.src32[k] = make_float4((float)px, (float)py, (float)pz, (float)qs);
         if (a.src32lo)

@@ -385,6 +385,19 @@ __global__ void k_tree_tasks(const int* __restrict__ tgt_start, int n_cells, int
   if (G < n_cells) count[G] = (tgt_start[(G + 1) << 3] - tgt_start[G << 3] + 31) >> 5;
 }
 
+// What the direct pairs need to sum an ion's own images in FP64: an ion
+// close to a dielectric interface has its own reflection 2d away, where
+// rounding the coordinates to FP32 would spoil a large term.
+struct OwnImages {
+  const DevScalars* sc;
+  const double* xc;
+  const double* q;
+  const double* shifts;
+  const int* ioff;
+  const int* icnt;
+  const int* img_shift;
+};
+
 template <int P>
 __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
                                                                int n_ions, const int* __restrict__ tgt_start,
@@ -395,7 +408,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
                                                                const float* __restrict__ M,
                                                                const int* __restrict__ task_start, int n_cells,
                                                                int S, int* __restrict__ queue,
-                                                               double* __restrict__ out, int ld) {
+                                                               double* __restrict__ out, int ld, OwnImages own) {
   // Persistent warps, no block barriers: each warp takes the next item from
   // the queue, compacts each level's list itself and stages multipoles in its
   // own slice of shared memory.
@@ -496,7 +509,11 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       gz += (double)fz * (double)(inv_w * inv_w);
     }
     // direct pairs: the 4 x 4 x 4 leaves around G, each target its own 27
-    // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is skipped
+    // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is
+    // skipped and its other own images are summed in FP64 from the shift
+    // table (the same terms as the prep's own-image sums)
+    const bool ion = active && ti < n_ions;
+    const int own0 = ion ? own.ioff[ti] : 0, own_n = ion ? own.icnt[ti] : 0;
     for (int j = part; j < 64; j += S) {
       const int ox = 2 * gx0 - 1 + (j & 3), oy = 2 * gy0 - 1 + ((j >> 2) & 3), oz = 2 * gz0 - 1 + (j >> 4);
       if (ox < 0 || oy < 0 || oz < 0 || ox >= nsideL || oy >= nsideL || oz >= nsideL) continue;
@@ -516,7 +533,24 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
         const int nb = min(32, s1 - sb);
         if (take)
           for (int k = 0; k < nb; ++k) {
-            if (ti < n_ions && sid[k] == ti) continue;
+            const int sidx = sid[k];
+            if (ion && (sidx == ti || (unsigned)(sidx - own0) < (unsigned)own_n)) {
+              if (sidx != ti) {
+                const double* sh = own.shifts + 5 * own.img_shift[sidx - n_ions];
+                const double xi = own.xc[3 * (size_t)ti], yi = own.xc[3 * (size_t)ti + 1];
+                const double zi = own.xc[3 * (size_t)ti + 2];
+                const double ddx = __dadd_rn(xi, sh[0]) - xi, ddy = __dadd_rn(yi, sh[1]) - yi;
+                const double ddz = __dadd_rn(__dmul_rn(sh[2], zi), sh[3]) - zi;
+                const double qs = sh[4] * (own.q[ti] - own.sc->qcorr);
+                const double inv = rsqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                const double qi = qs * inv, q3 = qi * inv * inv;
+                phi += qi;
+                gx += q3 * ddx;
+                gy += q3 * ddy;
+                gz += q3 * ddz;
+              }
+              continue;
+            }
             const float4 sv = stile[k];
             const float dx = sv.x - p.x, dy = sv.y - p.y, dz = sv.z - p.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
@@ -612,12 +646,13 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   k_tree_scan<<<1, 1024, 0, s>>>(task_count, n_cells, task_start);
   e = cudaMemsetAsync(queue, 0, 4, s);
   if (e != cudaSuccess) return e;
+  const OwnImages own{T.sc, T.xc, T.q, T.shifts, T.ioff, T.icnt, T.img_shift};
   const size_t sm = tree_eval_smem(t.P);
   const int eval_grid = 5 * tree_sm_count();
 #define HSMA_TREE_EVAL(PP)                                                                                \
   k_tree_eval<PP><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order,        \
                                                       T.src_sorted, T.src_order, T.src_start, T.M, task_start, \
-                                                      n_cells, T.parts, queue, T.out_parts, T.ld)
+                                                      n_cells, T.parts, queue, T.out_parts, T.ld, own)
   switch (t.P) {
     case 4: HSMA_TREE_EVAL(4); break;
     case 6: HSMA_TREE_EVAL(6); break;

@@ -50,10 +50,13 @@ def test_tree_matches_oracle_and_converges(P):
     assert errs[3][0] <= 2e-5 and errs[3][1] <= 1e-5, errs
 
 
-@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.5, -0.3)])
-def test_tree_2d(P, gam):
+@pytest.mark.parametrize("margin", [0.2, 1e-3])
+@pytest.mark.parametrize("gam", [(-0.95, -0.95), (0.5, -0.3), (0.95, 0.95)])
+def test_tree_2d(P, gam, margin):
+    # with a margin of 1e-3 some ions sit next to an interface, 2e-3 or less
+    # from their own reflection: that pair is summed in FP64
     c = workloads.small_case(2000, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=gam, G=24, seed=12)
-    x, q = workloads.electrolyte(c, margin=0.2)
+    x, q = workloads.electrolyte(c, margin=margin)
     st = O.make_setup(c.box, 2, 6, 600, gam[0], gam[1], dtn_grid=24)
     ref = O.evaluate(st, x, q)
     E, F, pot, L = run(P, c, x, q, tree_order=10)
