@@ -145,8 +145,9 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       at each target, direct FP32 pairs with the 27
  *                       neighbouring leaves.  An approximation of the sums:
  *                       at tree_order 10, force RMS about 2e-6 and energy
- *                       4e-6 relative to the direct sums.  Needs precision 1;
- *                       0 (default) = direct sums.
+ *                       4e-6 relative to the direct sums.  Needs precision 1
+ *                       (an evaluation at precision 0 or 2 returns
+ *                       HSMA_ERR_ARG); 0 (default) = direct sums.
  *   "tree_order"        expansion order of the tree: 4, 6, 8, 10 (default),
  *                       12 or 14.
  *   "tree_leaf_level"   leaf level L of the tree (8^L leaves over the root

@@ -423,7 +423,7 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   if (prec == 2) bad = bad || h->d_src32lo.ensure(simg * 16) || h->d_tgt32lo.ensure(nt * 16);
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
   if (h->near_tree) {
-    if (prec == 0) return fail(h, HSMA_ERR_ARG, "near_tree needs precision 1 (FP32 pair arithmetic)");
+    if (prec != 1) return fail(h, HSMA_ERR_ARG, "near_tree needs precision 1 (FP32 pair arithmetic)");
     int rc = plan_tree(h, n, nt, simg);
     if (rc) return rc;
   }

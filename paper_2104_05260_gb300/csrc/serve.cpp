@@ -73,6 +73,8 @@ struct Slot {
   Request* req = nullptr;
   const UnitGeo* geo = nullptr;
   double box[3] = {0, 0, 0};
+  double* h_shifts = nullptr;   // pinned staging of the shift table (no stream sync on upload)
+  size_t h_shifts_n = 0;        // its capacity in doubles
 };
 
 struct Server {
@@ -161,7 +163,22 @@ static int bind_request(Server* s, Slot& sl, Request* r, std::string* err) {
     g.nv = u.nv;
     g.nA = u.nA;
     g.rank = u.rank;
-    std::vector<double> sh(g.shifts.size() * 5);
+    // the slot's previous request has retired, so its pinned staging buffer
+    // is no longer read by a pending copy
+    const size_t nsh = g.shifts.size() * 5;
+    if (sl.h_shifts_n < nsh) {
+      if (sl.h_shifts) cudaFreeHost(sl.h_shifts);
+      sl.h_shifts = nullptr;
+      sl.h_shifts_n = 0;
+      if (cudaMallocHost((void**)&sl.h_shifts, nsh * 8) != cudaSuccess) {
+        cudaGetLastError();
+        sl.h_shifts = nullptr;
+        *err = "pinned shift buffer";
+        return HSMA_ERR_NOMEM;
+      }
+      sl.h_shifts_n = nsh;
+    }
+    double* sh = sl.h_shifts;
     for (size_t i = 0; i < g.shifts.size(); ++i) {
       sh[5 * i] = g.shifts[i].sx;
       sh[5 * i + 1] = g.shifts[i].sy;
@@ -170,7 +187,7 @@ static int bind_request(Server* s, Slot& sl, Request* r, std::string* err) {
       sh[5 * i + 4] = g.shifts[i].f;
     }
     const size_t M = g.par.M;
-    if (h->d_shifts.ensure(sh.size() * 8) || h->d_v.ensure((size_t)g.nv * 8) ||
+    if (h->d_shifts.ensure(nsh * 8) || h->d_v.ensure((size_t)g.nv * 8) ||
         h->d_A.ensure((size_t)g.nA * 8) || h->d_cphi.ensure((size_t)g.n_check * 8) ||
         h->d_cdz.ensure((size_t)g.n_check * 8) || h->d_Q.ensure(M * 8) ||
         h->d_s32.ensure(M * 16) || h->d_s64.ensure(M * 32)) {
@@ -178,7 +195,7 @@ static int bind_request(Server* s, Slot& sl, Request* r, std::string* err) {
       return HSMA_ERR_NOMEM;
     }
     // ordered on the server stream after any earlier batch that used them
-    if (cudaMemcpyAsync(h->d_shifts.p, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, h->stream) !=
+    if (cudaMemcpyAsync(h->d_shifts.p, sh, nsh * 8, cudaMemcpyHostToDevice, h->stream) !=
         cudaSuccess) {
       cudaGetLastError();
       *err = "shift upload";
@@ -343,7 +360,10 @@ void server_shutdown(hsma_ctx* h) {
   if (!h->srv) return;
   Server* s = h->srv;
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (Slot& sl : s->slots) delete sl.ctx;
+  for (Slot& sl : s->slots) {
+    delete sl.ctx;
+    if (sl.h_shifts) cudaFreeHost(sl.h_shifts);
+  }
   for (BatchBuf& bb : s->bufs) {
     if (bb.h_desc) cudaFreeHost(bb.h_desc);
     if (bb.h_start) cudaFreeHost(bb.h_start);

@@ -82,9 +82,12 @@ def test_tree_is_repeatable_and_matches_dense_at_bench_size(P):
 def test_tree_rejects_fp64_and_bad_order(P):
     c = workloads.case(1)
     x, q = workloads.electrolyte(c)
-    h = P.HSMA(c.box, 3, c.p, c.M, precision=0, near_tree=1)
-    with pytest.raises(P.HSMAError):
-        h.eval(x, q)
+    for prec in (0, 2):                    # the tree is an FP32 path only
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=prec, near_tree=1)
+        with pytest.raises(P.HSMAError):
+            h.eval(x, q)
+        h.close()
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, near_tree=1)
     with pytest.raises(P.HSMAError):
         h.set_option("tree_order", 40)
     h.close()

@@ -55,9 +55,12 @@ def test_no_band_is_written_by_the_evaluation_paths(P, prec):
         (workloads.small_case(302, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=(0.5, -0.3), G=24,
                               seed=8), {"dtn_grid": 24}),
     ]
-    if prec:
+    if prec == 1:                                # the tree is an FP32 path only
         runs.append((workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=9),
                      {"near_tree": 1, "tree_parts": 3}))
+        runs.append((workloads.small_case(1000, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600,
+                                          gammas=(0.95, 0.95), G=24, seed=10),
+                     {"near_tree": 1, "dtn_grid": 24}))
     for c, opt in runs:
         x, q = workloads.electrolyte(c, margin=1e-3) if c.dims == 2 else workloads.electrolyte(c)
         h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=prec, **opt)
