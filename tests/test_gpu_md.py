@@ -192,3 +192,25 @@ def test_slab_density_histogram_counts_every_ion(P):
     assert np.all((xs[:, 2] > 0) & (xs[:, 2] < box[2]))
     md.close()
     h.close()
+
+
+def test_md_with_the_tree_and_with_exact_differences(P):
+    # the MD step graph captures whichever electrostatics path the handle
+    # runs: the tree evaluation (persistent kernel, work queue) and the
+    # exact-difference pairs give the same short trajectory as the dense
+    # paths within their accuracy
+    x, v, q, box = system(n_side=8, L=12.0, seed=5)
+    out = {}
+    for label, opt in (("fp64", dict(precision=0)), ("fp32", dict(precision=1)),
+                       ("tree", dict(precision=1, near_tree=1)), ("exact", dict(precision=2))):
+        h = P.HSMA(box, 3, 6, 400, coulomb_prefactor=1.0, **opt)
+        md = P.MD(h, x, v, q, dt=0.002, kT=1.0, tdamp=0.1)
+        rows = md.run(20)
+        out[label] = (md.get("x_unwrapped"), rows)
+        md.close()
+        h.close()
+    ref_x, ref_rows = out["fp64"]
+    for label, tol in (("fp32", 1e-6), ("tree", 1e-6), ("exact", 1e-8)):
+        xs, rows = out[label]
+        assert np.abs(xs - ref_x).max() < tol, label
+        assert np.allclose(rows[:, 2], ref_rows[:, 2], rtol=1e-4, atol=0), label   # Coulomb energy rows
