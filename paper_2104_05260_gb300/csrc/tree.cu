@@ -176,26 +176,44 @@ __global__ void k_tree_gather(const float4* __restrict__ src, const int* __restr
 // One block per item (a cell of level il >= l: a contiguous range of leaves
 // in Morton order), its sources expanded about the centre of its level-l
 // ancestor.  Each lane takes one source and walks all (n, m) by the regular
-// recursions (P a compile-time constant); every term is summed over the
-// warp's 32 sources by a fixed butterfly and kept in a register of the lane
-// that owns it (k mod 32); the warps' rows are added in warp order in FP64.
-// part[item * nc + k].
+// recursions (P a compile-time constant).  The terms come out in a fixed
+// production order j (chain m = 0..P; n = m..P; cos then sin); each group of
+// 32 is written row-wise into a padded 32 x 33 tile of the warp's shared
+// memory and read back column-wise, so lane L sums term 32 g + L over the
+// warp's 32 sources in lane order.  The warps' rows are added in warp order
+// in FP64.  part[item * nc + k], k = n^2 + n +- m.
 constexpr int kP2mThreads = 128;
+
+// production index -> harmonic index k
+template <int P>
+__device__ __forceinline__ int p2m_term(int j) {
+  int m = 0, left = j;
+  while (true) {
+    const int len = m == 0 ? P + 1 : 2 * (P - m + 1);
+    if (left < len) break;
+    left -= len;
+    ++m;
+  }
+  if (m == 0) return left * left + left;
+  const int n = m + left / 2;
+  return n * n + n + ((left & 1) ? -m : m);
+}
 
 template <int P>
 __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int il, const float4* __restrict__ srcs,
                                                           const int* __restrict__ leaf_start,
                                                           double* __restrict__ part) {
   constexpr int nc = (P + 1) * (P + 1);
-  constexpr int nr = (nc + 31) / 32;    // terms owned per lane: k = lane + 32 r
-  __shared__ float acc[kP2mThreads / 32][nr * 32];
+  constexpr int ng = (nc + 31) / 32;    // groups of 32 terms; lane L owns term 32 g + L
+  constexpr int kWarps = kP2mThreads / 32;
+  __shared__ float acc[kWarps][ng * 32];
+  __shared__ float tile[kWarps][32 * 33];
   const int item = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* tw = tile[warp];
   const int shift = 3 * (t.L - il);
   const int s0 = leaf_start[item << shift], s1 = leaf_start[(item + 1) << shift];
-  float own[nr];
-#pragma unroll
-  for (int r = 0; r < nr; ++r) own[r] = 0.0f;
+  for (int g = 0; g < ng; ++g) acc[warp][g * 32 + lane] = 0.0f;
   if (s1 > s0) {
     int ix, iy, iz;
     {
@@ -216,6 +234,7 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
       const float x = (pt.x - cx) * inv_w, y = (pt.y - cy) * inv_w, z = (pt.z - cz) * inv_w;
       const float r2 = x * x + y * y + z * z;
       float C = pt.w, S = 0.0f;   // q (x + iy)^m
+      int j = 0;                  // production index
 #pragma unroll
       for (int m = 0; m <= P; ++m) {
         float v1 = 1.0f, v2 = 0.0f;
@@ -229,18 +248,18 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
             v2 = v1;
             v1 = v;
           }
-          // warp sums by a fixed butterfly; the owner lane of term k keeps it
-          float tc = v1 * C;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(0xffffffffu, tc, o);
-          const int kc = n * n + n + m;
-          own[kc >> 5] += (lane == (kc & 31)) ? tc : 0.0f;
-          if (m > 0) {
-            float ts = v1 * S;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
-            const int ks = n * n + n - m;
-            own[ks >> 5] += (lane == (ks & 31)) ? ts : 0.0f;
+          for (int cs = 0; cs < (m > 0 ? 2 : 1); ++cs) {
+            tw[lane * 33 + (j & 31)] = v1 * (cs == 0 ? C : S);
+            if ((j & 31) == 31 || j == nc - 1) {
+              __syncwarp();
+              float sum = 0.0f;
+#pragma unroll 8
+              for (int r = 0; r < 32; ++r) sum += tw[r * 33 + lane];
+              if ((j & ~31) + lane < nc) acc[warp][(j & ~31) + lane] += sum;
+              __syncwarp();
+            }
+            ++j;
           }
         }
         const float nC = x * C - y * S;
@@ -249,13 +268,12 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
       }
     }
   }
-#pragma unroll
-  for (int r = 0; r < nr; ++r) acc[warp][r * 32 + lane] = own[r];
   __syncthreads();
-  for (int k = threadIdx.x; k < nc; k += kP2mThreads) {
+  for (int jj = threadIdx.x; jj < nc; jj += kP2mThreads) {
     double sum = 0.0;
 #pragma unroll
-    for (int w2 = 0; w2 < kP2mThreads / 32; ++w2) sum += (double)acc[w2][k];
+    for (int w2 = 0; w2 < kWarps; ++w2) sum += (double)acc[w2][jj];
+    const int k = p2m_term<P>(jj);
     part[(size_t)item * nc + k] = sum * (double)t.fac[k];
   }
 }
