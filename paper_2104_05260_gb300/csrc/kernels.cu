@@ -349,13 +349,19 @@ __global__ void __launch_bounds__(kFitThreads) k_gemv_rows(const double* P, int 
   if (threadIdx.x == 0) A[blockIdx.x] = s;
 }
 
-__global__ void k_surface(const double* W, int M, int nA, const double* A, const double* ysurf,
-                          double scale, double* Q, float4* s32, double4_32a* s64) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
-  double s = 0.0;
+// Q = W A, one warp per surface point: the lanes read the row of W
+// coalesced (every 32nd coefficient each) and a fixed butterfly adds them.
+__global__ void __launch_bounds__(256) k_surface(const double* __restrict__ W, int M, int nA,
+                                                 const double* __restrict__ A, const double* __restrict__ ysurf,
+                                                 double scale, double* Q, float4* s32, double4_32a* s64) {
+  const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (m >= M) return;   // uniform per warp
   const double* w = W + (size_t)m * nA;
-  for (int r = 0; r < nA; ++r) s += w[r] * A[r];
+  double s = 0.0;
+  for (int r = lane; r < nA; r += 32) s += w[r] * A[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
   s *= scale;   // W and the surface points of a geometry built for a box scaled by 1/scale
   Q[m] = s;
   const double x = scale * ysurf[3 * m], y = scale * ysurf[3 * m + 1], z = scale * ysurf[3 * m + 2];
@@ -370,7 +376,7 @@ cudaError_t launch_fit(int dims, const double* part, int n_chunks, int ld, int N
   k_check_combine<<<(n_check + 255) / 256, 256, 0, s>>>(part, n_chunks, ld, N, n_check, dims, n_grad, v,
                                                         cphi, cdz);
   k_gemv_rows<<<nA, kFitThreads, 0, s>>>(P, nv, v, A);
-  k_surface<<<(M + 127) / 128, 128, 0, s>>>(W, M, nA, A, ysurf, scale, Q, s32, s64);
+  k_surface<<<(int)(((size_t)M * 32 + 255) / 256), 256, 0, s>>>(W, M, nA, A, ysurf, scale, Q, s32, s64);
   return cudaGetLastError();
 }
 
