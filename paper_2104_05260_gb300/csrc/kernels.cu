@@ -82,35 +82,30 @@ __device__ __forceinline__ bool image_in_B(const PrepArgs& a, int s, double xc, 
   return r2 < a.Rs2;
 }
 
-// Box-centred FP64 position of ion j for the whole warp: lane d < 3 wraps
-// coordinate d (one FP64 division each) and the warp shares the results.
-__device__ __forceinline__ void centre_ion(const PrepArgs& a, int j, double* xc, double* yc, double* zc) {
-  const int lane = threadIdx.x & 31;
-  double v = 0.0;
-  if (lane < 3) {
-    const double u = a.x[3 * (size_t)j + lane];
-    if (lane < 2 || a.dims == 3) {
-      v = wrap_centre(u, a.L[lane]);
-    } else {
-      if (!(u > 0.0 && u < a.L[2])) atomicOr(&a.sc->flags, FLAG_OUT_OF_SLAB);
-      v = __dsub_rn(u, 0.5 * a.L[2]);
-    }
-  }
-  *xc = __shfl_sync(0xffffffffu, v, 0);
-  *yc = __shfl_sync(0xffffffffu, v, 1);
-  *zc = __shfl_sync(0xffffffffu, v, 2);
+// Box-centred FP64 coordinate d of ion j (one thread per coordinate, so a
+// block's wraps share a few warp instructions of the narrow FP64 pipe).
+__device__ __forceinline__ double centre_coord(const PrepArgs& a, int j, int d) {
+  const double u = a.x[3 * (size_t)j + d];
+  if (d < 2 || a.dims == 3) return wrap_centre(u, a.L[d]);
+  if (!(u > 0.0 && u < a.L[2])) atomicOr(&a.sc->flags, FLAG_OUT_OF_SLAB);
+  return __dsub_rn(u, 0.5 * a.L[2]);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_count(PrepArgs a) {
   __shared__ int sc_cnt[kIonsPerBlock];
   __shared__ double sc_q[kIonsPerBlock], sc_aq[kIonsPerBlock];
+  __shared__ double sh_xc[3 * kIonsPerBlock];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * kIonsPerBlock + w;
+  if (threadIdx.x < 3 * kIonsPerBlock) {
+    const int jj = blockIdx.x * kIonsPerBlock + threadIdx.x / 3;
+    if (jj < a.N) sh_xc[threadIdx.x] = centre_coord(a, jj, threadIdx.x % 3);
+  }
+  __syncthreads();
   int c = 0;
   double qj = 0.0;
   if (j < a.N) {
-    double xc, yc, zc;
-    centre_ion(a, j, &xc, &yc, &zc);
+    const double xc = sh_xc[3 * w], yc = sh_xc[3 * w + 1], zc = sh_xc[3 * w + 2];
     if (lane == 0) {
       a.xc[3 * (size_t)j] = xc;
       a.xc[3 * (size_t)j + 1] = yc;
@@ -273,18 +268,18 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
       o += __popc(m);
     }
     if (a.self) {
-      for (int off = 16; off > 0; off >>= 1) {   // fixed-order warp sum
-        sp += __shfl_xor_sync(0xffffffffu, sp, off);
-        sgx += __shfl_xor_sync(0xffffffffu, sgx, off);
-        sgy += __shfl_xor_sync(0xffffffffu, sgy, off);
-        sgz += __shfl_xor_sync(0xffffffffu, sgz, off);
-      }
-      if (lane == 0) {
-        a.self[j] = sp;
-        a.self[(size_t)a.N + j] = sgx;
-        a.self[2 * (size_t)a.N + j] = sgy;
-        a.self[3 * (size_t)a.N + j] = sgz;
-      }
+      // fixed-order warp sums of the four quantities as one reduce-scatter
+      // (6 FP64 adds instead of 20): after the first two halvings lane l
+      // carries quantity c = 2 bit4(l) + bit3(l), then a butterfly over the
+      // remaining lane bits completes it; lane 8c writes it
+      const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+      double k0 = hi16 ? sgy : sp, k1 = hi16 ? sgz : sgx;
+      k0 += __shfl_xor_sync(0xffffffffu, hi16 ? sp : sgy, 16);
+      k1 += __shfl_xor_sync(0xffffffffu, hi16 ? sgx : sgz, 16);
+      double v = hi8 ? k1 : k0;
+      v += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+      for (int off = 4; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if ((lane & 7) == 0) a.self[(size_t)(lane >> 3) * a.N + j] = v;
     }
   }
   const int t = blockIdx.x * kPrepThreads + threadIdx.x;
