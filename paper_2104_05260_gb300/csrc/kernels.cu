@@ -180,11 +180,14 @@ __global__ void __launch_bounds__(kScanThreads) k_prep_scan(PrepArgs a, int nblk
 // shift alone and are formed once per block (FP64).
 constexpr int kSelfTable = 256;
 
+// One thread per ion: its identity entry, then its images in B in shift
+// order (the mask bits k_prep_count set in FP64), then its own-image sums in
+// FP64, added serially in shift order.  A thread per ion rather than a lane
+// per shift: only about a fifth of the shifts put an image in B, and GB300's
+// FP64 pipe charges a warp instruction a full pass whatever its active lanes.
+// Thread t also writes check point t.
 __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
-  __shared__ int sh_off[kIonsPerBlock];
   __shared__ double sh_self[4][kSelfTable];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * kIonsPerBlock + w;
   if (a.self)
     for (int t = threadIdx.x + 1; t < min(a.n_shift, kSelfTable); t += kPrepThreads) {
       const double* sh = a.shifts + 5 * t;
@@ -198,48 +201,42 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
         sh_self[3][t] = inv3 * dz;
       }
     }
-  if (threadIdx.x == 0) {
-    int o = a.blk[blockIdx.x];
-    for (int k = 0; k < kIonsPerBlock; ++k) {   // exclusive prefix over the block's ions
-      const int jj = blockIdx.x * kIonsPerBlock + k;
-      sh_off[k] = o;
-      o += (jj < a.N) ? a.cnt[jj] : 0;
-    }
-  }
   __syncthreads();
+  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
   if (j < a.N) {
-    int o = a.N + sh_off[w];
-    if (a.ioff && lane == 0) a.ioff[j] = o;
+    // blk holds the exclusive image offset of each group of kIonsPerBlock ions
+    int o = a.N + a.blk[j / kIonsPerBlock];
+    for (int i = j - j % kIonsPerBlock; i < j; ++i) o += a.cnt[i];
+    if (a.ioff) a.ioff[j] = o;
     const double xc = a.xc[3 * (size_t)j], yc = a.xc[3 * (size_t)j + 1], zc = a.xc[3 * (size_t)j + 2];
     const double qj = a.q[j] - a.sc->qcorr;
-    if (lane == 0) {
-      if (a.src32) {
-        a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
-        a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
-      }
-      if (a.src32lo) {
-        const float4 lo = make_float4((float)(xc - (double)(float)xc), (float)(yc - (double)(float)yc),
-                                      (float)(zc - (double)(float)zc), 0.f);
-        a.src32lo[j] = lo;
-        a.tgt32lo[j] = lo;
-      }
-      if (a.src64) {
-        a.src64[j] = make_double4_32a(xc, yc, zc, qj);
-        a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
-      }
+    if (a.src32) {
+      a.src32[j] = make_float4((float)xc, (float)yc, (float)zc, (float)qj);
+      a.tgt32[j] = make_float4((float)xc, (float)yc, (float)zc, 0.f);
+    }
+    if (a.src32lo) {
+      const float4 lo = make_float4((float)(xc - (double)(float)xc), (float)(yc - (double)(float)yc),
+                                    (float)(zc - (double)(float)zc), 0.f);
+      a.src32lo[j] = lo;
+      a.tgt32lo[j] = lo;
+    }
+    if (a.src64) {
+      a.src64[j] = make_double4_32a(xc, yc, zc, qj);
+      a.tgt64[j] = make_double4_32a(xc, yc, zc, 0.0);
     }
     // own-image sums in FP64 (FP32 path): the ion's interaction with its own
     // shifted images, which the FP32 pair kernel skips
     double sp = 0.0, sgx = 0.0, sgy = 0.0, sgz = 0.0;
-    for (int s0 = 1, g = 0; s0 < a.n_shift; s0 += 32, ++g) {
-      const int s = s0 + lane;
-      const unsigned m = a.mask[(size_t)j * a.mwords + g];   // decided in FP64 by k_prep_count
-      if ((m >> lane) & 1u) {
+    for (int g = 0; g < a.mwords; ++g) {
+      unsigned m = a.mask[(size_t)j * a.mwords + g];   // decided in FP64 by k_prep_count
+      while (m) {
+        const int s = 32 * g + __ffs(m);   // bit b stands for shift b + 1
+        m &= m - 1u;
         const double* sh = a.shifts + 5 * s;
         const double px = __dadd_rn(xc, sh[0]);
         const double py = __dadd_rn(yc, sh[1]);
         const double pz = __dadd_rn(__dmul_rn(sh[2], zc), sh[3]);
-        const int k = o + __popc(m & ((1u << lane) - 1u));
+        const int k = o++;
         if (a.img_shift) a.img_shift[k - a.N] = s;
         const double qs = sh[4] * qj;
         if (a.src32) a.src32[k] = make_float4((float)px, (float)py, (float)pz, (float)qs);
@@ -265,32 +262,22 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
           }
         }
       }
-      o += __popc(m);
     }
     if (a.self) {
-      // fixed-order warp sums of the four quantities as one reduce-scatter
-      // (6 FP64 adds instead of 20): after the first two halvings lane l
-      // carries quantity c = 2 bit4(l) + bit3(l), then a butterfly over the
-      // remaining lane bits completes it; lane 8c writes it
-      const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-      double k0 = hi16 ? sgy : sp, k1 = hi16 ? sgz : sgx;
-      k0 += __shfl_xor_sync(0xffffffffu, hi16 ? sp : sgy, 16);
-      k1 += __shfl_xor_sync(0xffffffffu, hi16 ? sgx : sgz, 16);
-      double v = hi8 ? k1 : k0;
-      v += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
-      for (int off = 4; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      if ((lane & 7) == 0) a.self[(size_t)(lane >> 3) * a.N + j] = v;
+      a.self[j] = sp;
+      a.self[(size_t)a.N + j] = sgx;
+      a.self[2 * (size_t)a.N + j] = sgy;
+      a.self[3 * (size_t)a.N + j] = sgz;
     }
   }
-  const int t = blockIdx.x * kPrepThreads + threadIdx.x;
-  if (t < a.n_check) {
-    const double* cp = a.check_pts + 3 * (size_t)t;
+  if (j < a.n_check) {
+    const double* cp = a.check_pts + 3 * (size_t)j;
     const double c0 = a.cscale * cp[0], c1 = a.cscale * cp[1], c2 = a.cscale * cp[2];
-    if (a.tgt32) a.tgt32[a.N + t] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
+    if (a.tgt32) a.tgt32[a.N + j] = make_float4((float)c0, (float)c1, (float)c2, 0.f);
     if (a.tgt32lo)
-      a.tgt32lo[a.N + t] = make_float4((float)(c0 - (double)(float)c0), (float)(c1 - (double)(float)c1),
+      a.tgt32lo[a.N + j] = make_float4((float)(c0 - (double)(float)c0), (float)(c1 - (double)(float)c1),
                                        (float)(c2 - (double)(float)c2), 0.f);
-    if (a.tgt64) a.tgt64[a.N + t] = make_double4_32a(c0, c1, c2, 0.0);
+    if (a.tgt64) a.tgt64[a.N + j] = make_double4_32a(c0, c1, c2, 0.0);
   }
 }
 
@@ -299,7 +286,8 @@ cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
   const int nb = (a.N + kIonsPerBlock - 1) / kIonsPerBlock;
   k_prep_count<<<nb, kPrepThreads, 0, s>>>(a);
   k_prep_scan<<<1, kScanThreads, 0, s>>>(a, nb);
-  k_prep_emit<<<prep_blocks(a.N, a.n_check), kPrepThreads, 0, s>>>(a);
+  const int ne = a.N > a.n_check ? a.N : a.n_check;
+  k_prep_emit<<<(ne + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
