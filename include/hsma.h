@@ -158,6 +158,11 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       an in-bounds write), 0 = restore it; lets a test see
  *                       "guard_violations" count it.  Needs an evaluation
  *                       first, else HSMA_ERR_ARG.
+ *   "tree_leaf_mode"    the tree's finest level: 1 = summed directly (every
+ *                       leaf of the 27 neighbours of the target's cell one
+ *                       level up), 2 = leaf multipoles plus direct pairs with
+ *                       the 27 neighbouring leaves, 0 (default) = 1 when the
+ *                       leaves hold about 48 images or fewer, else 2.
  *   "tree_parts"        1..8 (default 4): each 32-target task of the tree
  *                       evaluation is split into this many work items (every
  *                       tree_parts-th batch of each interaction list), which

@@ -294,6 +294,11 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   TreeArgs& t = h->tree_args;
   t.L = L;
   t.P = P;
+  // the finest level summed directly when its leaves are sparse: about 48
+  // images per occupied leaf or fewer (measured at 35 and 92 images a leaf:
+  // direct 3.9 ms against 4.4 ms; leaf multipoles 10.4 ms against 12.0 ms)
+  const double occupied = h->ns_est / ((g.par.sphere_mask ? 0.52 : 1.0) * (double)((size_t)1 << (3 * L)));
+  t.direct_leaf = h->tree_leaf_mode == 1 ? 1 : h->tree_leaf_mode == 2 ? 0 : (occupied <= 48.0 ? 1 : 0);
   t.Rs = (float)half;
   t.D = (float)(2.0 * half);
   t.inv_wL = (float)((double)(1 << L) / (2.0 * half));
@@ -602,11 +607,13 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[5], s);
   // kernels this pipeline launches: prep 3; near 1 and its chunk reduction
-  // 1, or the tree's 9 binning kernels, 2 per multipole level, task count and
-  // scan, evaluation and part reduction; fit 3; far 1; far reduction 1 (not
-  // with one far chunk); assembly 2
+  // 1, or the tree's 9 binning kernels, 2 per multipole level (2..L, or
+  // 2..L-1 with a direct leaf level), task count and scan, evaluation and
+  // part reduction; fit 3; far 1; far reduction 1 (not with one far chunk);
+  // assembly 2
   const bool far_one = h->far_series || h->chunks2 == 1;
-  h->kernels_per_eval = 3 + (h->near_tree ? 13 + 2 * (h->tree_L - 1) : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
+  const int m_levels = h->near_tree ? std::max(0, h->tree_L - 1 - h->tree_args.direct_leaf) : 0;
+  h->kernels_per_eval = 3 + (h->near_tree ? 13 + 2 * m_levels : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
   return HSMA_OK;
 }
 
@@ -873,6 +880,10 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "tree_parts") {
     if (!(v >= 1) || v > 8 || std::floor(v) != v) return fail(h, HSMA_ERR_ARG, "tree_parts must be in [1, 8]");
     h->tree_parts = (int)v;
+    h->plan_N = -1;
+  } else if (k == "tree_leaf_mode") {
+    if (v != 0 && v != 1 && v != 2) return fail(h, HSMA_ERR_ARG, "tree_leaf_mode must be 0, 1 or 2");
+    h->tree_leaf_mode = (int)v;
     h->plan_N = -1;
   } else if (k == "tree_leaf_level") {
     if (!(v >= 0) || v > 6 || v == 1) return fail(h, HSMA_ERR_ARG, "tree_leaf_level must be 0 (automatic) or in [2, 6]");

@@ -79,6 +79,7 @@ struct hsma_ctx {
   int tree_L = 0;
   int tree_leaf_level = 0;   // 0: from the expected image count
   int tree_parts = 4;        // work items per 32-target task of the tree evaluation
+  int tree_leaf_mode = 0;    // 0: by leaf occupancy, 1: direct leaf level, 2: leaf multipoles
   int kernels_per_eval = 0;  // kernel launches of the last enqueued evaluation
   uint64_t plan_gen = 0;     // incremented whenever the plan or its buffers change
   hsma::DevBuf d_tkey_s, d_tcnt_s, d_tstart_s, d_tcur_s, d_tord_s, d_tkey_t, d_tcnt_t, d_tstart_t, d_tcur_t,

@@ -105,6 +105,7 @@ struct TreeArgs {
   int moff[8];           // offset (floats) of level l's multipoles in M
   const float* norm;     // (P+1)^2: c_n0, sqrt(2) c_nm (2m-1)!! at n*(P+1) + m
   const float* fac;      // (P+1)^2: 4 pi/(2n+1) * norm^2 at k = n^2 + n + m
+  int direct_leaf;       // 1: the leaf level is summed directly (no leaf multipoles)
 };
 struct TreeLaunch {
   TreeArgs t;

@@ -1,12 +1,18 @@
 // Tree evaluation of the near-field and check-point sums (the O(N) path the
 // paper takes with an FMM library, Sec. 2.2 last step): the images in B are
-// binned into a uniform octree over the cube [-R_s, R_s]^3, each cell at
-// levels 2..L gets a multipole expansion of order P, and every target sums
+// binned into a uniform octree over the cube [-R_s, R_s]^3 with leaves at
+// level L, cells carry multipole expansions of order P, and every target sums
 //   - the multipoles of the cells in its FMM interaction lists (children of
 //     its parent's neighbours that are not its own neighbours), level by
 //     level (multipole-to-particle), and
-//   - the sources of its 27 neighbouring leaves directly (FP32 pairs),
-// which covers every source exactly once.  The expansion uses the real
+//   - the sources of its neighbourhood directly (FP32 pairs),
+// which covers every source exactly once.  Two layouts of the finest level:
+//   - leaf multipoles: lists at levels 2..L, direct pairs with the 27
+//     neighbouring leaves of the target's own leaf;
+//   - direct leaf level (for sparse leaves): lists at levels 2..L-1, direct
+//     pairs with every leaf of the 27 neighbours of the target's cell G of
+//     level L-1 (the 6 x 6 x 6 leaves around G), the same set for all of G's
+//     targets.  The expansion uses the real
 // orthonormal solid harmonics of the fit (Eq. 5) and the addition theorem
 //   1/|x - s| = sum_n 4 pi/(2n+1) sum_m R_nm(s - c) I_nm(x - c),
 // R_nm = r^n Y_nm, I_nm = r^(-n-1) Y_nm, in coordinates scaled by the cell
@@ -17,8 +23,8 @@
 // Binning uses atomic slots followed by a per-bin sort by index, and every
 // sum has a fixed order, so the result is deterministic.  All arithmetic of
 // the expansions is FP32 with FP64 sums across levels; the identity image of
-// an ion is the only source a target skips (its other images are summed
-// like any source).
+// an ion is skipped and its other own images among the direct pairs are
+// summed in FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -294,9 +300,13 @@ __global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_c
 // index order within each leaf) and one part of their lists.  For levels
 // l < L the interaction list depends only on G's ancestor, so each listed
 // cell's multipole is staged once in shared memory for the warp's targets.
-// At the leaf level the list is the children of G's neighbours; a lane skips
-// the leaves adjacent to its own.  Direct pairs come from the 4 x 4 x 4
-// leaves around G, each lane taking those adjacent to its own leaf.
+// With leaf multipoles, the leaf-level list is the children of G's
+// neighbours, a lane skipping the leaves adjacent to its own, and direct
+// pairs come from the 4 x 4 x 4 leaves around G, each lane taking those
+// adjacent to its own leaf; with a direct leaf level the direct pairs are the
+// 6 x 6 x 6 leaves around G for every lane.  Tiles whose index range holds no
+// identity or own image of any lane's target are summed two sources at a
+// time with paired FP32 instructions.
 //
 // Multipoles hold 4 pi/(2n+1) norm^2 sum q V'T, so the evaluation multiplies
 // by the irregular polynomial U'T alone; 1/(n-m) comes from a table.
@@ -437,6 +447,10 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* sM = tree_smem + (size_t)warp * kBatch * nc4;                        // kBatch multipoles
   float4* stile = reinterpret_cast<float4*>(tree_smem + (size_t)kWarps * kBatch * nc4) + warp * 32;
+  float* tx = reinterpret_cast<float*>(stile);   // the warp's direct-pair tile: x, y, z, q arrays
+  float* ty = tx + 32;
+  float* tz = tx + 64;
+  float* tq = tx + 96;
   int* sid = reinterpret_cast<int*>(reinterpret_cast<float4*>(tree_smem + (size_t)kWarps * kBatch * nc4) +
                                     kTreeThreads) + warp * 32;
   int* slist = sid + (kTreeThreads - warp * 32) + warp * 216;                  // compacted list, 216 per warp
@@ -464,13 +478,17 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
     const bool active = slot < t1;
     const int ti = active ? tgt_order[slot] : tgt_order[t0];
     const float4 p = tgt[ti];
-    // this target's leaf (the first leaf of G whose range holds the slot)
-    int leaf = G << 3;
-    while (leaf < ((G + 1) << 3) - 1 && tgt_start[leaf + 1] <= slot) ++leaf;
-    int lx, ly, lz;
-    morton_decode(leaf, t.L, &lx, &ly, &lz);
+    // this target's leaf (the first leaf of G whose range holds the slot);
+    // only the leaf-multipole layout needs it
+    int lx = 0, ly = 0, lz = 0;
+    if (!t.direct_leaf) {
+      int leaf = G << 3;
+      while (leaf < ((G + 1) << 3) - 1 && tgt_start[leaf + 1] <= slot) ++leaf;
+      morton_decode(leaf, t.L, &lx, &ly, &lz);
+    }
     double phi = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int l = 2; l <= t.L; ++l) {
+    const int l_top = t.direct_leaf ? t.L - 1 : t.L;
+    for (int l = 2; l <= l_top; ++l) {
       // the reference cell: G's ancestor at l < L; at l = L the lists of all
       // eight leaves together (children of G's neighbours)
       const int sh = (t.L - 1) - l;
@@ -526,29 +544,71 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       gy += (double)fy * (double)(inv_w * inv_w);
       gz += (double)fz * (double)(inv_w * inv_w);
     }
-    // direct pairs: the 4 x 4 x 4 leaves around G, each target its own 27
-    // (FP32 pairs, FP64 sums per leaf); the identity image of an ion is
-    // skipped and its other own images are summed in FP64 from the shift
-    // table (the same terms as the prep's own-image sums)
+    // direct pairs (FP32 pairs, FP64 sums per leaf): the 4 x 4 x 4 leaves
+    // around G, each target its own 27; or, with a direct leaf level, the
+    // 6 x 6 x 6 leaves around G, all of them for every target.  The identity
+    // image of an ion is skipped and its other own images are summed in FP64
+    // from the shift table (the same terms as the prep's own-image sums).
     const bool ion = active && ti < n_ions;
     const int own0 = ion ? own.ioff[ti] : 0, own_n = ion ? own.icnt[ti] : 0;
-    for (int j = part; j < 64; j += S) {
-      const int ox = 2 * gx0 - 1 + (j & 3), oy = 2 * gy0 - 1 + ((j >> 2) & 3), oz = 2 * gz0 - 1 + (j >> 4);
+    const int span = t.direct_leaf ? 6 : 4, lo_off = t.direct_leaf ? -2 : -1;
+    for (int jl = part; jl < span * span * span; jl += S) {
+      const int ox = 2 * gx0 + lo_off + jl % span, oy = 2 * gy0 + lo_off + (jl / span) % span;
+      const int oz = 2 * gz0 + lo_off + jl / (span * span);
       if (ox < 0 || oy < 0 || oz < 0 || ox >= nsideL || oy >= nsideL || oz >= nsideL) continue;
       const int code = morton(ox, oy, oz);
       const int s0 = leaf_start[code], s1 = leaf_start[code + 1];
       if (s1 <= s0) continue;
-      const bool take = active && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1;
+      const bool take =
+          active && (t.direct_leaf || (abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1));
       if (!__any_sync(0xffffffffu, take)) continue;
       float fp = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+      float2 fp2 = make_float2(0.f, 0.f), fx2 = fp2, fy2 = fp2, fz2 = fp2;
       for (int sb = s0; sb < s1; sb += 32) {
+        // the warp's tile as x, y, z, q arrays; slots past the leaf's end hold
+        // a far, uncharged source
         __syncwarp();
+        float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        int id = -1;
         if (sb + lane < s1) {
-          stile[lane] = srcs[sb + lane];
-          sid[lane] = src_order[sb + lane];
+          v = srcs[sb + lane];
+          id = src_order[sb + lane];
         }
+        tx[lane] = v.x;
+        ty[lane] = v.y;
+        tz[lane] = v.z;
+        tq[lane] = v.w;
+        sid[lane] = id;
         __syncwarp();
         const int nb = min(32, s1 - sb);
+        // a leaf's sources are in increasing index order, so the tile holds
+        // neither the target's identity image nor an own image of it when
+        // both lie outside [sid[0], sid[nb-1]]: then pairs go two at a time
+        const int lo = sid[0], hi = sid[nb - 1];
+        const bool clean =
+            !ion || ((ti < lo || ti > hi) && (own_n == 0 || own0 + own_n <= lo || own0 > hi));
+        if (__all_sync(0xffffffffu, clean)) {
+          if (take) {
+            const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y);
+            const float2 npz = make_float2(-p.z, -p.z);
+            for (int k = 0; k < nb; k += 2) {   // an odd tile ends on a padding slot
+              const float2 dx = __fadd2_rn(*reinterpret_cast<const float2*>(tx + k), npx);
+              const float2 dy = __fadd2_rn(*reinterpret_cast<const float2*>(ty + k), npy);
+              const float2 dz = __fadd2_rn(*reinterpret_cast<const float2*>(tz + k), npz);
+              float2 r2 = __fmul2_rn(dx, dx);
+              r2 = __ffma2_rn(dy, dy, r2);
+              r2 = __ffma2_rn(dz, dz, r2);
+              const float2 inv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+              const float2 qi = __fmul2_rn(*reinterpret_cast<const float2*>(tq + k), inv);
+              fp2 = __fadd2_rn(fp2, qi);
+              const float2 q3 = __fmul2_rn(qi, __fmul2_rn(inv, inv));
+              fx2 = __ffma2_rn(q3, dx, fx2);
+              fy2 = __ffma2_rn(q3, dy, fy2);
+              fz2 = __ffma2_rn(q3, dz, fz2);
+            }
+          }
+          continue;
+        }
         if (take)
           for (int k = 0; k < nb; ++k) {
             const int sidx = sid[k];
@@ -569,11 +629,10 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
               }
               continue;
             }
-            const float4 sv = stile[k];
-            const float dx = sv.x - p.x, dy = sv.y - p.y, dz = sv.z - p.z;
+            const float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
             const float ri = rsqrtf(r2);
-            const float qr = sv.w * ri;
+            const float qr = tq[k] * ri;
             const float qr3 = qr * ri * ri;
             fp += qr;
             fx += qr3 * dx;
@@ -581,10 +640,10 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
             fz += qr3 * dz;
           }
       }
-      phi += fp;
-      gx += fx;
-      gy += fy;
-      gz += fz;
+      phi += fp + (fp2.x + fp2.y);
+      gx += fx + (fx2.x + fx2.y);
+      gy += fy + (fy2.x + fy2.y);
+      gz += fz + (fz2.x + fz2.y);
     }
     if (active) {
       // as the pair kernels: phi and its gradient with respect to the target
@@ -636,8 +695,9 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   k_tree_sort_bins<<<grid, 256, 0, s>>>(T.src_start, nleaf, T.src_order);
   k_tree_sort_bins<<<grid, 256, 0, s>>>(T.tgt_start, nleaf, T.tgt_order);
   k_tree_gather<<<grid, 256, 0, s>>>(T.src, T.src_order, 0, T.sc, T.src_sorted);
-  // multipoles, level by level: items are cells of level il = max(l, L - 1)
-  for (int l = 2; l <= t.L; ++l) {
+  // multipoles, level by level (not the leaf level when it is summed
+  // directly): items are cells of level il = max(l, L - 1)
+  for (int l = 2; l <= (t.direct_leaf ? t.L - 1 : t.L); ++l) {
     const int il = l >= t.L - 1 ? l : t.L - 1;
     const int items = 1 << (3 * il);
 #define HSMA_TREE_P2M(PP) k_tree_p2m<PP><<<items, kP2mThreads, 0, s>>>(t, l, il, T.src_sorted, T.src_start, T.part)

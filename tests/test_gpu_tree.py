@@ -136,3 +136,27 @@ def test_tree_parts_agree_and_each_is_repeatable(P):
         with pytest.raises(P.HSMAError):
             h.set_option("tree_parts", bad)
     h.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tree_leaf_modes(P, mode):
+    # the finest level summed directly (mode 1) or through leaf multipoles
+    # (mode 2): both against the oracle, in 3D and next to dielectric walls
+    c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 6, 800), x, q)
+    E, F, pot, L = run(P, c, x, q, tree_order=10, tree_leaf_mode=mode)
+    assert frms(F, ref["forces"]) <= 2e-5 and abs(E - ref["energy"]) <= 1e-5 * abs(ref["energy"])
+    c = workloads.small_case(2000, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=(0.95, 0.95), G=24,
+                             seed=12)
+    x, q = workloads.electrolyte(c, margin=1e-3)
+    st = O.make_setup(c.box, 2, 6, 600, 0.95, 0.95, dtn_grid=24)
+    ref = O.evaluate(st, x, q)
+    E, F, pot, L = run(P, c, x, q, tree_order=10, tree_leaf_mode=mode)
+    scale = 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
+    assert abs(E - ref["energy"]) <= 1e-5 * scale
+    assert frms(F, ref["forces"]) <= 2e-5
+    h = P.HSMA(c.box, 3, 6, 800, near_tree=1)
+    with pytest.raises(P.HSMAError):
+        h.set_option("tree_leaf_mode", 3)
+    h.close()
