@@ -296,8 +296,20 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   t.P = P;
   // the finest level summed directly when its leaves are sparse: about 48
   // images per occupied leaf or fewer (measured at 35 and 92 images a leaf:
-  // direct 3.9 ms against 4.4 ms; leaf multipoles 10.4 ms against 12.0 ms)
-  const double occupied = h->ns_est / ((g.par.sphere_mask ? 0.52 : 1.0) * (double)((size_t)1 << (3 * L)));
+  // direct 3.9 ms against 4.4 ms; leaf multipoles 10.4 ms against 12.0 ms).
+  // The images fill the sphere B, in 2D only within the z-extent of the image
+  // layers (a slab of half-thickness hz through it), or, unmasked, the cube.
+  double frac = 1.0;
+  if (g.par.sphere_mask) {
+    double hz = half;
+    if (g.par.dims == 2) {
+      double zmax = 0.0;
+      for (const Shift& sh : g.shifts) zmax = std::max(zmax, std::fabs(sh.zo) + 0.5 * g.par.box[2]);
+      hz = std::min(half, zmax);
+    }
+    frac = 3.14159265358979323846 * (2.0 * hz * half * half - 2.0 * hz * hz * hz / 3.0) / (8.0 * half * half * half);
+  }
+  const double occupied = h->ns_est / (frac * (double)((size_t)1 << (3 * L)));
   t.direct_leaf = h->tree_leaf_mode == 1 ? 1 : h->tree_leaf_mode == 2 ? 0 : (occupied <= 48.0 ? 1 : 0);
   t.Rs = (float)half;
   t.D = (float)(2.0 * half);
