@@ -186,10 +186,14 @@ constexpr int kSelfTable = 256;
 // per shift: only about a fifth of the shifts put an image in B, and GB300's
 // FP64 pipe charges a warp instruction a full pass whatever its active lanes.
 // Thread t also writes check point t.
-__global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
+// One warp per block: the FP64 pipe is the limit, so small N still spreads
+// over many SMs.
+constexpr int kEmitThreads = 32;
+
+__global__ void __launch_bounds__(kEmitThreads) k_prep_emit(PrepArgs a) {
   __shared__ double sh_self[4][kSelfTable];
   if (a.self)
-    for (int t = threadIdx.x + 1; t < min(a.n_shift, kSelfTable); t += kPrepThreads) {
+    for (int t = threadIdx.x + 1; t < min(a.n_shift, kSelfTable); t += kEmitThreads) {
       const double* sh = a.shifts + 5 * t;
       if (sh[2] == 1.0) {
         const double dx = sh[0], dy = sh[1], dz = sh[3];
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_emit(PrepArgs a) {
       }
     }
   __syncthreads();
-  const int j = blockIdx.x * kPrepThreads + threadIdx.x;
+  const int j = blockIdx.x * kEmitThreads + threadIdx.x;
   if (j < a.N) {
     // blk holds the exclusive image offset of each group of kIonsPerBlock ions
     int o = a.N + a.blk[j / kIonsPerBlock];
@@ -287,7 +291,7 @@ cudaError_t launch_prep(const PrepArgs& a, int nblk, cudaStream_t s) {
   k_prep_count<<<nb, kPrepThreads, 0, s>>>(a);
   k_prep_scan<<<1, kScanThreads, 0, s>>>(a, nb);
   const int ne = a.N > a.n_check ? a.N : a.n_check;
-  k_prep_emit<<<(ne + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, s>>>(a);
+  k_prep_emit<<<(ne + kEmitThreads - 1) / kEmitThreads, kEmitThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
