@@ -350,6 +350,7 @@ def other_cases(P, torch, dev, stream):
             torch.cuda.synchronize()
             rec["tree_fp32_evals_per_s"] = 1e3 * max(3, n32) / a.elapsed_time(b)
             rec["tree_levels"] = int(P.hsma_get_info(h.h, "tree_levels"))
+            rec["tree_direct_leaf"] = int(P.hsma_get_info(h.h, "tree_direct_leaf"))
             rec["tree_vs_dense_rel_energy"] = abs(float(e[0]) - energies[1]) / abs(energies[1])
             # fd holds the forces of the last dense run (FP64 where it ran, else FP32)
             ref = "fp64" if 0 in energies else "fp32"

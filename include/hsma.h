@@ -99,7 +99,7 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       formed exactly: coordinates carried as FP32 hi + lo
  *                       pairs, (hi_s - hi_t) + (lo_s - lo_t), so close pairs
  *                       keep FP32 relative accuracy however large the box
- *                       (about 1.2 x the cost of 1).
+ *                       (about 1.4 x the cost of 1).
  *   "dtn_grid"          G, grid points per side on each 2D face (>= 4).
  *   "coulomb_prefactor" multiplies energy, forces and potential.
  *   "timing"            1 = record per-phase CUDA-event times (hsma_get_info).
@@ -108,7 +108,8 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "autotune"          1 (default) = on the first evaluation of each N, time
  *                       the near/check launch for a few kernel variants and
  *                       chunk counts and keep the fastest (cached per process
- *                       by N and check-point count); 0 = fixed heuristic.
+ *                       by N, check-point count and expected image count);
+ *                       0 = fixed heuristic.
  *   "targets_per_thread" kernel variant: 1, 2, 4 (scalar FP32), 12, 14
  *                       (packed FP32x2, 2 or 4 targets), 24 (packed, sums in
  *                       shared memory) or 32, 34 (exact differences, 2 or 4
@@ -142,10 +143,11 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       FMM library): images binned into a uniform octree over
  *                       [-R_s, R_s]^3, multipole expansions of order
  *                       tree_order per cell, FMM interaction lists evaluated
- *                       at each target, direct FP32 pairs with the 27
- *                       neighbouring leaves.  An approximation of the sums:
- *                       at tree_order 10, force RMS about 2e-6 and energy
- *                       4e-6 relative to the direct sums.  Needs precision 1
+ *                       at each target, direct FP32 pairs with its
+ *                       neighbourhood (see tree_leaf_mode).  An
+ *                       approximation of the sums: at tree_order 10, force
+ *                       RMS about 1e-6 and energy 3e-6 to 5e-6 relative to
+ *                       the direct sums.  Needs precision 1
  *                       (an evaluation at precision 0 or 2 returns
  *                       HSMA_ERR_ARG); 0 (default) = direct sums.
  *   "tree_order"        expansion order of the tree: 4, 6, 8, 10 (default),
@@ -215,7 +217,8 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * last evaluation), "t_total_ms", "t_prep_ms", "t_near_ms", "t_fit_ms",
  * "t_far_ms", "t_assemble_ms" (with option timing = 1), "chunks",
  * "far_chunks", "far_field", "tree_levels" (leaf level L of the tree, 0 when
- * off), "kernels_per_eval" (kernel launches of one evaluation), "grid",
+ * off), "tree_direct_leaf" (1 when the tree sums its leaf level directly),
+ * "kernels_per_eval" (kernel launches of one evaluation), "grid",
  * "slots", "kernel", "tile_targets", "guard_violations" (process-wide: how
  * many device buffers of this library, live or already freed, have had the
  * 256-byte guard band behind their end overwritten; every buffer is

@@ -982,6 +982,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "far_chunks") *value = h->far_series ? 1 : h->chunks2;
   else if (k == "far_field") *value = h->far_series;
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
+  else if (k == "tree_direct_leaf") *value = h->near_tree ? h->tree_args.direct_leaf : 0;
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
   else if (k == "guard_violations") *value = (double)guard_violations();
   else if (k == "grid") *value = h->grid1;

@@ -147,6 +147,10 @@ def test_tree_leaf_modes(P, mode):
     ref = O.evaluate(O.make_setup(c.box, 3, 6, 800), x, q)
     E, F, pot, L = run(P, c, x, q, tree_order=10, tree_leaf_mode=mode)
     assert frms(F, ref["forces"]) <= 2e-5 and abs(E - ref["energy"]) <= 1e-5 * abs(ref["energy"])
+    h = P.HSMA(c.box, 3, 6, 800, precision=1, near_tree=1, tree_leaf_mode=mode)
+    h.eval(x, q)
+    assert int(h.info("tree_direct_leaf")) == (1 if mode == 1 else 0)
+    h.close()
     c = workloads.small_case(2000, dims=2, box=(20.0, 20.0, 10.0), p=6, M=600, gammas=(0.95, 0.95), G=24,
                              seed=12)
     x, q = workloads.electrolyte(c, margin=1e-3)
