@@ -405,7 +405,8 @@ __device__ __forceinline__ void morton_decode(int code, int bits, int* x, int* y
 // Work items of the evaluation: a task is up to 32 consecutive targets of one
 // cell G of level L-1 (task_start[G] .. task_start[G+1]); each task is split
 // into S parts, part s taking every S-th batch of each level's interaction
-// list and every S-th of the 64 direct-pair leaves.  An item (task, part) is
+// list and every S-th of the candidate leaves for direct pairs (4x4x4 around
+// G's children, or the 6x6x6 of the direct leaf level).  An item (task, part) is
 // computed the same way whichever warp takes it, and writes its own partial
 // out[(s*4 + c)*ld + t]; the parts are summed afterwards in fixed order.
 __global__ void k_tree_tasks(const int* __restrict__ tgt_start, int n_cells, int* __restrict__ count) {
