@@ -58,7 +58,8 @@ extern "C" {
 #define HSMA_ERR_BUDGET     (-5)  /* serving: request larger than the HBM budget */
 #define HSMA_ERR_TIMEOUT    (-6)  /* a bounded device wait ran out */
 #define HSMA_ERR_CUDA       (-7)  /* any other CUDA runtime error */
-#define HSMA_ERR_NUMERIC    (-8)  /* the fit lost rank (degenerate geometry) */
+#define HSMA_ERR_NUMERIC    (-8)  /* the fit lost rank (degenerate geometry), or
+                                     the energy is not finite */
 
 typedef struct hsma_ctx* hsma_t;
 
@@ -197,7 +198,10 @@ int hsma_set_stream(hsma_t h, void* stream);
  * removed as q_i -= sum q / N).  3D positions are wrapped into the box; in 2D
  * x and y are wrapped and z must be inside (0, Lz).
  * energy: 1 double (required).  forces: N*3 or NULL.
- * Blocks until the results are written.
+ * Blocks until the results are written.  Inputs are not scanned: a
+ * non-finite position or charge makes the energy non-finite, and the call
+ * then returns HSMA_ERR_NUMERIC without writing *energy (the forces are
+ * written, non-finite for the ions it reaches); the handle stays usable.
  * Errors: HSMA_ERR_ARG, HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_OUT_OF_SLAB,
  * HSMA_ERR_NOMEM, HSMA_ERR_NUMERIC, HSMA_ERR_TIMEOUT, HSMA_ERR_CUDA.
  */

@@ -646,6 +646,8 @@ int finish_eval(hsma_ctx* h, double* energy) {
   if (r.flags & FLAG_OUT_OF_SLAB) return fail(h, HSMA_ERR_OUT_OF_SLAB, "some z outside (0, Lz)");
   if (r.flags & FLAG_NOT_NEUTRAL) return fail(h, HSMA_ERR_NOT_NEUTRAL, "system not neutral");
   if (r.flags & FLAG_TIMEOUT) return fail(h, HSMA_ERR_TIMEOUT, "device wait timed out");
+  if (!std::isfinite(r.energy))
+    return fail(h, HSMA_ERR_NUMERIC, "energy is not finite (a position or charge is not finite)");
   if (energy) *energy = r.energy;
   return HSMA_OK;
 }

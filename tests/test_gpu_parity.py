@@ -259,6 +259,28 @@ def test_degenerate_inputs(P, prec):
     assert rel(E, ref["energy"]) <= E_TOL[prec] and frms(F, ref["forces"]) <= F_TOL[prec]
 
 
+@pytest.mark.parametrize("prec,tree", [(0, 0), (1, 0), (2, 0), (1, 1)])
+def test_non_finite_inputs(P, prec, tree):
+    # a non-finite position or charge makes the energy non-finite: the call
+    # reports HSMA_ERR_NUMERIC and the handle stays usable
+    c = workloads.small_case(2000, dims=3, box=(13.0, 13.0, 13.0), p=6, M=800, seed=19)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, 6, 800, precision=prec, near_tree=tree)
+    for which, i, v in (("x", 5, np.nan), ("x", 1999, np.inf), ("q", 7, np.nan), ("q", 0, -np.inf)):
+        xb, qb = x.copy(), q.copy()
+        if which == "x":
+            xb[i, 1] = v
+        else:
+            qb[i] = v
+        with pytest.raises(P.HSMAError) as e:
+            h.eval(xb, qb)
+        assert e.value.code == -8, (which, i, v)
+    ref = O.evaluate(O.make_setup(c.box, 3, 6, 800), x, q)
+    E, F, _ = h.eval(x, q)
+    h.close()
+    assert rel(E, ref["energy"]) <= E_TOL[prec] and frms(F, ref["forces"]) <= F_TOL[prec]
+
+
 def test_repeatable_bitwise(P):
     c = workloads.case(1)
     x, q = workloads.electrolyte(c)
