@@ -200,8 +200,8 @@ int hsma_set_stream(hsma_t h, void* stream);
  * energy: 1 double (required).  forces: N*3 or NULL.
  * Blocks until the results are written.  Inputs are not scanned: a
  * non-finite position or charge makes the energy non-finite, and the call
- * then returns HSMA_ERR_NUMERIC without writing *energy (the forces are
- * written, non-finite for the ions it reaches); the handle stays usable.
+ * then returns HSMA_ERR_NUMERIC (hsma_poll does the same for a served
+ * request); the handle stays usable.
  * Errors: HSMA_ERR_ARG, HSMA_ERR_NOT_NEUTRAL, HSMA_ERR_OUT_OF_SLAB,
  * HSMA_ERR_NOMEM, HSMA_ERR_NUMERIC, HSMA_ERR_TIMEOUT, HSMA_ERR_CUDA.
  */
@@ -334,7 +334,8 @@ int hsma_submit(hsma_t server, const double* x, const double* q, int64_t N,
 /*
  * hsma_poll -- HSMA_PENDING while the request runs; HSMA_OK once energy (1
  * double) and forces (N*3, or NULL) are written, after which the ticket is
- * retired.  A negative code reports that request's failure.
+ * retired.  A negative code reports that request's failure (and retires the
+ * ticket); hsma_last_error(server) then gives that request's own message.
  */
 int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces);
 

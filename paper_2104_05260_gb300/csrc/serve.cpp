@@ -48,6 +48,7 @@ struct Request {
   double* hf = nullptr;
   double energy = 0;
   int status = HSMA_PENDING;
+  std::string err;         // why the request failed (status < 0)
   size_t bytes = 0;
   int slot = -1;
 };
@@ -89,7 +90,6 @@ struct Server {
   std::map<uint64_t, Request*> all;
   std::map<std::tuple<double, double, int, int>, std::unique_ptr<UnitGeo>> geos;
   BatchBuf bufs[kBatchBufs];
-  std::string err;
   // host-side fault injection (tests): the request with this ticket fails as
   // if a CUDA call had failed while it was being bound to a slot
   uint64_t inject_fail_ticket = 0;
@@ -223,8 +223,13 @@ static void retire(Server* s) {
     if (q == cudaErrorNotReady) continue;
     for (Request* r : bb.reqs) {
       Slot& sl = s->slots[r->slot];
-      if (q != cudaSuccess) r->status = HSMA_ERR_CUDA;
-      else r->status = finish_eval(sl.ctx, &r->energy);
+      if (q != cudaSuccess) {
+        r->status = HSMA_ERR_CUDA;
+        r->err = cudaGetErrorString(q);
+      } else {
+        r->status = finish_eval(sl.ctx, &r->energy);
+        if (r->status != HSMA_OK) r->err = sl.ctx->err;
+      }
       s->in_use -= (double)r->bytes;
       sl.req = nullptr;
     }
@@ -314,7 +319,7 @@ static int step(Server* s) {
       }
       if (rc != HSMA_OK) {
         r->status = rc;
-        s->err = err;
+        r->err = err;
         continue;
       }
       sl.req = r;
@@ -330,6 +335,7 @@ static int step(Server* s) {
         cudaGetLastError();
         for (Request* r : bb->reqs) {
           r->status = rc;
+          r->err = "the batch launch failed";
           s->in_use -= (double)r->bytes;
           s->slots[r->slot].req = nullptr;
         }
@@ -517,7 +523,7 @@ int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces) {
       }
     }
   } else {
-    server->err = s->err;
+    server->err = r->err;
   }
   s->all.erase(it);
   free_request(r);

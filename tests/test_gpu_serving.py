@@ -114,14 +114,19 @@ def test_submit_rejects_bad_requests(P):
 
 
 def test_failed_request_does_not_disturb_the_others(P):
-    # host-side fault injection: one request fails when it is admitted; the
-    # loop reports that request's error and completes every other request
-    reqs = [request(N, 6, s) for N, s in ((1000, 41), (1200, 42), (900, 43), (1500, 44))]
+    # host-side fault injection: one request fails when it is admitted, and
+    # one carries a NaN charge (its energy is not finite); the loop reports
+    # each failed request's own error and completes every other request
+    reqs = [request(N, 6, s) for N, s in ((1000, 41), (1200, 42), (900, 43), (1500, 44), (1100, 45))]
+    c4, x4, q4 = reqs[4]
+    q4 = q4.copy()
+    q4[3] = np.nan
+    reqs[4] = (c4, x4, q4)
     server = P.hsma_server_create(4, 4e9, 1)
     P.hsma_set_option(server, "inject_fail_ticket", 2)    # the second submission
     tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
     assert tickets[1] == 2
-    results = {}
+    results, msgs = {}, {}
     for _ in range(100000):
         for i, t in enumerate(tickets):
             if i in results:
@@ -130,13 +135,15 @@ def test_failed_request_does_not_disturb_the_others(P):
                 r = P.hsma_poll(server, t, reqs[i][0].N)
             except P.HSMAError as e:
                 results[i] = e.code
+                msgs[i] = str(e)
                 continue
             if r is not None:
                 results[i] = r
         if len(results) == len(tickets):
             break
     P.hsma_destroy(server)
-    assert results[1] == -7
+    assert results[1] == -7 and "injected failure" in msgs[1], msgs
+    assert results[4] == -8 and "not finite" in msgs[4], msgs
     for i in (0, 2, 3):
         c, x, q = reqs[i]
         h = P.HSMA(c.box, 3, c.p, c.M)
