@@ -21,7 +21,6 @@ import os
 import platform
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np

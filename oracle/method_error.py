@@ -24,7 +24,7 @@ if ROOT not in sys.path:
 
 import workloads  # noqa: E402
 from oracle import hsma as O  # noqa: E402
-from oracle.ewald import ewald3d, ewald2d_field, slab_ewald, image_factor, image_z, slab_lmax  # noqa: E402
+from oracle.ewald import ewald3d, ewald2d_field, image_factor, image_z, slab_lmax  # noqa: E402
 
 
 def rel_rms(F, Fe):
