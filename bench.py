@@ -404,17 +404,19 @@ def pair_sources_sha1():
     return hashlib.sha1(src).hexdigest()
 
 
-def traffic_records():
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def traffic_records(tr=TRAFFIC_JSON):
     """The DRAM-traffic records of profiles/traffic.json, one per captured
     (kernel, source chunks) launch plan."""
-    tr = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tr):
         return []
     d = json.load(open(tr))
     return d.get("records", [d] if "bytes_per_launch" in d else [])
 
 
-def record_traffic(csv_path, kernel, workload, chunks, command):
+def record_traffic(csv_path, kernel, workload, chunks, command, tr=TRAFFIC_JSON):
     """Add to profiles/traffic.json the DRAM bytes of the near-field launch in
     an ncu CSV (--csv --log-file) holding gpu__time_duration.sum,
     dram__bytes_read.sum and dram__bytes_write.sum: of the captured launches
@@ -436,13 +438,14 @@ def record_traffic(csv_path, kernel, workload, chunks, command):
     rec = {"kernel": kernel, "workload": workload, "pair_sources_sha1": pair_sources_sha1(), "chunks": chunks,
            "bytes_per_launch": int(rd + wr), "read_bytes": int(rd), "write_bytes": int(wr),
            "command": command}
-    recs = [r for r in traffic_records() if not (r.get("kernel") == kernel and r.get("chunks") == chunks)]
+    recs = [r for r in traffic_records(tr) if not (r.get("kernel") == kernel and r.get("chunks") == chunks)]
     recs.append(rec)
     recs.sort(key=lambda r: (r.get("kernel", ""), r.get("chunks", 0)))
     out = {"hash_covers": "paper_2104_05260_gb300/csrc/pair.cu and the PairArgs and DevScalars structs of "
                           "internal.hpp; a record whose pair_sources_sha1 differs is not used by bench.py",
            "records": recs}
-    json.dump(out, open(os.path.join(ROOT, "profiles", "traffic.json"), "w"), indent=1)
+    with open(tr, "w") as f:
+        json.dump(out, f, indent=1)
     return rec
 
 

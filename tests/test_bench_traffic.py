@@ -1,0 +1,72 @@
+"""Host logic of bench.py's DRAM-traffic records: parsing an ncu CSV of
+several launches, picking the near-field launch, and keeping one record per
+(kernel, chunk count).  No GPU: the CSV is written here in ncu's layout."""
+import csv
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+HDR = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+       "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+
+
+def write_csv(path, launches):
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(HDR)
+        for i, metrics in enumerate(launches):
+            for name, unit, v in metrics:
+                w.writerow([str(i), "1", "python", "h", "void k_pair_f32x2s<2>(PairArgs)", "1", "7", "(256, 1, 1)",
+                            "(456, 1, 1)", "0", "10.3", "Command line profiler metrics", name, unit, v])
+
+
+def launch(ns, rd, wr, unit="byte", tunit="ns"):
+    return [("dram__bytes_read.sum", unit, rd), ("dram__bytes_write.sum", unit, wr),
+            ("gpu__time_duration.sum", tunit, ns)]
+
+
+def test_longest_launch_is_recorded_and_records_merge(tmp_path):
+    tr = str(tmp_path / "traffic.json")
+    c1 = str(tmp_path / "a.csv")
+    # far field first (short), then the near field (long); thousands separators as ncu prints them
+    write_csv(c1, [launch("106,656", "1,680,640", "45,056"), launch("25,096,992", "23,778,048", "246,297,344")])
+    rec = bench.record_traffic(c1, "k_pair_f32x2s<2> near field", "w", 92, "cmd", tr=tr)
+    assert rec["bytes_per_launch"] == 23778048 + 246297344 and rec["chunks"] == 92
+    assert rec["pair_sources_sha1"] == bench.pair_sources_sha1()
+    # another chunk count is added beside it; MB units and msecond are scaled
+    c2 = str(tmp_path / "b.csv")
+    write_csv(c2, [launch("26.1", "12.6", "24.3", unit="Mbyte", tunit="msecond"),
+                   launch("0.1", "1.0", "0.1", unit="Mbyte", tunit="msecond")])
+    bench.record_traffic(c2, "k_pair_f32x2s<2> near field", "w", 23, "cmd", tr=tr)
+    recs = bench.traffic_records(tr)
+    assert [r["chunks"] for r in recs] == [23, 92]
+    assert recs[0]["bytes_per_launch"] == int(12.6e6) + int(24.3e6)
+    # re-recording a chunk count replaces its record
+    bench.record_traffic(c1, "k_pair_f32x2s<2> near field", "w", 23, "cmd", tr=tr)
+    recs = bench.traffic_records(tr)
+    assert len(recs) == 2 and recs[0]["bytes_per_launch"] == 23778048 + 246297344
+
+
+def test_single_record_files_still_read(tmp_path):
+    tr = str(tmp_path / "traffic.json")
+    with open(tr, "w") as f:
+        json.dump({"kernel": "k", "chunks": 46, "bytes_per_launch": 1}, f)
+    assert bench.traffic_records(tr) == [{"kernel": "k", "chunks": 46, "bytes_per_launch": 1}]
+    assert bench.traffic_records(str(tmp_path / "missing.json")) == []
+
+
+def test_committed_records_are_well_formed():
+    # one record per (kernel, chunks), each with its bytes and the command
+    # that captured it; a record whose source hash no longer matches is
+    # simply not used by the bench
+    recs = bench.traffic_records()
+    keys = [(r["kernel"], r["chunks"]) for r in recs]
+    assert recs and len(set(keys)) == len(keys)
+    for r in recs:
+        assert r["bytes_per_launch"] == r["read_bytes"] + r["write_bytes"] > 0
+        assert r["command"].startswith("ncu ") and "--clock-control none" in r["command"]
