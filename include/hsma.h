@@ -49,7 +49,8 @@ extern "C" {
 
 #define HSMA_OK               0
 #define HSMA_PENDING          1
-#define HSMA_ERR_ARG        (-1)  /* bad argument: p < 1, M < (p+1)^2, |gamma| > 1,
+#define HSMA_ERR_ARG        (-1)  /* bad argument: p outside 1..40, M < (p+1)^2 or
+                                     M (p+1)^2 > 2^31, |gamma| > 1,
                                      N < 1, dims not 2 or 3, box <= 0, NULL pointer,
                                      unknown option or ticket */
 #define HSMA_ERR_NOT_NEUTRAL (-2) /* |sum q| > 1e-10 sum |q| */
@@ -70,8 +71,10 @@ typedef struct hsma_ctx* hsma_t;
  *        2D: periodic in x, y; charges must lie in 0 < z < Lz, with the
  *        dielectric interfaces at z = 0 (bottom) and z = Lz (top).
  * dims:  3 (HSMA3D) or 2 (HSMA2D).
- * p:     harmonic order P of Eq. 5, >= 1; (p+1)^2 basis functions.
- * M:     number of Fibonacci surface charges, >= (p+1)^2.
+ * p:     harmonic order P of Eq. 5, 1..40; (p+1)^2 basis functions.
+ * M:     number of Fibonacci surface charges, >= (p+1)^2 and at most
+ *        2^31 / (p+1)^2 (the surface map is an M x (p+1)^2 FP64 matrix
+ *        built on the host; the same bound holds for n_monitor).
  * gamma_top, gamma_bot: dielectric mismatches of the top and bottom media,
  *        gamma = (eps_c - eps_out)/(eps_c + eps_out) in [-1, 1] (Sec. 2.1,
  *        after Eq. 4).  Ignored when dims == 3.
@@ -263,8 +266,9 @@ int hsma_get_array(hsma_t h, const char* name, double* out, int64_t n);
  * lam <= 0, n_monitor <= 0 or G <= 0 select the defaults; grad_weight > 0
  * adds the gradient-periodicity rows with that weight (option grad_rows),
  * <= 0 leaves them out; surface_rule is the option of that name.  n is the
- * capacity of out in doubles.
- * Errors: HSMA_ERR_ARG, HSMA_ERR_NUMERIC.
+ * capacity of out in doubles; a too small n is HSMA_ERR_ARG (for "T" it is
+ * checked before the matrix is formed).
+ * Errors: HSMA_ERR_ARG, HSMA_ERR_NOMEM (host memory), HSMA_ERR_NUMERIC.
  */
 int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamma_top,
                         double gamma_bot, double lam, int n_monitor, int G,

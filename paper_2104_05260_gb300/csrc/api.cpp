@@ -805,7 +805,8 @@ int hsma_create(const double box[3], int dims, int p, int M, double gamma_top, d
   if (!out || !box) return HSMA_ERR_ARG;
   *out = nullptr;
   if (dims != 2 && dims != 3) return HSMA_ERR_ARG;
-  if (p < 1 || p > 40 || M < (p + 1) * (p + 1)) return HSMA_ERR_ARG;
+  if (p < 1 || p > 40 || M < (p + 1) * (p + 1) || !geometry_size_ok(p, M, 2 * (p + 1) * (p + 1)))
+    return HSMA_ERR_ARG;
   for (int d = 0; d < 3; ++d)
     if (!(box[d] > 0) || !std::isfinite(box[d])) return HSMA_ERR_ARG;
   if (dims == 2 && (!(std::fabs(gamma_top) <= 1) || !(std::fabs(gamma_bot) <= 1))) return HSMA_ERR_ARG;
@@ -1060,6 +1061,7 @@ extern "C" int hsma_geometry_array(const double box[3], int dims, int p, int M, 
   const std::string k(name);
   std::vector<double> v;
   if (k == "T") {
+    if ((int64_t)M * g.nv > n) return HSMA_ERR_ARG;
     v.assign((size_t)M * g.nv, 0.0);
     for (int m = 0; m < M; ++m)
       for (int r = 0; r < g.nA; ++r) {

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <complex>
 #include <memory>
+#include <new>
 
 #include "../../include/hsma.h"
 
@@ -402,12 +403,20 @@ void solid_basis_grad(int p, double x, double y, double z, double s, double* val
   }
 }
 
-int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
+bool geometry_size_ok(int p, int M, int n_monitor) {
+  const double nb = (double)(p + 1) * (p + 1), cap = 2147483648.0;
+  return p <= 40 && (double)M * nb <= cap && (double)n_monitor * nb <= cap;
+}
+
+static int build_geometry_impl(const GeoParams& gp, Geometry* g, std::string* err) {
   const int p = gp.p, M = gp.M;
   const int nb = (p + 1) * (p + 1), nA = nb - 1;
   if (gp.dims != 2 && gp.dims != 3) { *err = "dims must be 2 or 3"; return HSMA_ERR_ARG; }
   if (p < 1 || M < nb) { *err = "need p >= 1 and M >= (p+1)^2"; return HSMA_ERR_ARG; }
   if (gp.n_monitor < nb) { *err = "n_monitor must be >= (p+1)^2"; return HSMA_ERR_ARG; }
+  if (!geometry_size_ok(p, M, gp.n_monitor)) {
+    *err = "need p <= 40 and M, n_monitor each at most 2^31 / (p+1)^2"; return HSMA_ERR_ARG;
+  }
   if (!(gp.lam > 1.0)) { *err = "lambda must be > 1"; return HSMA_ERR_ARG; }
   for (int d = 0; d < 3; ++d)
     if (!(gp.box[d] > 0)) { *err = "box lengths must be > 0"; return HSMA_ERR_ARG; }
@@ -578,6 +587,15 @@ int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
       g->W[(size_t)m * nA + k - 1] = gp.surface_rule == 0 ? fac[k] * ys[k] : (fac[k] * ys[k]) * wm;
   }
   return HSMA_OK;
+}
+
+int build_geometry(const GeoParams& gp, Geometry* g, std::string* err) {
+  try {
+    return build_geometry_impl(gp, g, err);
+  } catch (const std::bad_alloc&) {
+    *err = "host memory ran out while building the fit operators";
+    return HSMA_ERR_NOMEM;
+  }
 }
 
 }  // namespace hsma

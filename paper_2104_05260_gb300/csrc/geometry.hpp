@@ -59,7 +59,14 @@ void sphere_radius(const double box[3], double lam, double* Rc, double* Rs, doub
 // Build the shift table only (identity first).
 void build_shifts(const GeoParams& gp, double Rs, std::vector<Shift>* out);
 
-// Full set-up.  Returns 0, or a negative HSMA_ERR_* with *err set.
+// Size limits of the host-built fit operators: p <= 40, and M and
+// n_monitor each times (p+1)^2 at most 2^31 entries (16 GiB of FP64).
+bool geometry_size_ok(int p, int M, int n_monitor);
+
+// Full set-up.  Returns 0, or a negative HSMA_ERR_* with *err set:
+// HSMA_ERR_ARG for parameters out of range (including the size limits),
+// HSMA_ERR_NOMEM when host memory runs out, HSMA_ERR_NUMERIC when the fit
+// matrix loses rank.
 int build_geometry(const GeoParams& gp, Geometry* g, std::string* err);
 
 // Real orthonormal solid harmonics (r/s)^n Y_nm at (x, y, z)/s, n <= p,

@@ -447,8 +447,8 @@ int hsma_submit(hsma_t server, const double* x, const double* q, int64_t N, cons
     h->err = "bad submit arguments";
     return HSMA_ERR_ARG;
   }
-  if (p < 1 || p > 40 || M < (p + 1) * (p + 1)) {
-    h->err = "need p >= 1 and M >= (p+1)^2";
+  if (p < 1 || p > 40 || M < (p + 1) * (p + 1) || !geometry_size_ok(p, M, 2 * (p + 1) * (p + 1))) {
+    h->err = "need 1 <= p <= 40 and (p+1)^2 <= M <= 2^31 / (p+1)^2";
     return HSMA_ERR_ARG;
   }
   for (int d = 0; d < 3; ++d)

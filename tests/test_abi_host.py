@@ -138,3 +138,17 @@ def test_geometry_rejects_bad_arguments(P):
         P.hsma_geometry_array((10, 10, 10), 3, 6, 800, "sizes", 8, lam=0.9)
     with pytest.raises(P.HSMAError):
         P.hsma_geometry_array((20, 20, 10), 2, 6, 800, "sizes", 8, gamma_top=1.2)
+    # size limits: p <= 40 and M (p+1)^2 <= 2^31, refused before any
+    # allocation (here and in hsma_create, which checks before any CUDA call)
+    m_max = 2 ** 31 // 41 ** 2
+    for p, M in ((41, 2000), (40, m_max + 1), (6, 2 ** 31 - 1)):
+        with pytest.raises(P.HSMAError) as e:
+            P.hsma_geometry_array((10, 10, 10), 3, p, M, "sizes", 8)
+        assert e.value.code == -1, (p, M)
+        with pytest.raises(P.HSMAError) as e:
+            P.hsma_create((10, 10, 10), 3, p, M)
+        assert e.value.code == -1, (p, M)
+    # an output too small for the composite operator is refused before it is formed
+    with pytest.raises(P.HSMAError) as e:
+        P.hsma_geometry_array((10, 10, 10), 3, 6, 800, "T", 10)
+    assert e.value.code == -1
