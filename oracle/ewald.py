@@ -249,6 +249,34 @@ def slab_lmax(g_up, g_low, Lx, Ly, Lz, eps=1e-16):
             return l
 
 
+def slab_field(tgt, pos, q, Lx, Ly, Lz, g_up, g_low, rcut=None, tol=1e-16, lmax=None, exclude=None,
+               chunk=32):
+    """Potential and gradient of the dielectric slab (Sec. 2.1, Eq. 4) at the
+    points ``tgt``: the direct 2D-periodic sum of the charges (pos, q) plus
+    every image layer l = 1..lmax of both sets.  pos are box-centred with
+    |z| < Lz/2; ``exclude`` as in ewald2d_field (direct layer only).
+    Returns (phi, grad, lmax)."""
+    tgt = np.asarray(tgt, dtype=np.float64)
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    if rcut is None:
+        rcut = 0.5 * min(Lx, Ly) + 0.5 * Lz
+    if lmax is None:
+        lmax = slab_lmax(g_up, g_low, Lx, Ly, Lz)
+    phi, grad = ewald2d_field(tgt, pos, q, Lx, Ly, rcut, tol, exclude=exclude, chunk=chunk)
+    for l in range(1, lmax + 1):
+        for sign in (+1, -1):
+            f = image_factor(l, sign, g_up, g_low)
+            if f == 0.0:
+                continue
+            img = pos.copy()
+            img[:, 2] = image_z(pos[:, 2], l, sign, Lz)
+            p, gr = ewald2d_field(tgt, img, f * q, Lx, Ly, rcut, tol, chunk=chunk)
+            phi += p
+            grad += gr
+    return phi, grad, lmax
+
+
 def slab_ewald(pos, q, Lx, Ly, Lz, g_up, g_low, rcut=None, tol=1e-16, lmax=None):
     """Energy, potential and gradient of the dielectric slab (Sec. 2.1, Eq. 4).
 
@@ -258,21 +286,7 @@ def slab_ewald(pos, q, Lx, Ly, Lz, g_up, g_low, rcut=None, tol=1e-16, lmax=None)
     """
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
-    n = len(q)
-    if rcut is None:
-        rcut = 0.5 * min(Lx, Ly) + 0.5 * Lz
-    if lmax is None:
-        lmax = slab_lmax(g_up, g_low, Lx, Ly, Lz)
-    phi, grad = ewald2d_field(pos, pos, q, Lx, Ly, rcut, tol, exclude=np.arange(n))
-    for l in range(1, lmax + 1):
-        for sign in (+1, -1):
-            f = image_factor(l, sign, g_up, g_low)
-            if f == 0.0:
-                continue
-            img = pos.copy()
-            img[:, 2] = image_z(pos[:, 2], l, sign, Lz)
-            p, gr = ewald2d_field(pos, img, f * q, Lx, Ly, rcut, tol)
-            phi += p
-            grad += gr
+    phi, grad, lmax = slab_field(pos, pos, q, Lx, Ly, Lz, g_up, g_low, rcut=rcut, tol=tol, lmax=lmax,
+                                 exclude=np.arange(len(q)))
     energy = 0.5 * float(np.dot(q, phi))
     return energy, phi, grad, lmax

@@ -40,9 +40,12 @@ notes of the repository):
     with dn the outward normal derivative, g that face's gamma and Lambda_G the
     periodic discrete DtN map (2D DFT, multiply by |h|, inverse DFT).  These
     rows are weighted by R_c / G (a grid-size-independent surface average in
-    potential units).  Parity unpinned for these DtN rows: the paper's own
-    discretisation (the 2D-dilation formula) is not available, so only the
-    end result of HSMA2D is pinned, against the Ewald2D image series.
+    potential units).  The face rows are pinned to the exact slab field: on
+    the image-series Ewald potential of a neutral slab they vanish up to the
+    grid's aliasing (residual below 1e-8 of the terms, falling with G), and
+    swapped (1 +- g), a flipped normal or |h|^2 for |h| break that pin.  The
+    paper's own discretisation of the DtN integral (the 2D-dilation formula)
+    is not available; this periodic-grid reading stands in for it.
  R6 Surface charges: the single layer sigma = sum A_nm (2n+1) R_s^(n-1)/(4 pi) Y_nm
     reproduces sum A_nm r^n Y_nm inside B (Laplace expansion of 1/|r - y|), so
     Q_m = sum A_nm (2n+1) R_s^(n+1) / M Y_nm(y_m / R_s).
@@ -167,6 +170,7 @@ class Setup:
     sphere_mask: bool = True                   # R2 (False: R12)
     surface_rule: int = 0                      # R3 (1: R18)
     wsurf: np.ndarray = field(default=None)    # (M,) R18 weights on the unit sphere
+    D: np.ndarray = field(default=None)        # the fit's design matrix (rows as in P's comment)
 
 
 def shift_table(dims, box, Rs, gamma_top=0.0, gamma_bot=0.0):
@@ -209,6 +213,33 @@ def dtn_lambda(field2d, Lx, Ly):
     hy = 2.0 * math.pi * ky / Ly
     habs = np.sqrt(hx[:, None] ** 2 + hy[None, :] ** 2)
     return np.real(np.fft.ifft2(np.fft.fft2(field2d) * habs))
+
+
+# Sign of the outward normal of the two faces, in face_grid order (top, bottom):
+# dPhi/dn = FACE_SIGNS[f] * dPhi/dz.
+FACE_SIGNS = (1.0, -1.0)
+
+
+def dtn_weights(g, sn):
+    """Coefficients (c_z, c_L) of a face row of R5, c_z dPhi/dz + c_L Lambda_G Phi:
+    (1 + g) dPhi/dn + (1 - g) Lambda_G Phi with dPhi/dn = sn dPhi/dz.  The
+    form follows from continuity of Phi and of eps dPhi/dz across the face,
+    dPhi_out/dn = -Lambda Phi outside (no charges there, decay away from the
+    slab) and eps_c : eps_out = (1 + g) : (1 - g) (Sec. 2.1, Eq. 4's g)."""
+    return (1.0 + g) * sn, (1.0 - g)
+
+
+def dtn_rows(phi, dphidz, g, sn, Lx, Ly):
+    """The face condition of R5 applied to a field sampled on one face's
+    G x G grid (face_grid order): (1 + g) dPhi/dn + (1 - g) Lambda_G Phi.
+    phi and dphidz are (G*G,) or (G*G, k) arrays; each column is one field."""
+    cz, cl = dtn_weights(g, sn)
+    phi = np.asarray(phi, dtype=np.float64)
+    G = int(round(math.sqrt(phi.shape[0])))
+    cols = phi.reshape(G * G, -1)
+    lam = np.stack([dtn_lambda(cols[:, c].reshape(G, G), Lx, Ly).ravel()
+                    for c in range(cols.shape[1])], axis=1)
+    return (cz * np.asarray(dphidz, dtype=np.float64).reshape(G * G, -1) + cl * lam).reshape(phi.shape)
 
 
 def face_grid(box, G):
@@ -282,12 +313,10 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
         st.check_pts = np.vstack([mon, wrap, top, bot])
         wd = st.Rc / G
         blocks = [Dper]
-        for pts, g, sn in ((top, gamma_top, 1.0), (bot, gamma_bot, -1.0)):
+        for pts, g, sn in ((top, gamma_top, FACE_SIGNS[0]), (bot, gamma_bot, FACE_SIGNS[1])):
             B = H.solid(p, pts, st.Rc)[:, 1:]
             dB = H.solid_dz(p, pts, st.Rc)[:, 1:]
-            LB = np.stack([dtn_lambda(B[:, c].reshape(G, G), Lx, Ly).ravel()
-                           for c in range(nb - 1)], axis=1)
-            blocks.append(wd * ((1.0 + g) * sn * dB + (1.0 - g) * LB))
+            blocks.append(wd * dtn_rows(B, dB, g, sn, Lx, Ly))
         D = np.vstack(blocks)
     n_base_rows = D.shape[0]
     if st.grad_rows:
@@ -301,6 +330,7 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
     inv = np.where(sv > cut, 1.0 / np.where(sv > cut, sv, 1.0), 0.0)
     st.rank = int(np.sum(sv > cut))
     st.sing = sv
+    st.D = D
     pinv = (Vt.T * inv) @ U.T              # (nb-1, rows)
 
     # P maps the raw check vector v to A: A = pinv @ rhs(v).
@@ -322,13 +352,14 @@ def make_setup(box, dims, p, M, gamma_top=0.0, gamma_bot=0.0, lam=None,
         P[:, kidx] -= Pper
         P[:, nm + kidx] += Pper
         r0 = len(kidx)
-        for f, (g, sn) in enumerate(((gamma_top, 1.0), (gamma_bot, -1.0))):
+        for f, (g, sn) in enumerate(((gamma_top, FACE_SIGNS[0]), (gamma_bot, FACE_SIGNS[1]))):
+            cz, cl = dtn_weights(g, sn)
             Pf = pinv[:, r0 + f * G * G: r0 + (f + 1) * G * G]
             LPf = np.stack([dtn_lambda(Pf[c].reshape(G, G), Lx, Ly).ravel()
                             for c in range(nb - 1)], axis=0)
             off = 2 * nm + f * G * G
-            P[:, off:off + G * G] += -wd * (1.0 - g) * LPf
-            P[:, ncheck + off:ncheck + off + G * G] += -wd * (1.0 + g) * sn * Pf
+            P[:, off:off + G * G] += -wd * cl * LPf
+            P[:, ncheck + off:ncheck + off + G * G] += -wd * cz * Pf
     if st.grad_rows:
         # raw vector gains [d_x Phi_B ; d_y Phi_B ; d_z Phi_B] at [mon ; wrap]
         nv0 = P.shape[1]

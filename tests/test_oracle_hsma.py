@@ -196,11 +196,16 @@ def test_hsma_translation_and_permutation_invariance():
     assert np.linalg.norm(F.sum(0)) < 1e-4 * np.abs(F).sum()
 
 
+# (force, energy) bounds: about 3x the errors measured with this seed
+# (force 1.3e-4 / 2.2e-4 / 1.5e-4, energy 1.2e-4 / 6.9e-4 / 3.2e-6)
+HSMA2D_BOUNDS = {0.0: (4e-4, 4e-4), 0.95: (7e-4, 2.1e-3), -0.95: (5e-4, 1e-5)}
+
+
 @pytest.mark.parametrize("gam", [0.0, 0.95, -0.95])
 def test_hsma2d_vs_ewald2d(gam):
     # 2D reading (DtN rows on a periodic face grid); charges kept 0.5 from the
-    # walls as the paper's LJ walls do.  Parity of the fit with the paper's own
-    # DtN discretisation is not pinned; the end result is, here.
+    # walls as the paper's LJ walls do.  The face rows themselves are pinned to
+    # the exact slab field in test_oracle_dtn.py; the end result is pinned here.
     c = workloads.small_case(40, dims=2, box=(20.0, 20.0, 10.0), p=8, M=1500,
                              gammas=(gam, gam), seed=9)
     x, q = workloads.electrolyte(c, margin=0.5)
@@ -209,8 +214,9 @@ def test_hsma2d_vs_ewald2d(gam):
     Ee, _, ge, _ = slab_ewald(xc, q, Lx, Ly, Lz, gam, gam, tol=1e-12)
     st = hsma.make_setup(c.box, 2, 8, 1500, gam, gam, dtn_grid=80)
     out = hsma.evaluate(st, x, q)
-    assert rel_force_err(out["forces"], -q[:, None] * ge) < 2e-3
-    assert abs(out["energy"] - Ee) < 2e-3 * abs(Ee)
+    bf, be = HSMA2D_BOUNDS[gam]
+    assert rel_force_err(out["forces"], -q[:, None] * ge) < bf
+    assert abs(out["energy"] - Ee) < be * abs(Ee)
 
 
 def test_2d_layers_and_errors():
