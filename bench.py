@@ -1,13 +1,17 @@
 """Benchmark: HSMA3D energy+force evaluations per second on one GB300.
 
 Workload (one "step" = one full evaluation of the hot path: prep, near field,
-check-point sums, fit + surface map, far field, assembly):
-  N = 100,000 ions (+-1, neutral, uniform, number density 0.1, so L = 100),
-  p = 8, M = 2,000 Fibonacci surface charges, lambda = 1.3 (27-cell shell),
-  FP32 pair arithmetic with compensated FP64 accumulation.
+check-point sums, fit + surface map, far field, assembly), the largest
+single-GPU configuration:
+  N = 262,144 ions (87,381 at +2, 174,762 at -1, one at 0: neutral; uniform,
+  number density 0.1, so L = 137.9), p = 10, M = 4,000 Fibonacci surface
+  charges, lambda = 1.3 (27-cell shell), FP32 pair arithmetic with compensated
+  FP64 accumulation and an FP64 fit.
 Seeded synthetic input (the paper's electrolytes are MD states that are not
 available).  ``value`` is evaluations/s with inputs resident in HBM; ``e2e``
 is the same through the C ABI with pinned host buffers, copies included.
+The N = 100,000, p = 8, M = 2,000 workload is reported beside it (``case2``),
+and the served request stream last (``serve``, ``serve_precision2``).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,7 +37,21 @@ import workloads  # noqa: E402
 METRIC = "HSMA energy+force evals/s & pair-ints/s at stated rel. error; serve p50/p99 ms"
 FP32_INSTR_PER_PAIR = 13      # 3 FADD, 3 FMUL/FFMA for r^2, 4 FMUL, 1 FADD, 3 FFMA
 FLOP_PER_PAIR = 20            # FMA = 2, rsqrt = 2
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128              # FP32 lanes per SM
+
+
+def sm_count():
+    """Streaming multiprocessors of the current CUDA device."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def host_cores():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def peaks():
@@ -120,14 +138,36 @@ def max_over_ranks(dist, v, device):
     return float(t.item())
 
 
-def oracle_sample(c, x, q, n_targets, seed=99, n_check=None, st=None):
+def _pairs_parallel(O, tgt, src, qs, exclude, threads):
+    """The oracle's direct sum, its targets split over a thread pool (NumPy
+    releases the interpreter lock inside its array operations)."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = len(tgt)
+    parts = [p for p in np.array_split(np.arange(n), max(1, min(n, 4 * threads))) if len(p)]
+    phi = np.zeros(n)
+    grad = np.zeros((n, 3))
+
+    def one(ix):
+        ex = None if exclude is None else exclude[ix]
+        return ix, O.pair_field(tgt[ix], src, qs, exclude=ex)
+
+    with ThreadPoolExecutor(threads) as pool:
+        for ix, (p, g) in pool.map(one, parts):
+            phi[ix] = p
+            grad[ix] = g
+    return phi, grad
+
+
+def oracle_sample(c, x, q, n_targets, seed=99, n_check=None, st=None, threads=None):
     """Time the oracle on a bounded sample; return (s per full eval, details).
 
     The near set, fit and surface map run in full; the near + far sums run on
     n_targets sampled ions and are scaled by N / n_targets.  With n_check, the
-    check-point sums also run on a sample (timing only) and are scaled.
+    check-point sums also run on a sample (timing only) and are scaled.  The
+    pair sums are split over ``threads`` host threads by target.
     """
     from oracle import hsma as O
+    threads = threads or host_cores()
     t0 = time.perf_counter()
     if st is None:
         st = O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
@@ -140,30 +180,29 @@ def oracle_sample(c, x, q, n_targets, seed=99, n_check=None, st=None):
     ipos, iq, isrc, isid = O.near_set(st, xc, qc)
     nc = len(st.check_pts)
     if n_check is None or n_check >= nc:
-        cphi, cgrad = O.pair_field(st.check_pts, ipos, iq)
+        cphi, cgrad = _pairs_parallel(O, st.check_pts, ipos, iq, None, threads)
         t_chk = 0.0
     else:
         ci = np.sort(rng.choice(nc, n_check, replace=False))
         tc = time.perf_counter()
-        sphi, sgrad = O.pair_field(st.check_pts[ci], ipos, iq)
+        sphi, sgrad = _pairs_parallel(O, st.check_pts[ci], ipos, iq, None, threads)
         t_chk = (time.perf_counter() - tc) * (nc / n_check - 1.0)
         cphi = np.zeros(nc); cgrad = np.zeros((nc, 3))
         cphi[ci] = sphi; cgrad[ci] = sgrad
     A = st.P @ O.check_raw(st, cphi, cgrad)
     Q = st.W @ A
-    t2 = time.perf_counter() + t_chk
+    t2 = time.perf_counter()
     s0 = O.self_shift(st)
     self_idx = np.full(c.N, -1)
     m0 = isid == s0
     self_idx[isrc[m0]] = np.nonzero(m0)[0]
-    nphi, ngrad = O.pair_field(xc[idx], ipos, iq, exclude=self_idx[idx])
-    fphi, fgrad = O.pair_field(xc[idx], st.ysurf, Q)
+    nphi, ngrad = _pairs_parallel(O, xc[idx], ipos, iq, self_idx[idx], threads)
+    fphi, fgrad = _pairs_parallel(O, xc[idx], st.ysurf, Q, None, threads)
     t3 = time.perf_counter()
-    t3 = t3 + t_chk
-    t_full = (t2 - t1) + (t3 - t2) * c.N / n_targets
+    t_full = (t2 - t1 + t_chk) + (t3 - t2) * c.N / n_targets
     F = -qc[idx, None] * (ngrad + fgrad)
     return t_full, dict(idx=idx, F=F, phi=nphi + fphi, t_setup=t_setup, t_fixed=t2 - t1,
-                        t_targets=t3 - t2, Ns=len(iq))
+                        t_targets=t3 - t2, t_wall=t3 - t1, Ns=len(iq), threads=threads)
 
 
 def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None, precision=1):
@@ -295,7 +334,7 @@ def other_cases(P, torch, dev, stream):
     out = {}
     cases = [(workloads.case(1), 20, 5), (workloads.case(3, -0.95), 20, 3),
              (workloads.case(3, 0.0), 20, 3), (workloads.case(3, 0.95), 20, 3),
-             (workloads.case(5), 5, 0)]
+             (workloads.case(2), 5, 1), (workloads.case(5), 3, 0)]
     for c, n32, n64 in cases:
         x, q = workloads.electrolyte(c)
         xd = torch.from_numpy(x).to(dev)
@@ -620,38 +659,173 @@ def md_e3(P, valence=1, steps_eq=20000, steps_prod=200000, every=100, seed=13, b
             "anion_profile": [round(float(v), 3) for v in prof[1]]}
 
 
-def cores_used():
-    return 1   # the oracle's pair sums are single-threaded NumPy
+def workload_config(c, ws=1):
+    """The workload's config, the same for both arms."""
+    return {"workload": c.name, "N": c.N, "p": c.p, "M": c.M, "lambda": c.lam,
+            "box": [round(v, 6) for v in c.box], "parallelism": f"replicas x{ws}"}
 
 
-def run_reference(args, c, rank, dist):
+def run_reference(args, c, rank, dist, ws):
     if rank != 0:
         return
     from oracle import hsma as O
     x, q = workloads.electrolyte(c)
     st = O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
                       dtn_grid=c.dtn_grid)
-    n_t, n_c = min(40, c.N), 32
+    threads = host_cores()
+    n_t, n_c = min(128, c.N), 64
     for _ in range(args.warmup):
-        oracle_sample(c, x, q, n_t, n_check=n_c, st=st)
-    ts = []
+        oracle_sample(c, x, q, n_t, n_check=n_c, st=st, threads=threads)
+    t_eval, t_wall = [], []
     for k in range(args.steps):
-        t, d = oracle_sample(c, x, q, n_t, seed=100 + k, n_check=n_c, st=st)
-        ts.append(t)
-    t_eval = float(np.mean(ts))
-    v = 1.0 / t_eval
+        t, d = oracle_sample(c, x, q, n_t, seed=100 + k, n_check=n_c, st=st, threads=threads)
+        t_eval.append(t)
+        t_wall.append(d["t_wall"])
+    # each step computes part of an evaluation: the near set, the fit and the
+    # surface map in full, the pair sums of a sample; evals_per_step is that
+    # part's share of one evaluation's (scaled) time
+    v = 1.0 / float(np.mean(t_eval))
+    ms_step = 1e3 * float(np.mean(t_wall))
     sample = (f"per step: near set, fit and surface map in full; check-point sums on {n_c} "
               f"sampled check points and near+far sums on {n_t} sampled ions, each scaled to "
-              f"the full count")
+              f"the full count; pair sums split by target over {threads} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_eval, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms_step, "evals_per_step": v * ms_step / 1e3,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": c.name, "N": c.N, "p": c.p, "M": c.M, "lambda": c.lam},
-            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores_used(), "kind": "oracle",
+            "config": workload_config(c, ws),
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": threads, "kind": "oracle",
                              "sample": sample, "cpu": platform.processor() or platform.machine()},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+KERNEL_NAMES = {12: "k_pair_f32x2<1>", 14: "k_pair_f32x2<2>", 24: "k_pair_f32x2s<2>", 1: "k_pair_f32<1>",
+                2: "k_pair_f32<2>", 4: "k_pair_f32<4>", 32: "k_pair_f32x2x<1>", 34: "k_pair_f32x2x<2>",
+                44: "k_pair_f32x2xs<2>"}
+
+
+def pair_roofline(P, h, c, pairs_near, near_ms, peak_instr, mhz_src, sms, lib_total_ms=None):
+    """FP32 issue-rate roofline of the near-field + check-point launch."""
+    plan = {"kernel": KERNEL_NAMES.get(int(P.hsma_get_info(h.h, "kernel")), "k_pair_f32"),
+            "chunks": int(P.hsma_get_info(h.h, "chunks")), "grid": int(P.hsma_get_info(h.h, "grid")),
+            "tile_targets": int(P.hsma_get_info(h.h, "tile_targets"))}
+    t_near = near_ms / 1e3
+    achieved = pairs_near * FP32_INSTR_PER_PAIR / t_near / 1e12
+    roof = {"bound": "alu", "kernel": plan["kernel"] + " (near field + check points)",
+            "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s",
+            "frac": achieved / peak_instr, "traffic": None,
+            "algorithmic": f"{FP32_INSTR_PER_PAIR} FP32-pipe instructions per pair x {pairs_near} pairs "
+                           f"(targets x images in B) per launch",
+            "flops_view": {"achieved_tflops": pairs_near * FLOP_PER_PAIR / t_near / 1e12,
+                           "peak_tflops": 2 * peak_instr,
+                           "frac": (pairs_near * FLOP_PER_PAIR / t_near / 1e12) / (2 * peak_instr)},
+            "peak_source": f"{sms} SMs x {FP32_LANES} FP32 lanes x {mhz_src}",
+            "near_ms": near_ms}
+    if lib_total_ms is not None:
+        roof["lib_total_ms"] = lib_total_ms
+    try:
+        sha = pair_sources_sha1()
+        for rec in traffic_records():
+            if (rec.get("pair_sources_sha1") == sha and rec.get("chunks") == plan["chunks"]
+                    and rec.get("workload") == c.name and rec.get("kernel", "").startswith(plan["kernel"])):
+                roof["traffic"] = rec.get("bytes_per_launch")
+                roof["traffic_workload"] = rec.get("workload")
+    except Exception:
+        pass
+    return roof, plan
+
+
+def timed_evals(P, torch, stream, h, xd, qd, N, e, f, n):
+    """Mean device time (ms) of n evaluations on the stream, inputs resident."""
+    P.hsma_eval_into(h.h, xd, qd, N, e, f)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n):
+        P.hsma_eval_into(h.h, xd, qd, N, e, f)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / n
+
+
+def secondary_case(P, torch, dev, stream, c, peak_instr, mhz_src, sms, steps=10):
+    """Another dense workload at full size, inputs resident, L2 flushed between
+    evaluations: evaluations/s, pair interactions/s and the near-field launch's
+    FP32 roofline."""
+    x, q = workloads.electrolyte(c)
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q).to(dev)
+    fd = torch.empty((c.N, 3), dtype=torch.float64, device=dev)
+    e = np.zeros(1)
+    h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=1, timing=1, dtn_grid=c.dtn_grid)
+    P.hsma_set_stream(h.h, stream.cuda_stream)
+    for _ in range(3):
+        P.hsma_eval_into(h.h, xd, qd, c.N, e, fd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    ms, near = [], []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.hsma_eval_into(h.h, xd, qd, c.N, e, fd)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        near.append(P.hsma_get_info(h.h, "t_near_ms"))
+    Ns = int(P.hsma_get_info(h.h, "Ns"))
+    nck = int(P.hsma_get_info(h.h, "n_check"))
+    pairs_near = (c.N + nck) * Ns
+    pairs = pairs_near + c.N * c.M
+    roof, plan = pair_roofline(P, h, c, pairs_near, float(np.mean(near)), peak_instr, mhz_src, sms)
+    h.close()
+    t = float(np.mean(ms)) / 1e3
+    return {"workload": c.name, "N": c.N, "p": c.p, "M": c.M, "evals_per_s": 1.0 / t, "ms_per_eval": 1e3 * t,
+            "N_s": Ns, "n_check": nck, "pairs_per_eval": pairs, "pair_ints_per_s": pairs / t,
+            "plan": plan, "roofline": roof}
+
+
+def paper_accuracy(P, torch, dev, stream):
+    """Throughput at the accuracy the paper times at (relative force error
+    about 1e-5 against the exact sum, Sec. 3.2 and Sec. 5): the unmasked
+    27-cell near set at p = 10 (reading R12), dense and tree, at N = 100,000.
+    The method's error at the same parameters is measured here against Ewald
+    on the N = 1000 system (FP32 pairs, through the library)."""
+    from oracle.ewald import ewald3d
+    opts = dict(sphere_mask=0, n_monitor=242)
+    p, M = 10, 2000
+    small = workloads.case(1)
+    xs, qs = workloads.electrolyte(small)
+    L = small.box[0]
+    xc = (xs - L * np.floor(xs / L)) - 0.5 * L
+    Ee, _, ge = ewald3d(xc, qs, small.box)
+    Fe = -qs[:, None] * ge
+    out = {"parameters": f"p = {p}, M = {M}, N_m = 242, lambda = 1.3, unmasked 27-cell near set (R12), FP32 pairs"}
+    errs = {}
+    for tree in (0, 1):
+        h = P.HSMA(small.box, 3, p, M, precision=1, near_tree=tree, **opts)
+        E, F, _ = h.eval(xs, qs)
+        h.close()
+        errs[tree] = (float(math.sqrt(np.mean(np.sum((F - Fe) ** 2, 1)) / np.mean(np.sum(Fe ** 2, 1)))),
+                      abs(E - Ee) / abs(Ee))
+    c = workloads.case(2)
+    x, q = workloads.electrolyte(c)
+    xd = torch.from_numpy(x).to(dev)
+    qd = torch.from_numpy(q).to(dev)
+    f = torch.empty((c.N, 3), dtype=torch.float64, device=dev)
+    e = np.zeros(1)
+    for tree, n in ((0, 3), (1, 10)):
+        h = P.HSMA(c.box, 3, p, M, precision=1, near_tree=tree, **opts)
+        P.hsma_set_stream(h.h, stream.cuda_stream)
+        ms = timed_evals(P, torch, stream, h, xd, qd, c.N, e, f, n)
+        key = "tree" if tree else "dense"
+        out[key] = {"workload": f"hsma3d_n100000_rho0.1_p{p}_M{M}_unmasked", "evals_per_s": 1e3 / ms,
+                    "N_s": int(P.hsma_get_info(h.h, "Ns")),
+                    "rel_force_err_vs_ewald_n1000": errs[tree][0], "rel_energy_err_vs_ewald_n1000": errs[tree][1]}
+        h.close()
+    return out
 
 
 def main():
@@ -661,15 +835,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other-cases", action="store_true")
-    ap.add_argument("--case", type=int, default=2, help="workload case (default 2: N = 100,000)")
+    ap.add_argument("--case", type=int, default=5,
+                    help="workload case (default 5: N = 262,144, p = 10, M = 4000; 2: N = 100,000)")
     ap.add_argument("--clocks-log", default=None,
                     help="keep the nvidia-smi samples of the timed region in this CSV file")
     ap.add_argument("--record-traffic", default=None,
                     help="add to profiles/traffic.json the near-field launch of this ncu CSV, captured "
-                         "with --targets-per-thread 24 --chunks K, and exit")
+                         "with --targets-per-thread T --chunks K on --case C, and exit")
     ap.add_argument("--chunks", type=int, default=0,
                     help="source chunks of the near-field launch (0: the library's autotuner)")
     ap.add_argument("--targets-per-thread", type=int, default=0,
@@ -687,21 +862,23 @@ def main():
                     help="0: surface charges (Eq. 8, default); 1: the fitted series (Eq. 5)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.record_traffic:
-        if args.targets_per_thread != 24 or args.chunks < 1:
-            raise SystemExit("--record-traffic needs --targets-per-thread 24 and --chunks K")
-        k = args.chunks
-        print(json.dumps(record_traffic(
-            args.record_traffic, "k_pair_f32x2s<2> near field + check points", "hsma3d_n100000_rho0.1_p8_M2000",
-            k, "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-               "--clock-control none -k regex:k_pair_f32x2s -s 4 -c 2 --csv --log-file near_traffic.csv "
-               "python bench.py --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --no-serve "
-               f"--no-other-cases --targets-per-thread 24 --chunks {k}")))
-        return
     c = workloads.case(args.case)
+    if args.record_traffic:
+        if not args.targets_per_thread or args.chunks < 1:
+            raise SystemExit("--record-traffic needs --targets-per-thread T and --chunks K")
+        k, tpt = args.chunks, args.targets_per_thread
+        kname = KERNEL_NAMES[tpt]
+        regex = kname.split("<")[0]
+        print(json.dumps(record_traffic(
+            args.record_traffic, kname + " near field + check points", c.name,
+            k, "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+               f"--clock-control none -k regex:{regex} -s 4 -c 2 --csv --log-file near_traffic.csv "
+               f"python bench.py --case {args.case} --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 "
+               f"--no-serve --no-other-cases --targets-per-thread {tpt} --chunks {k}")))
+        return
     dist, rank, ws, local = dist_init(args)
     if args.impl == "reference":
-        run_reference(args, c, rank, dist)
+        run_reference(args, c, rank, dist, ws)
         if dist:
             dist.barrier()
         return
@@ -734,7 +911,8 @@ def main():
 
     x, q = workloads.electrolyte(c, seed=c.seed + 1000 * rank)
     N = c.N
-    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, timing=1, far_field=args.far_field, near_tree=args.near_tree)
+    h = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=1, timing=1,
+               far_field=args.far_field, near_tree=args.near_tree, dtn_grid=c.dtn_grid)
     if args.targets_per_thread:
         h.set_option("targets_per_thread", args.targets_per_thread)
     if args.chunks:
@@ -777,11 +955,6 @@ def main():
     energy = float(ebuf[0])
     Ns = int(P.hsma_get_info(h.h, "Ns"))
     n_check = int(P.hsma_get_info(h.h, "n_check"))
-    kern = {12: "k_pair_f32x2<1>", 14: "k_pair_f32x2<2>", 24: "k_pair_f32x2s<2>", 1: "k_pair_f32<1>",
-            2: "k_pair_f32<2>",
-            4: "k_pair_f32<4>"}.get(int(P.hsma_get_info(h.h, "kernel")), "k_pair_f32")
-    plan = {"kernel": kern, "chunks": int(P.hsma_get_info(h.h, "chunks")),
-            "grid": int(P.hsma_get_info(h.h, "grid")), "tile_targets": int(P.hsma_get_info(h.h, "tile_targets"))}
     pairs_near = (N + n_check) * Ns
     pairs_far = 0 if args.far_field else N * c.M     # the series has no pair sum
     pairs = pairs_near + pairs_far
@@ -807,41 +980,29 @@ def main():
     # the plain FP64 GPU form, for the record
     fp64 = None
     if args.fp64_steps > 0:
-        h64 = P.HSMA(c.box, 3, c.p, c.M, precision=0, timing=1)
+        h64 = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=0, timing=1,
+                     dtn_grid=c.dtn_grid)
         P.hsma_set_stream(h64.h, stream.cuda_stream)
         e64 = np.zeros(1)
         f64 = torch.empty((N, 3), dtype=torch.float64, device=dev)
-        P.hsma_eval_into(h64.h, xd, qd, N, e64, f64)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.fp64_steps):
-            P.hsma_eval_into(h64.h, xd, qd, N, e64, f64)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t64 = a.elapsed_time(b) / args.fp64_steps
+        t64 = timed_evals(P, torch, stream, h64, xd, qd, N, e64, f64, args.fp64_steps)
         dF = (fd - f64).double()
         fp64 = {"evals_per_s": 1e3 / t64, "ms_per_eval": t64,
                 "near_ms": P.hsma_get_info(h64.h, "t_near_ms"),
                 "fp32_vs_fp64_rel_energy": abs(energy - float(e64[0])) / abs(float(e64[0])),
-                "fp32_vs_fp64_rel_force_rms": float(torch.sqrt((dF ** 2).sum() / (f64 ** 2).sum()))}
+                "fp32_vs_fp64_rel_force_rms": float(torch.sqrt((dF ** 2).sum() / (f64 ** 2).sum())),
+                "fp32_vs_fp64_max_ion_force_err": float(
+                    (torch.sqrt((dF ** 2).sum(1)).max() / torch.sqrt((f64 ** 2).sum(1).mean())).item())}
         h64.close()
         # precision 2 (exact source-target differences) against the same FP64 result
-        h2 = P.HSMA(c.box, 3, c.p, c.M, precision=2)
+        h2 = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=2, dtn_grid=c.dtn_grid)
         P.hsma_set_stream(h2.h, stream.cuda_stream)
         e2 = np.zeros(1)
         f2 = torch.empty((N, 3), dtype=torch.float64, device=dev)
-        P.hsma_eval_into(h2.h, xd, qd, N, e2, f2)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(5):
-            P.hsma_eval_into(h2.h, xd, qd, N, e2, f2)
-        b.record(stream)
-        torch.cuda.synchronize()
+        t2 = timed_evals(P, torch, stream, h2, xd, qd, N, e2, f2, 5)
         dF2 = (f2 - f64).double()
-        fp64["precision2"] = {"evals_per_s": 5e3 / a.elapsed_time(b),
-                              "kernel": int(P.hsma_get_info(h2.h, "kernel")),
+        fp64["precision2"] = {"evals_per_s": 1e3 / t2,
+                              "kernel": KERNEL_NAMES.get(int(P.hsma_get_info(h2.h, "kernel"))),
                               "rel_energy_vs_fp64": abs(float(e2[0]) - float(e64[0])) / abs(float(e64[0])),
                               "rel_force_rms_vs_fp64": float(torch.sqrt((dF2 ** 2).sum() / (f64 ** 2).sum()))}
         h2.close()
@@ -852,78 +1013,87 @@ def main():
         return
 
     mhz, mhz_src = peaks()
-    peak_instr = SMS * FP32_LANES * mhz * 1e6 / 1e12          # T lane-instr/s
-    t_near = float(np.mean(near_ms)) / 1e3
-    achieved = pairs_near * FP32_INSTR_PER_PAIR / t_near / 1e12
-    roof = {"bound": "alu", "kernel": plan["kernel"] + " (near field + check points)",
-            "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s",
-            "frac": achieved / peak_instr, "traffic": None,
-            "flops_view": {"achieved_tflops": pairs_near * FLOP_PER_PAIR / t_near / 1e12,
-                           "peak_tflops": 2 * peak_instr,
-                           "frac": (pairs_near * FLOP_PER_PAIR / t_near / 1e12) / (2 * peak_instr)},
-            "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({mhz_src})",
-            "near_ms": 1e3 * t_near, "lib_total_ms": float(np.mean(total_lib_ms))}
+    sms = sm_count()
+    peak_instr = sms * FP32_LANES * mhz * 1e6 / 1e12          # T lane-instr/s
+    mhz_txt = f"{mhz:.0f} MHz ({mhz_src})"
+    roof, plan = pair_roofline(P, h, c, pairs_near, float(np.mean(near_ms)), peak_instr, mhz_txt, sms,
+                               lib_total_ms=float(np.mean(total_lib_ms)))
     if args.near_tree:
         # the tree does not sum the dense pairs: no pair-count roofline
         roof = {"bound": "alu", "kernel": "k_tree_eval<10> (near field + check points)", "achieved": None,
                 "peak": peak_instr, "unit": "T FP32-pipe instr/s", "frac": None, "traffic": None,
-                "note": "tree evaluation; see profiles/k_tree_eval_hsma3d_n100000_p8_M2000_P10.md",
-                "near_ms": 1e3 * t_near, "lib_total_ms": float(np.mean(total_lib_ms))}
-    if not args.near_tree:
-        try:
-            sha = pair_sources_sha1()
-            for rec in traffic_records():
-                if (rec.get("pair_sources_sha1") == sha and rec.get("chunks") == plan["chunks"]
-                        and rec.get("kernel", "").startswith(plan["kernel"])):
-                    roof["traffic"] = rec.get("bytes_per_launch")
-        except Exception:
-            pass
+                "near_ms": float(np.mean(near_ms)), "lib_total_ms": float(np.mean(total_lib_ms))}
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 accumulation/fit",
             "data": "synthetic",
-            "config": {"workload": c.name, "N": N, "p": c.p, "M": c.M, "lambda": c.lam,
-                       "N_s": Ns, "n_check": n_check, "precision": "fp32-compute/fp64-accumulate",
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}",
-                       "far_field": "series (Eq. 5)" if args.far_field else "surface charges (Eq. 8)",
-                       "near_field": "tree, order 10" if args.near_tree else "direct sums",
-                       "plan": plan},
+            "config": workload_config(c, ws),
+            "run": {"N_s": Ns, "n_check": n_check, "precision": "fp32-compute/fp64-accumulate",
+                    "l2": "flushed between steps (256 MB write)",
+                    "far_field": "series (Eq. 5)" if args.far_field else "surface charges (Eq. 8)",
+                    "near_field": "tree, order 10" if args.near_tree else "direct sums", "plan": plan},
             "pair_ints_per_s": pairs * ws / (ms_step / 1e3), "pairs_per_eval": pairs,
             "energy": energy, "roofline": roof,
             "e2e": {"value": ws / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": N * 32,
                     "d2h_bytes_per_step": N * 24 + 8},
-            "gpu_launches": int(P.hsma_get_info(h.h, "kernels_per_eval")) * args.steps, "clocks": clk.summary(), "fp64_path": fp64}
+            "gpu_launches": int(P.hsma_get_info(h.h, "kernels_per_eval")) * args.steps, "clocks": clk.summary(),
+            "fp64_path": fp64}
     if not args.no_cpu_baseline:
-        t_full, d = oracle_sample(c, x, q, 400)
+        n_s = 512
+        t_full, d = oracle_sample(c, x, q, n_s)
         Fg = fd.cpu().numpy()[d["idx"]]
         Fo = d["F"]
         line["cpu_baseline"] = {
-            "value": 1.0 / t_full, "unit": "evals/s", "cores": cores_used(), "kind": "oracle",
-            "sample": (f"full check-point sums + fit, near+far on 400 of {N} ions, scaled by N/400; "
-                       f"measured {d['t_fixed'] + d['t_targets']:.1f} s"),
+            "value": 1.0 / t_full, "unit": "evals/s", "cores": d["threads"], "kind": "oracle",
+            "sample": (f"full check-point sums + fit, near+far on {n_s} of {N} ions, scaled by N/{n_s}; "
+                       f"pair sums split by target over {d['threads']} host threads; "
+                       f"measured {d['t_wall']:.1f} s wall"),
             "cpu": platform.processor() or platform.machine()}
         line["accuracy_vs_oracle"] = {
-            "sampled_ions": 400,
+            "sampled_ions": n_s,
             "rel_force_rms": float(math.sqrt(np.mean(np.sum((Fg - Fo) ** 2, 1)) / np.mean(np.sum(Fo ** 2, 1)))),
+            "max_ion_force_err_over_rms": float(np.sqrt(np.sum((Fg - Fo) ** 2, 1)).max()
+                                                / math.sqrt(np.mean(np.sum(Fo ** 2, 1)))),
             "rel_energy_vs_fp64_gpu": fp64["fp32_vs_fp64_rel_energy"] if fp64 else None}
-    if not args.no_serve:
-        line["serve"] = serve_bench(P)
-        line["serve_precision2"] = serve_bench(P, precision=2)
     if not args.no_other_cases:
+        if args.case != 2:
+            line["case2"] = secondary_case(P, torch, dev, stream, workloads.case(2), peak_instr, mhz_txt, sms)
+        line["case3_2d"] = secondary_case(P, torch, dev, stream, workloads.case(3, 0.95), peak_instr, mhz_txt,
+                                          sms)
+        line["paper_accuracy"] = paper_accuracy(P, torch, dev, stream)
         if not args.far_field and not args.near_tree:
-            line["far_field_series"] = far_series_compare(P, torch, stream, c, xd, qd, fd, h)
+            c2 = workloads.case(2)
+            x2, q2 = workloads.electrolyte(c2)
+            xd2 = torch.from_numpy(x2).to(dev)
+            qd2 = torch.from_numpy(q2).to(dev)
+            fd2 = torch.empty((c2.N, 3), dtype=torch.float64, device=dev)
+            h2b = P.HSMA(c2.box, 3, c2.p, c2.M, precision=1, timing=1)
+            P.hsma_set_stream(h2b.h, stream.cuda_stream)
             e0 = np.zeros(1)
-            P.hsma_eval_into(h.h, xd, qd, N, e0, fd)
+            P.hsma_eval_into(h2b.h, xd2, qd2, c2.N, e0, fd2)
+            torch.cuda.synchronize()
+            line["far_field_series"] = far_series_compare(P, torch, stream, c2, xd2, qd2, fd2, h2b)
+            P.hsma_eval_into(h2b.h, xd2, qd2, c2.N, e0, fd2)
             torch.cuda.synchronize()
             line["option_variants"] = [
-                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), sphere_mask=0),
-                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), grad_rows=1),
-                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), n=10, near_tree=1),
-                option_variant(P, torch, stream, c, xd, qd, fd, float(e0[0]), n=10, near_tree=1, far_field=1)]
+                option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), sphere_mask=0),
+                option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), grad_rows=1),
+                option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), n=10, near_tree=1),
+                option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), n=10, near_tree=1, far_field=1)]
+            h2b.close()
         line["other_cases"] = other_cases(P, torch, dev, stream)
         line["paper_like"] = paper_like(P, torch, dev, stream)
-        line["md_e1_short"] = md_e1(P, valence=1, steps_eq=500, steps_prod=2000, rdf_every=100)
+    if not args.no_serve:
+        # last, so that the end of the line (what a log tail keeps) shows them
+        line["serve"] = serve_bench(P)
+        line["serve_precision2"] = serve_bench(P, precision=2)
+        line["serve_summary"] = {
+            f"precision{k}": {key: round(float(line[name][key]), 4) for key in
+                              ("evals_per_s", "p50_ms", "p99_ms", "one_at_a_time_evals_per_s",
+                               "saturated_evals_per_s", "saturated_vs_one_at_a_time", "served_vs_fp64",
+                               "max_rel_force_rms_vs_fp64")}
+            for k, name in ((1, "serve"), (2, "serve_precision2"))}
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

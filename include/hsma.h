@@ -278,15 +278,18 @@ int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamm
 /*
  * hsma_pair_sum_static -- the direct pair sum (the kernel behind the near
  * field, the check-point sums and the far field) without any device
- * allocation.  The paper has no counterpart: this entry point exists for
- * callers that cannot call cudaMalloc -- code running while CUDA stream
- * capture is active in global mode, engines that hand out all device memory
- * from their own pool, real-time loops that must not allocate.
+ * allocation.  The paper has no counterpart.  It exists for callers that
+ * cannot call cudaMalloc: engines that hand out all device memory from their
+ * own pool and forbid raw cudaMalloc/cudaFree (an allocation behind the pool's
+ * back breaks its accounting), plug-ins that run inside such an engine, and
+ * real-time loops that must not pay for an allocation or for the
+ * synchronisation that freeing implies.
  *
- * targets: n_tgt*3 doubles (x, y, z), device memory.
- * sources: n_src*4 doubles (x, y, z, q), device memory.
- * out:     n_tgt*4 doubles, device memory: phi(t) = sum_s q_s/|x_s - t| and
- *          its gradient with respect to t (dphi/dx, dphi/dy, dphi/dz).
+ * targets: n_tgt*3 doubles (x, y, z), device memory of the current device.
+ * sources: n_src*4 doubles (x, y, z, q), device memory of the current device.
+ * out:     n_tgt*4 doubles, device memory of the current device:
+ *          phi(t) = sum_s q_s/|x_s - t| and its gradient with respect to t
+ *          (dphi/dx, dphi/dy, dphi/dz), row-major per target.
  *          A source at exactly a target's position divides by zero.
  * precision: 0 = FP64 pairs, 1 = FP32 pairs with compensated accumulation.
  * stream:  cudaStream_t to run on (NULL = the legacy default stream); the call
@@ -297,13 +300,17 @@ int hsma_geometry_array(const double box[3], int dims, int p, int M, double gamm
  * leaves its contents behind; every element a call reads is written by that
  * same call first, so nothing needs clearing.  Calls whose work overlaps on
  * the GPU (other streams, other host threads) race on it: order them.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, which may load the module); make that first call
- * before any stream capture.  The call allocates nothing itself.
+ * The first call on each device (and the first after that device's context
+ * has been replaced, e.g. by cudaDeviceReset) looks up the array's device
+ * address with cudaGetSymbolAddress, which may load the module; make that
+ * first call before any stream capture.  The call allocates nothing itself.
+ * The chunk partial sums are combined by a small fixed-order kernel of its
+ * own (8 warps per 32 targets), not by the evaluation's reduction.
  * Limit: (n_tgt + n_src) * (16 bytes in FP32, 32 in FP64) plus 32 * n_tgt
  * bytes of partial sums must fit in 64 MiB; larger inputs are rejected with
  * HSMA_ERR_ARG before any device work.
- * Errors: HSMA_ERR_ARG (NULL pointer, n < 1, precision, size), HSMA_ERR_CUDA.
+ * Errors: HSMA_ERR_ARG (NULL pointer, n < 1, precision, size, or a pointer
+ * that is not memory of the current device), HSMA_ERR_CUDA.
  */
 int hsma_pair_sum_static(const double* targets, int64_t n_tgt, const double* sources,
                          int64_t n_src, double* out, int precision, void* stream);

@@ -230,12 +230,19 @@ def hsma_pair_sum_static(targets, sources, out, precision=1, stream_ptr=0):
     """Direct pair sum with the library's static scratch (no device allocation).
 
     targets (n_t, 3), sources (n_s, 4: x, y, z, q) and out (n_t, 4: phi,
-    dphi/dx, dphi/dy, dphi/dz) are float64 CUDA tensors; the work is enqueued
-    on the given stream and is complete when that stream reaches it.
+    dphi/dx, dphi/dy, dphi/dz) are float64 CUDA tensors on one device; the
+    call runs with that device current, the work is enqueued on the given
+    stream and is complete when that stream reaches it.
     """
+    if not all(_is_torch(a) and a.is_cuda for a in (targets, sources, out)):
+        raise ValueError("hsma_pair_sum_static takes CUDA tensors only")
+    if not (targets.device == sources.device == out.device):
+        raise ValueError("targets, sources and out must be on the same CUDA device")
+    import torch
     nt, ns = int(targets.shape[0]), int(sources.shape[0])
-    rc = lib().hsma_pair_sum_static(_ptr(targets, 3 * nt), nt, _ptr(sources, 4 * ns), ns,
-                                    _ptr(out, 4 * nt), int(precision), ctypes.c_void_p(stream_ptr))
+    with torch.cuda.device(targets.device):
+        rc = lib().hsma_pair_sum_static(_ptr(targets, 3 * nt), nt, _ptr(sources, 4 * ns), ns,
+                                        _ptr(out, 4 * nt), int(precision), ctypes.c_void_p(stream_ptr))
     if rc != HSMA_OK:
         raise HSMAError(rc, "hsma_pair_sum_static failed")
     return out

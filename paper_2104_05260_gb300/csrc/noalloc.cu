@@ -2,14 +2,15 @@
 // far-field kernel of the evaluation) for callers that cannot allocate
 // device memory.
 //
-// Who needs it: code that runs while CUDA stream capture is active in global
-// mode (cudaMalloc is not allowed then), engines that hand out all device
-// memory from their own pool and forbid raw cudaMalloc/cudaFree, and
-// real-time loops that must not pay for an allocation.  Such a caller passes
-// its inputs and outputs as device pointers; the kernel's scratch (the
-// converted targets and sources and the per-chunk partial sums) lives in one
-// file-scope __device__ array of fixed size instead of memory from
-// cudaMalloc.
+// Who needs it: engines that hand out all device memory from their own pool
+// and forbid raw cudaMalloc/cudaFree (an allocation behind the pool's back
+// breaks its accounting), plug-ins that run inside such an engine, and
+// real-time loops that must not pay for an allocation or the synchronisation
+// that cudaFree implies.  Such a caller passes its inputs and outputs as
+// device pointers; the kernel's scratch (the converted targets and sources
+// and the per-chunk partial sums) lives in one file-scope __device__ array of
+// fixed size instead of memory from cudaMalloc.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,24 +30,74 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchAddr {
+  void* ptr = nullptr;
+  unsigned long long ctx_id = 0;   // context the address belongs to
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the scratch array for the current device.  Host code may
-// not use g_static_scratch itself: on the host that name is only a stand-in.
+// Unique id of the current CUDA context (0 if the driver cannot tell).  A
+// device reset or a new primary context loads the module again, possibly at
+// another address, so the cached address is keyed by the context's id.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetIdFn)f;
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array for the current device and context,
+// looked up with cudaGetSymbolAddress the first time (per device, and again
+// after the device's context has been replaced).  Host code may not use
+// g_static_scratch itself: on the host that name is only a stand-in.
 cudaError_t scratch_for_current_device(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchAddr& c = g_scratch[dev];
+  if (!c.ptr || c.ctx_id != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
+    c.ptr = p;
+    c.ctx_id = ctx;
   }
-  *out = g_scratch_ptr[dev];
+  *out = c.ptr;
   return cudaSuccess;
+}
+
+// True when p is device memory of the current device (or managed memory).
+bool on_current_device(const void* p) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -67,13 +118,34 @@ __global__ void k_convert(const double* __restrict__ tgt, int n_tgt, const doubl
   }
 }
 
-__global__ void k_combine(const double* __restrict__ part, int n_chunks, int n_tgt, double* out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_tgt) return;
-  for (int c = 0; c < 4; ++c) {
-    double s = 0.0;
-    for (int ch = 0; ch < n_chunks; ++ch) s += part[((size_t)ch * 4 + c) * n_tgt + t];
-    out[4 * (size_t)t + c] = s;
+// out[4 t + c] = sum over chunks of part[(chunk * 4 + c) * n_tgt + t].  A block
+// takes 32 targets; its 8 warps sum every 8th chunk (lanes over targets, so
+// the reads are coalesced), then warp 0 adds the 8 partial sums in warp
+// order.  The order is fixed, so the result does not depend on the launch.
+constexpr int kCombineWarps = 8;
+__global__ void __launch_bounds__(32 * kCombineWarps) k_combine(const double* __restrict__ part, int n_chunks,
+                                                                int n_tgt, double* __restrict__ out) {
+  __shared__ double sh[kCombineWarps][4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  if (t < n_tgt) {
+    for (int ch = w; ch < n_chunks; ch += kCombineWarps) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s[c] += part[((size_t)ch * 4 + c) * n_tgt + t];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) sh[w][c][lane] = s[c];
+  __syncthreads();
+  if (w == 0 && t < n_tgt) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCombineWarps; ++k) v += sh[k][c][lane];
+      out[4 * (size_t)t + c] = v;
+    }
   }
 }
 
@@ -92,6 +164,8 @@ extern "C" int hsma_pair_sum_static(const double* targets, int64_t n_tgt, const 
   const size_t per_chunk = round256((size_t)4 * n_tgt * 8);
   if (n_tgt > (1 << 30) || n_src > (1 << 30) || fixed + per_chunk > kStaticScratchBytes)
     return HSMA_ERR_ARG;   // beyond the 64 MiB static scratch
+  if (!on_current_device(targets) || !on_current_device(sources) || !on_current_device(out))
+    return HSMA_ERR_ARG;   // host memory or another GPU's memory: not reachable as scratch-free device input
   void* base = nullptr;
   cudaError_t e = scratch_for_current_device(&base);
   if (e != cudaSuccess) {
@@ -128,7 +202,7 @@ extern "C" int hsma_pair_sum_static(const double* targets, int64_t n_tgt, const 
   const long items = (long)tiles * chunks;
   e = launch_pair(precision, tpt, a, (int)(items < slots ? items : slots), s);
   if (e == cudaSuccess) {
-    k_combine<<<(int)((n_tgt + 255) / 256), 256, 0, s>>>(part, chunks, (int)n_tgt, out);
+    k_combine<<<(int)((n_tgt + 31) / 32), 32 * kCombineWarps, 0, s>>>(part, chunks, (int)n_tgt, out);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {

@@ -42,6 +42,22 @@ def pot_err(pot, ref):
     d = pot - ref
     return math.sqrt(np.mean((d - d.mean()) ** 2) / np.mean(ref ** 2))
 
+# Per-ion bound beside the relative RMS: the largest single-ion force error
+# (and, after removing the mean offset, potential error) relative to the RMS of
+# the reference, at most FMAX times the RMS bound.  A local mistake (one ion's
+# own images, an ion next to a wall) can hide inside an RMS over all ions.
+FMAX = 20
+
+
+def fmax(F, Fr):
+    return float(np.sqrt(np.sum((F - Fr) ** 2, 1)).max() / math.sqrt(np.mean(np.sum(Fr ** 2, 1))))
+
+
+def pmax(pot, ref):
+    d = pot - ref
+    return float(np.abs(d - d.mean()).max() / math.sqrt(np.mean(ref ** 2)))
+
+
 
 def check_series(P, c, x, q, prec, st=None, **opt):
     st = st or O.make_setup(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], lam=c.lam,
@@ -56,6 +72,7 @@ def check_series(P, c, x, q, prec, st=None, **opt):
     scale = abs(ref["energy"]) if prec == 0 else 0.5 * float(np.sum(np.abs(ref["q"] * ref["phi"])))
     assert abs(E - ref["energy"]) <= E_TOL[prec] * scale, (E, ref["energy"], scale)
     assert frms(F, ref["forces"]) <= F_TOL[prec]
+    assert fmax(F, ref["forces"]) <= FMAX * F_TOL[prec], fmax(F, ref["forces"])
     assert pot_err(pot, ref["phi"]) <= F_TOL[prec]
     if prec == 0:
         # the coefficients the series kernel consumes (FP32 check sums perturb

@@ -1,13 +1,14 @@
 """The no-allocation pair sum (hsma_pair_sum_static) against the regular path.
 
-Callers that cannot call cudaMalloc (code inside global-mode stream capture,
-engines that own all device memory through their own pool, real-time loops)
-use hsma_pair_sum_static, whose scratch is a fixed array inside the library.
-This file checks, through the C ABI, that it reproduces what the regular
-evaluation computes with the same kernel: Phi_B and dPhi_B/dz at the check
-points, summed over the images inside the sphere B.  Two calls in a row must
-both agree (the second one finds the first one's data in the shared scratch).
-This file is collected last on purpose.
+Callers that cannot call cudaMalloc (engines that hand out all device memory
+from their own pool, plug-ins inside them, real-time loops that must not
+allocate) use hsma_pair_sum_static, whose scratch is a fixed array inside the
+library.  This file checks, through the C ABI, that it reproduces what the
+regular evaluation computes with the same kernel -- Phi_B and dPhi_B/dz at the
+check points, summed over the images inside the sphere B -- and the oracle's
+direct sum of the same images.  Two calls in a row must both agree (the
+second one finds the first one's data in the shared scratch), and torch's
+allocator must see no new memory.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -51,14 +52,22 @@ def test_static_pair_sum_matches_regular_path(P, prec):
     tgt = torch.from_numpy(np.ascontiguousarray(cpts)).to(dev)
     src = torch.from_numpy(np.ascontiguousarray(np.column_stack([ipos, iq]))).to(dev)
     stream = torch.cuda.current_stream(dev)
+    # the oracle's direct sum over the same images at the same points
+    ophi, ograd = O.pair_field(cpts, ipos, iq)
+    outs = [torch.full((nc, 4), float("nan"), dtype=torch.float64, device=dev) for _ in range(2)]
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated(dev)
     for call in range(2):
-        out = torch.full((nc, 4), float("nan"), dtype=torch.float64, device=dev)
-        P.hsma_pair_sum_static(tgt, src, out, prec, stream.cuda_stream)
-        stream.synchronize()
-        o = out.cpu().numpy()
+        P.hsma_pair_sum_static(tgt, src, outs[call], prec, stream.cuda_stream)
+    stream.synchronize()
+    assert torch.cuda.memory_allocated(dev) == before
+    for call in range(2):
+        o = outs[call].cpu().numpy()
         assert np.all(np.isfinite(o)), call
         assert np.abs(o[:, 0] - cphi).max() <= TOL[prec] * np.abs(cphi).max(), call
         assert np.abs(o[:, 3] - cdz).max() <= TOL[prec] * np.abs(cdz).max(), call
+        assert np.abs(o[:, 0] - ophi).max() <= TOL[prec] * np.abs(ophi).max(), call
+        assert np.abs(o[:, 1:] - ograd).max() <= TOL[prec] * np.abs(ograd).max(), call
 
 
 def test_static_pair_sum_rejects_oversize(P):
@@ -73,3 +82,19 @@ def test_static_pair_sum_rejects_oversize(P):
     with pytest.raises(P.HSMAError) as e:
         P.hsma_pair_sum_static(t, s, o, 0)
     assert e.value.code == -1
+
+
+def test_static_pair_sum_rejects_host_memory(P):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    t = torch.zeros((8, 3), dtype=torch.float64, device=dev)
+    s = torch.zeros((8, 4), dtype=torch.float64, device=dev)
+    o = torch.zeros((8, 4), dtype=torch.float64, device=dev)
+    with pytest.raises(ValueError):
+        P.hsma_pair_sum_static(t.cpu(), s, o, 1)
+    # through the C entry point itself: a host pointer is refused before any launch
+    import ctypes
+    h = np.zeros((8, 4))
+    rc = P.lib().hsma_pair_sum_static(ctypes.c_void_p(t.data_ptr()), 8, ctypes.c_void_p(h.ctypes.data), 8,
+                                      ctypes.c_void_p(o.data_ptr()), 1, None)
+    assert rc == -1
