@@ -205,7 +205,7 @@ def oracle_sample(c, x, q, n_targets, seed=99, n_check=None, st=None, threads=No
                         t_targets=t3 - t2, t_wall=t3 - t1, Ns=len(iq), threads=threads)
 
 
-def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None, precision=1):
+def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=None, precision=1, **server_opts):
     """Served workload: independent HSMA3D requests, Poisson arrivals.
 
     Requests: neutral +-1 electrolytes at density 0.1, N log-uniform in
@@ -248,6 +248,8 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     arrivals = workloads.poisson_arrivals(n_req, rate, seed=seed)
 
     server = P.hsma_server_create(slots, budget, precision)
+    for k, v in server_opts.items():
+        P.hsma_set_option(server, k, v)
     for p in (6, 8, 10):                       # build the three unit geometries, untimed
         c, x, q = next(r for r in reqs if r[0].p == p)
         t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
@@ -281,6 +283,8 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
 
     # served capacity: the same requests all submitted at once (saturated queue)
     server = P.hsma_server_create(slots, budget, precision)
+    for k, v in server_opts.items():
+        P.hsma_set_option(server, k, v)
     for p in (6, 8, 10):                       # unit geometries, untimed
         c, x, q = next(r for r in reqs if r[0].p == p)
         t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
@@ -291,12 +295,14 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     # the second is timed; results are collected in submission order, and
     # each poll also advances the server
     for timed in (False, True):
+        g0 = P.hsma_get_info(server, "gpu_ms")
         t_sat = time.perf_counter()
         sat_tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
         for i in range(n_req):
             while P.hsma_poll(server, sat_tickets[i], reqs[i][0].N, out=fbuf[i]) is None:
                 pass
         sat_span = time.perf_counter() - t_sat
+        sat_gpu_s = (P.hsma_get_info(server, "gpu_ms") - g0) / 1e3
     P.hsma_destroy(server)
     de = [abs(out[i][0] - r64[i][1]) / abs(r64[i][1]) for i in sample]
     # the same error against the energy scale 1/2 sum |q_i Phi_i| (|E| itself can
@@ -313,12 +319,13 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     return {"workload": f"{n_req} requests, N log-uniform [1e3, 5e4], p in {{6,8,10}}, M = 4p^2+400, "
                         f"rho = 0.1, Poisson arrivals at {rate:.1f}/s (0.8 x the one-at-a-time capacity "
                         f"at precision {precision})",
-            "precision": precision, "slots": slots, "budget_bytes": budget,
+            "precision": precision, "slots": slots, "budget_bytes": budget, "server_options": server_opts,
             "evals_per_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_N": float(np.mean([c.N for c, _, _ in reqs])),
             "one_at_a_time_fp64_evals_per_s": 1.0 / t64, "one_at_a_time_evals_per_s": 1.0 / t32,
             "served_vs_fp64": (n_req / span) * t64,
             "saturated_evals_per_s": n_req / sat_span,
+            "saturated_batch_device_s": sat_gpu_s, "saturated_wall_s": sat_span,
             "saturated_vs_one_at_a_time": (n_req / sat_span) * t32,
             "saturated_vs_fp64": (n_req / sat_span) * t64,
             "sample": f"{n_sample} requests stratified by N, timed one at a time",
@@ -328,7 +335,7 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
             "max_rel_force_rms_vs_fp64": float(max(df))}
 
 
-def other_cases(P, torch, dev, stream):
+def other_cases(P, torch, dev, stream, peak_instr):
     """Evaluations/s of the other workload shapes (inputs resident in HBM),
     FP32 and FP64 paths, with the FP32 energy error against the FP64 path."""
     out = {}
@@ -387,6 +394,20 @@ def other_cases(P, torch, dev, stream):
             b.record(stream)
             torch.cuda.synchronize()
             rec["tree_fp32_evals_per_s"] = 1e3 * max(3, n32) / a.elapsed_time(b)
+            # the tree's own near stage, timed per phase, and its roofline
+            ht = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=1, near_tree=1,
+                        timing=1, dtn_grid=c.dtn_grid)
+            P.hsma_set_stream(ht.h, stream.cuda_stream)
+            et = np.zeros(1)
+            f2 = torch.empty_like(fd)
+            tn = []
+            for _ in range(4):
+                P.hsma_eval_into(ht.h, xd, qd, c.N, et, f2)
+                torch.cuda.synchronize()
+                tn.append(P.hsma_get_info(ht.h, "t_near_ms"))
+            rec["tree_roofline"] = tree_roofline(P, ht, xd, qd, c.N, et, f2, float(np.median(tn[1:])), 10,
+                                                 peak_instr)
+            ht.close()
             rec["tree_levels"] = int(P.hsma_get_info(h.h, "tree_levels"))
             rec["tree_direct_leaf"] = int(P.hsma_get_info(h.h, "tree_direct_leaf"))
             rec["tree_vs_dense_rel_energy"] = abs(float(e[0]) - energies[1]) / abs(energies[1])
@@ -737,6 +758,34 @@ def pair_roofline(P, h, c, pairs_near, near_ms, peak_instr, mhz_src, sms, lib_to
     return roof, plan
 
 
+M2P_OPS_PER_TERM = 17     # FP32 operations per (n, m >= 0) term of a multipole evaluation (M2P)
+
+
+def tree_roofline(P, h, xd, qd, N, e, f, near_ms, order, peak_instr):
+    """FP32 issue-rate roofline of the tree evaluation of the near field and
+    check points: one extra evaluation with the counting kernel gives the
+    multipole evaluations (M2P) and FP32 direct pairs it performs; the
+    algorithmic work is M2P x (P+1)(P+2)/2 terms x 17 + pairs x 13 FP32
+    operations, over the near stage's CUDA-event time of the timed runs."""
+    P.hsma_set_option(h.h, "tree_count", 1)
+    P.hsma_eval_into(h.h, xd, qd, N, e, f)
+    import torch
+    torch.cuda.synchronize()
+    m2p = P.hsma_get_info(h.h, "tree_m2p")
+    direct = P.hsma_get_info(h.h, "tree_direct_pairs")
+    P.hsma_set_option(h.h, "tree_count", 0)
+    terms = (order + 1) * (order + 2) // 2
+    ops = m2p * terms * M2P_OPS_PER_TERM + direct * FP32_INSTR_PER_PAIR
+    achieved = ops / (near_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": f"k_tree_eval<{order}> (near field + check points, with its binning "
+                                      f"and multipole kernels)",
+            "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s", "frac": achieved / peak_instr,
+            "traffic": None, "m2p_per_eval": m2p, "direct_pairs_per_eval": direct,
+            "algorithmic": f"M2P x {terms} terms x {M2P_OPS_PER_TERM} + direct pairs x {FP32_INSTR_PER_PAIR} "
+                           f"FP32 operations = {ops:.4g} per evaluation",
+            "near_ms": near_ms}
+
+
 def timed_evals(P, torch, stream, h, xd, qd, N, e, f, n):
     """Mean device time (ms) of n evaluations on the stream, inputs resident."""
     P.hsma_eval_into(h.h, xd, qd, N, e, f)
@@ -1019,10 +1068,8 @@ def main():
     roof, plan = pair_roofline(P, h, c, pairs_near, float(np.mean(near_ms)), peak_instr, mhz_txt, sms,
                                lib_total_ms=float(np.mean(total_lib_ms)))
     if args.near_tree:
-        # the tree does not sum the dense pairs: no pair-count roofline
-        roof = {"bound": "alu", "kernel": "k_tree_eval<10> (near field + check points)", "achieved": None,
-                "peak": peak_instr, "unit": "T FP32-pipe instr/s", "frac": None, "traffic": None,
-                "near_ms": float(np.mean(near_ms)), "lib_total_ms": float(np.mean(total_lib_ms))}
+        roof = tree_roofline(P, h, xd, qd, N, ebuf, fd, float(np.mean(near_ms)), 10, peak_instr)
+        roof["lib_total_ms"] = float(np.mean(total_lib_ms))
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -1082,7 +1129,7 @@ def main():
                 option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), n=10, near_tree=1),
                 option_variant(P, torch, stream, c2, xd2, qd2, fd2, float(e0[0]), n=10, near_tree=1, far_field=1)]
             h2b.close()
-        line["other_cases"] = other_cases(P, torch, dev, stream)
+        line["other_cases"] = other_cases(P, torch, dev, stream, peak_instr)
         line["paper_like"] = paper_like(P, torch, dev, stream)
     if not args.no_serve:
         # last, so that the end of the line (what a log tail keeps) shows them

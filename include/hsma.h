@@ -121,6 +121,21 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       shared memory) for precision 2; turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
+ *   "tree_count"        1 = the tree evaluation runs its counting instance,
+ *                       which also counts the multipole evaluations (M2P)
+ *                       and FP32 direct pairs it performs (info keys
+ *                       "tree_m2p", "tree_direct_pairs"); slower, for the
+ *                       roofline only.  0 (default) = off.
+ *   "fused_reduce"      1 (default) = each pair launch sums its per-chunk
+ *                       partials itself: the CTA that finishes a target
+ *                       tile's last chunk adds that tile's partials in the
+ *                       fixed order of the separate reduction (bitwise the
+ *                       same result, one launch fewer, partials read back
+ *                       while still in L2); 0 = a separate reduction launch.
+ *   "dynamic_schedule"  1 (default) = pair-launch CTAs take (tile, chunk)
+ *                       items from a device counter; 0 = a static
+ *                       round-robin.  Either way each item writes its own
+ *                       partial, so results are the same.
  *   "sphere_mask"       1 (default) = the near set is the images inside the
  *                       sphere B (Sec. 2.2, first step); 0 = every image of
  *                       the enumerated cells (3D: all 27 at lambda <= sqrt 3),
@@ -181,10 +196,18 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       and its gradient, per particle (cost N (p+1)^2 instead
  *                       of N M).  The two agree to the surface quadrature's
  *                       error; the series skips that quadrature.
- * On a server handle (hsma_server_create) the only key is
+ * On a server handle (hsma_server_create) the keys are
  *   "inject_fail_ticket" fault injection for tests: the request with this
  *                       ticket fails with HSMA_ERR_CUDA when it is admitted,
  *                       without touching the GPU; 0 = off.
+ *   "ragged_variant"    pair-kernel code of the ragged launches: 12 (default,
+ *                       2 targets per thread, 512-target tiles) or 24 (4
+ *                       targets, sums in shared memory, 1024-target tiles)
+ *                       at precision 1; 32 (default) or 44 at precision 2.
+ *                       Only while the server holds no request.
+ *   "ragged_dynamic"    1 (default) = the ragged launches' CTAs take items
+ *                       from a device counter; 0 = static round-robin.
+ *                       Results are the same either way.
  * Errors: HSMA_ERR_ARG (unknown key or value out of range).
  */
 int hsma_set_option(hsma_t h, const char* key, double value);
@@ -231,7 +254,13 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * 256-byte guard band behind their end overwritten; every buffer is
  * allocated with such a band holding a fixed pattern, compared when the
  * buffer is freed and, for live buffers, when this key is read; waits for
- * the device first).
+ * the device first), "fused_reduce", "dynamic_schedule" (the options),
+ * "tree_m2p", "tree_direct_pairs" (the tree evaluation's work at the last
+ * evaluation with option tree_count = 1).
+ * On a server handle (hsma_server_create) the keys are "batches" (batches
+ * enqueued so far), "inflight_at_last_batch" (earlier batches still on the
+ * GPU when the last one was enqueued), "queued" (requests waiting for a
+ * slot) and "gpu_ms" (the summed device-time spans of the retired batches).
  * Errors: HSMA_ERR_ARG for an unknown key.
  */
 int hsma_get_info(hsma_t h, const char* key, double* value);

@@ -53,6 +53,10 @@ int guard_changed(void* p, size_t n) {
 
 int DevBuf::ensure(size_t bytes) {
   if (bytes <= n) return 0;
+  // a buffer that has to grow grows by half again at least, so that a run of
+  // slowly increasing sizes (serving slots) reallocates, and waits for the
+  // device, only a few times
+  if (n > 0) bytes = std::max(bytes, n + n / 2);
   release();
   if (bytes == 0) return 0;
   if (cudaMalloc(&p, bytes + kGuardBytes) != cudaSuccess) {
@@ -176,7 +180,7 @@ static int cuda_fail(hsma_ctx* h, cudaError_t e, const char* where) {
 hsma_ctx::~hsma_ctx() {
   for (DevBuf* b : {&d_shifts, &d_check, &d_P, &d_W, &d_ysurf, &d_v, &d_A, &d_cphi, &d_cdz, &d_Q,
                     &d_s32, &d_s64, &d_x, &d_q, &d_xc, &d_cnt, &d_blk, &d_blkq, &d_blkaq, &d_src32,
-                    &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad,
+                    &d_src64, &d_tgt32, &d_tgt64, &d_part, &d_fpart, &d_forces, &d_pot, &d_grad, &d_ticket, &d_twork,
                     &d_blke, &d_sc, &d_ioff, &d_self, &d_mask, &d_norm, &d_red1, &d_red2, &d_tkey_s,
                     &d_tcnt_s, &d_tstart_s, &d_tcur_s, &d_tord_s, &d_tkey_t, &d_tcnt_t, &d_tstart_t, &d_tcur_t,
                     &d_tord_t, &d_tsrc, &d_tpart, &d_tM, &d_tnorm, &d_tfac, &d_src32lo, &d_tgt32lo,
@@ -387,6 +391,13 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
   T.ioff = (const int*)h->d_ioff.p;
   T.icnt = (const int*)h->d_cnt.p;
   T.img_shift = (const int*)h->d_imgshift.p;
+  if (h->tree_count && h->d_twork.p) {   // allocated when the option is set (this may run under capture)
+    if (cudaMemsetAsync(h->d_twork.p, 0, 2 * sizeof(unsigned long long), h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, HSMA_ERR_CUDA, "tree work counters");
+    }
+    T.work = (unsigned long long*)h->d_twork.p;
+  }
   cudaError_t e = launch_tree(T, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "tree launch");
   return HSMA_OK;
@@ -438,6 +449,19 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
     bad = bad || h->d_src32.ensure(simg * 16) || h->d_tgt32.ensure(nt * 16) ||
           h->d_ioff.ensure(n * 4) || h->d_self.ensure(n * 32);
   if (prec == 2) bad = bad || h->d_src32lo.ensure(simg * 16) || h->d_tgt32lo.ensure(nt * 16);
+  // tile counters of the fused reduction, for the smallest tile any variant
+  // uses (256 targets), then the two launches' queue counters; all zero
+  // between launches
+  h->ticket_far = (int)(nt / 256 + 1);
+  h->ticket_queue = h->ticket_far + (int)(n / 256 + 1);
+  const size_t nticket = (size_t)h->ticket_queue + 4;
+  if (h->fused_reduce || h->dynamic_schedule) {
+    bad = bad || h->d_ticket.ensure(nticket * 4);
+    if (!bad && cudaMemsetAsync(h->d_ticket.p, 0, nticket * 4, h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      bad = true;
+    }
+  }
   if (bad) return fail(h, HSMA_ERR_NOMEM, "device buffers for N = " + std::to_string(N));
   if (h->near_tree) {
     if (prec != 1) return fail(h, HSMA_ERR_ARG, "near_tree needs precision 1 (FP32 pair arithmetic)");
@@ -522,6 +546,11 @@ PairArgs near_args(hsma_ctx* h, int64_t N) {
   p1.icnt = prec ? (const int*)h->d_cnt.p : nullptr;
   p1.src_lo = prec == 2 ? (const float4*)h->d_src32lo.p : nullptr;
   p1.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;
+  if (h->fused_reduce) {
+    p1.red = (double*)h->d_red1.p;
+    p1.ticket = (int*)h->d_ticket.p;
+  }
+  if (h->dynamic_schedule) p1.queue = (int*)h->d_ticket.p + h->ticket_queue;
   return p1;
 }
 
@@ -532,7 +561,7 @@ int stage_fit(hsma_ctx* h, int64_t N) {
   // the near/check partials summed over chunks once; the fit and the
   // assembly read the single row set
   cudaError_t e = cudaSuccess;
-  if (!h->near_tree)   // the tree writes its single row set directly
+  if (!h->near_tree && !h->fused_reduce)   // the tree and the fused launch write one row set
     e = launch_reduce_chunks((const double*)h->d_part.p, h->chunks1, h->n_tgt1, h->n_tgt1,
                              (double*)h->d_red1.p, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
@@ -561,15 +590,23 @@ PairArgs far_args(hsma_ctx* h, int64_t N) {
   p2.part = (double*)h->d_fpart.p;
   p2.ld = (int)N;
   p2.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;   // surface charges: no lo part
+  if (h->fused_reduce) {
+    p2.red = (double*)h->d_red2.p;
+    p2.ticket = (int*)h->d_ticket.p + h->ticket_far;
+  }
+  if (h->dynamic_schedule) p2.queue = (int*)h->d_ticket.p + h->ticket_queue + 2;
   return p2;
 }
 
 // Stage 5: potentials, forces, energy; scalars back to pinned host memory.
 int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   const int prec = h->precision;
-  const bool far_one = h->far_series || h->chunks2 == 1;
+  // the far field's single row set: the series writes it, the fused launch
+  // sums its chunks itself, one chunk needs no sum
+  const bool far_one = h->far_series || (!h->fused_reduce && h->chunks2 == 1);
+  const bool far_sum = !h->far_series && !h->fused_reduce && h->chunks2 > 1;
   cudaError_t e = cudaSuccess;
-  if (!far_one)
+  if (far_sum)
     e = launch_reduce_chunks((const double*)h->d_fpart.p, h->chunks2, (int)N, (int)N, (double*)h->d_red2.p,
                              h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
@@ -619,13 +656,14 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   if (rc) return rc;
   if (tm) cudaEventRecord(h->ev[5], s);
   // kernels this pipeline launches: prep 3; near 1 and its chunk reduction
-  // 1, or the tree's 9 binning kernels, 2 per multipole level (2..L, or
+  // 1 (none when the launch sums its own chunks), or the tree's 9 binning kernels, 2 per multipole level (2..L, or
   // 2..L-1 with a direct leaf level), task count and scan, evaluation and
   // part reduction; fit 3; far 1; far reduction 1 (not with one far chunk);
   // assembly 2
-  const bool far_one = h->far_series || h->chunks2 == 1;
+  const bool far_sum = !h->far_series && !h->fused_reduce && h->chunks2 > 1;
   const int m_levels = h->near_tree ? std::max(0, h->tree_L - 1 - h->tree_args.direct_leaf) : 0;
-  h->kernels_per_eval = 3 + (h->near_tree ? 13 + 2 * m_levels : 2) + 3 + 1 + (far_one ? 0 : 1) + 2;
+  h->kernels_per_eval =
+      3 + (h->near_tree ? 13 + 2 * m_levels : (h->fused_reduce ? 1 : 2)) + 3 + 1 + (far_sum ? 1 : 0) + 2;
   return HSMA_OK;
 }
 
@@ -642,6 +680,12 @@ int finish_eval(hsma_ctx* h, double* energy) {
       }
       h->times[i] = t;
     }
+  }
+  if (h->tree_count && h->near_tree && h->d_twork.p) {
+    unsigned long long w[2] = {0, 0};
+    if (cudaMemcpy(w, h->d_twork.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) cudaGetLastError();
+    h->tree_work[0] = (double)w[0];
+    h->tree_work[1] = (double)w[1];
   }
   if (r.flags & FLAG_OUT_OF_SLAB) return fail(h, HSMA_ERR_OUT_OF_SLAB, "some z outside (0, Lz)");
   if (r.flags & FLAG_NOT_NEUTRAL) return fail(h, HSMA_ERR_NOT_NEUTRAL, "system not neutral");
@@ -712,7 +756,7 @@ static int tune_near(hsma_ctx* h, int64_t N) {
     // chunks fill the GPU at small N but cost partial traffic
     cudaEventRecord(h->ev[0], s);
     cudaError_t e = launch_pair(prec, prec ? c.tpt : 1, a, grid, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !h->fused_reduce)
       e = launch_reduce_chunks(a.part, a.n_chunks, a.ld, h->n_tgt1, (double*)h->d_red1.p, s);
     cudaEventRecord(h->ev[1], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(h->ev[1]);
@@ -911,6 +955,19 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "graphs") {
     h->use_graphs = (v != 0);
     drop_graph(h);
+  } else if (k == "tree_count") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "tree_count must be 0 or 1");
+    if (v == 1 && h->d_twork.ensure(2 * sizeof(unsigned long long)))
+      return fail(h, HSMA_ERR_NOMEM, "tree work counters");
+    h->tree_count = (int)v;
+    drop_graph(h);
+  } else if (k == "fused_reduce" || k == "dynamic_schedule") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, k + " must be 0 or 1");
+    (k == "fused_reduce" ? h->fused_reduce : h->dynamic_schedule) = (int)v;
+    h->tuned_N = -1;
+    h->tuned_chunks = 0;
+    h->plan_N = -1;
+    drop_graph(h);
   } else if (k == "autotune") {
     h->autotune = (v != 0);
     h->tuned_N = -1;
@@ -963,6 +1020,10 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N, double* 
 int hsma_get_info(hsma_t h, const char* key, double* value) {
   if (!h || !key || !value) return HSMA_ERR_ARG;
   const std::string k(key);
+  if (h->is_server) {
+    if (server_get_info(h, k, value) != HSMA_OK) return fail(h, HSMA_ERR_ARG, "unknown server info key " + k);
+    return HSMA_OK;
+  }
   if (!h->is_server && (k == "Rc" || k == "Rs" || k == "n_shifts" || k == "n_check" || k == "rank")) {
     int rc = ensure_geometry(h);
     if (rc) return rc;
@@ -987,6 +1048,10 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
   else if (k == "tree_direct_leaf") *value = h->near_tree ? h->tree_args.direct_leaf : 0;
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
+  else if (k == "tree_m2p") *value = h->tree_work[0];
+  else if (k == "tree_direct_pairs") *value = h->tree_work[1];
+  else if (k == "fused_reduce") *value = h->fused_reduce;
+  else if (k == "dynamic_schedule") *value = h->dynamic_schedule;
   else if (k == "guard_violations") *value = (double)guard_violations();
   else if (k == "grid") *value = h->grid1;
   else if (k == "slots") *value = h->slots;

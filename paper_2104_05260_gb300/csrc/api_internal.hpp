@@ -92,6 +92,18 @@ struct hsma_ctx {
   int64_t tuned_N = -1;
   int tuned_chunks = 0;
   int part_chunks_min = 0;   // d_part holds at least this many chunks
+  // pair launches: chunk partials summed inside the launch by the last CTA of
+  // each tile (fused_reduce), items taken from a counter (dynamic_schedule)
+  int fused_reduce = 1;
+  int dynamic_schedule = 1;
+  // tree evaluation work counts (option tree_count): M2P evaluations and FP32
+  // direct pairs of the last evaluation
+  int tree_count = 0;
+  hsma::DevBuf d_twork;
+  double tree_work[2] = {0, 0};
+  hsma::DevBuf d_ticket;     // per-tile counters of both launches, then two queues
+  int ticket_far = 0;        // offset of the far launch's counters in d_ticket
+  int ticket_queue = 0;      // offset of the two queue pairs in d_ticket
   ~hsma_ctx();
 };
 
@@ -109,3 +121,4 @@ int mask_words(const hsma::Geometry& g);
 int finish_eval(hsma_ctx* h, double* energy);
 void server_shutdown(hsma_ctx* h);
 int server_set_option(hsma_ctx* h, const std::string& key, double v);
+int server_get_info(hsma_ctx* h, const std::string& key, double* v);

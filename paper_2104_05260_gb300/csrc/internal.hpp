@@ -72,6 +72,17 @@ struct PairArgs {
   // (hi_s - hi_t) + (lo_s - lo_t)
   const float4* src_lo = nullptr;
   const float4* tgt_lo = nullptr;
+  // Fused chunk reduction (red != NULL): items are numbered tile-major, and
+  // the CTA that completes the last chunk of a target tile sums that tile's
+  // partials over the chunks, in the fixed order of k_reduce_chunks, into
+  // red[c*ld + t].  ticket holds one counter per tile, zero between launches
+  // (the reducing CTA sets it back).
+  double* red = nullptr;
+  int* ticket = nullptr;
+  // Dynamic schedule (queue != NULL): CTAs take items from the counter
+  // queue[0]; queue[1] counts CTAs that found the queue empty, and the last
+  // of them sets both back to zero for the next launch.
+  int* queue = nullptr;
 };
 
 struct PairPlan {
@@ -88,10 +99,11 @@ cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream
 int pair_slots(int precision, int tpt);   // resident CTAs on the whole GPU
 // One launch over several packed-FP32 pair sums (descs and start in device
 // memory; start has n_desc + 1 entries, start[n_desc] = total items).
-cudaError_t launch_pair_ragged(int precision, const PairArgs* descs, const int* start, int n_desc, int grid,
-                               cudaStream_t s);
-int pair_ragged_slots(int precision);
-int pair_ragged_variant(int precision);   // kernel code the ragged launch runs (plan tiles with it)
+cudaError_t launch_pair_ragged(int precision, int variant, const PairArgs* descs, const int* start, int n_desc,
+                               int grid, int* queue, cudaStream_t s);
+int pair_ragged_slots(int precision, int variant);
+int pair_ragged_variant(int precision);   // default kernel code of the ragged launch (plan tiles with it)
+bool pair_ragged_code_ok(int precision, int variant);
 // Far field as the fitted series itself (no surface charges): out[c*N + i],
 // c = phi, grad; norm[n*(p+1) + m] = c_n0 (m = 0), sqrt(2) c_nm (2m-1)!! (m > 0)
 // with c_nm the orthonormal harmonic normalisation; A as the fit writes it.
@@ -129,6 +141,10 @@ struct TreeLaunch {
   const int* ioff;       // n_ions: first section-1 image of each ion
   const int* icnt;       // n_ions: its number of section-1 images
   const int* img_shift;  // section-1 image (index - n_ions) -> shift index
+  // when not NULL, the evaluation runs its counting instance, which adds to
+  // work[0] the multipole evaluations (M2P) and to work[1] the FP32 direct
+  // pairs it sums (the algorithmic work behind the tree's roofline)
+  unsigned long long* work = nullptr;
 };
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
 size_t tree_eval_smem(int P);

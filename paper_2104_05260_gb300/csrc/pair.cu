@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "internal.hpp"
 
 namespace hsma {
@@ -47,17 +49,117 @@ __device__ __forceinline__ void own_range(const PairArgs& a, int t0, int tt, int
   *hi = a.ioff[tl] + a.icnt[tl];
 }
 
+// (tile, chunk) of a work item: tile-major with a fused reduction (a tile's
+// chunks run close together, so its partials are still in L2 when the last
+// one sums them), chunk-major otherwise.
+__device__ __forceinline__ void item_tile_chunk(const PairArgs& a, int item, int* tile, int* chunk) {
+  if (a.red) {
+    *tile = item / a.n_chunks;
+    *chunk = item - *tile * a.n_chunks;
+  } else {
+    *tile = item % a.n_tiles;
+    *chunk = item / a.n_tiles;
+  }
+}
+
+// After a CTA has written its (tile, chunk) partials: count the chunk in, and
+// if it was the tile's last, sum the tile's partials over the chunks into
+// red.  Per target and component the order is that of k_reduce_chunks: eight
+// running sums s_k over the chunks ch = k (mod 8) in increasing order, then
+// ((s0 + s4) + (s2 + s6)) + ((s1 + s5) + (s3 + s7)); so the result is bitwise
+// the same as the separate reduction, whichever CTA finishes last.  A warp
+// takes 4 targets at a time with 8 lanes each (lane = 8 * target + k); the
+// final sums use shuffles within each group of 8.  The partials of other
+// CTAs are read through L2 (ld.cg).  Called by every thread of the CTA.
+__device__ void fused_reduce(const PairArgs& a, int tile, int tile_targets) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket + tile, 1) == a.n_chunks - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int t0 = tile * tile_targets;
+  const int t1 = min(a.n_tgt, t0 + tile_targets);
+  const size_t ld = (size_t)a.ld;
+  const int lane = threadIdx.x & 31, k = lane & 7;
+  const int first = 4 * (threadIdx.x >> 5) + (lane >> 3);    // target slot of this lane's group
+  const int groups = 4 * (blockDim.x >> 5);
+  for (int tb = t0; tb < t1; tb += groups) {
+    const int t = tb + first;
+    const bool live = t < t1;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    if (live) {
+      const double* p = a.part + t;
+      int ch = k;
+      for (; ch + 24 < a.n_chunks; ch += 32) {   // four chunks per step, loads first
+        double v[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v[u][c] = __ldcg(p + ((size_t)(ch + 8 * u) * 4 + c) * ld);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) s[c] += v[u][c];
+      }
+      for (; ch < a.n_chunks; ch += 8)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[c] += __ldcg(p + ((size_t)ch * 4 + c) * ld);
+    }
+    // s_k += s_{k+4}; s_k += s_{k+2}; s_0 += s_1 (as the separate reduction)
+#pragma unroll
+    for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double o = __shfl_down_sync(0xffffffffu, s[c], w, 8);
+        if (k < w) s[c] += o;
+      }
+    if (live && k == 0)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a.red[(size_t)c * ld + t] = s[c];
+  }
+  if (threadIdx.x == 0) a.ticket[tile] = 0;
+}
+
+// The item loop of the pair kernels: a static round-robin schedule, or, with
+// a.queue, items taken from a counter (the last CTA to find it empty resets
+// it).  body(item) must be called by every thread of the CTA.
+template <class Body>
+__device__ __forceinline__ void for_each_item(const PairArgs& a, Body&& body) {
+  const int items = a.n_tiles * a.n_chunks;
+  if (!a.queue) {
+    for (int item = blockIdx.x; item < items; item += gridDim.x) body(item);
+    return;
+  }
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= items) break;
+    body(item);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.queue + 1, 1) == (int)gridDim.x - 1) {
+      a.queue[0] = 0;
+      a.queue[1] = 0;
+    }
+  }
+}
+
 template <int TPT>
-__global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
-  __shared__ float4 sh[kTile32];
+__device__ __forceinline__ void pair_item_f32(const PairArgs& a, int item, float4* sh) {
   const float4* __restrict__ tgt = (const float4*)a.tgt;
   const float4* __restrict__ src = (const float4*)a.src;
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  {
+    int tile, chunk;
+    item_tile_chunk(a, item, &tile, &chunk);
     const int t0 = tile * kPairThreads * TPT;
     float tx[TPT], ty[TPT], tz[TPT];
     float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
@@ -152,7 +254,14 @@ __global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
         o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
       }
     }
+    if (a.red) fused_reduce(a, tile, kPairThreads * TPT);
   }
+}
+
+template <int TPT>
+__global__ void __launch_bounds__(kPairThreads) k_pair_f32(PairArgs a) {
+  __shared__ float4 sh[kTile32];
+  for_each_item(a, [&](int item) { pair_item_f32<TPT>(a, item, sh); });
 }
 
 // Packed FP32x2 variant: the same per-pair arithmetic on two targets at once
@@ -169,7 +278,8 @@ __device__ __forceinline__ void pair_item_f32x2(const PairArgs& a, int item, flo
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
   {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+    int tile, chunk;
+    item_tile_chunk(a, item, &tile, &chunk);
     const int t0 = tile * kPairThreads * TPT;
     // pair k holds targets t0 + tid + (2k)*256 and t0 + tid + (2k+1)*256, negated
     float2 nx[NP], ny[NP], nz[NP];
@@ -287,6 +397,7 @@ __device__ __forceinline__ void pair_item_f32x2(const PairArgs& a, int item, flo
         o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
       }
     }
+    if (a.red) fused_reduce(a, tile, kPairThreads * TPT);
   }
 }
 
@@ -311,7 +422,8 @@ __device__ __forceinline__ void pair_item_f32x2s(const PairArgs& a, int item, fl
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  int tile, chunk;
+  item_tile_chunk(a, item, &tile, &chunk);
   const int t0 = tile * kPairThreads * TPT;
   float2 nx[NP], ny[NP], nz[NP];
 #pragma unroll
@@ -424,6 +536,7 @@ __device__ __forceinline__ void pair_item_f32x2s(const PairArgs& a, int item, fl
       }
     }
   }
+  if (a.red) fused_reduce(a, tile, kPairThreads * TPT);
 }
 
 // Exact-difference variant (precision 2): each coordinate is carried as an
@@ -440,7 +553,8 @@ __device__ __forceinline__ void pair_item_f32x2x(const PairArgs& a, int item, fl
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  int tile, chunk;
+  item_tile_chunk(a, item, &tile, &chunk);
   const int t0 = tile * kPairThreads * TPT;
   float2 nx[NP], ny[NP], nz[NP], mx[NP], my[NP], mz[NP];   // -hi, -lo of the targets
   float hp[TPT], lp[TPT], hx[TPT], lx[TPT], hy[TPT], ly[TPT], hz[TPT], lz[TPT];
@@ -567,13 +681,13 @@ __device__ __forceinline__ void pair_item_f32x2x(const PairArgs& a, int item, fl
       o[3 * (size_t)a.ld] = (double)hz[k] + (double)lz[k];
     }
   }
+  if (a.red) fused_reduce(a, tile, kPairThreads * TPT);
 }
 
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads) k_pair_f32x2x(PairArgs a) {
   __shared__ float4 sh[4 * kTile32];
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2x<NP>(a, item, sh);
+  for_each_item(a, [&](int item) { pair_item_f32x2x<NP>(a, item, sh); });
 }
 
 // Exact differences (as in pair_item_f32x2x) with the compensated sums in
@@ -586,7 +700,8 @@ __device__ __forceinline__ void pair_item_f32x2xs(const PairArgs& a, int item, f
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile32 - 1) / kTile32 * kTile32;
-  const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
+  int tile, chunk;
+  item_tile_chunk(a, item, &tile, &chunk);
   const int t0 = tile * kPairThreads * TPT;
   float2 nx[NP], ny[NP], nz[NP], mx[NP], my[NP], mz[NP];   // -hi, -lo of the targets
 #pragma unroll
@@ -709,129 +824,173 @@ __device__ __forceinline__ void pair_item_f32x2xs(const PairArgs& a, int item, f
       }
     }
   }
+  if (a.red) fused_reduce(a, tile, kPairThreads * TPT);
 }
 
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2xs(PairArgs a) {
   __shared__ float4 sh[4 * kTile32];
   extern __shared__ float acc[];   // 8 * 2NP * kPairThreads floats
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2xs<NP>(a, item, sh, acc);
+  for_each_item(a, [&](int item) { pair_item_f32x2xs<NP>(a, item, sh, acc); });
 }
 
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 3) k_pair_f32x2s(PairArgs a) {
   __shared__ float4 sh[2 * kTile32];
   extern __shared__ float acc[];   // 8 * 2NP * kPairThreads floats
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2s<NP>(a, item, sh, acc);
+  for_each_item(a, [&](int item) { pair_item_f32x2s<NP>(a, item, sh, acc); });
 }
 
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads) k_pair_f32x2(PairArgs a) {
   __shared__ float4 sh[2 * kTile32];
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) pair_item_f32x2<NP>(a, item, sh);
+  for_each_item(a, [&](int item) { pair_item_f32x2<NP>(a, item, sh); });
 }
 
 // Ragged launch over several independent pair sums (requests of the serving
 // loop): item i belongs to the descriptor d with start[d] <= i < start[d+1].
 // Each item writes only its own descriptor's partials, so every request's
-// result is the same whatever else shares the launch.
-// Ragged launches run the packed kernel with 2 targets per thread (code 12):
-// its 512-target tiles give small requests more items than the 4-target
-// variants, which keeps served latency down.  Descriptors must be planned
-// with that tile size.
-__global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged(const PairArgs* __restrict__ descs,
-                                                                const int* __restrict__ start,
-                                                                int n_desc) {
-  __shared__ float4 sh[2 * kTile32];
+// result is the same whatever else shares the launch.  Items are taken in
+// a static round-robin, or from the counter queue[0] when queue is not null
+// (queue[1] counts CTAs that found it empty; the last resets both).
+// Variants, by the pair-kernel code of the items (descriptors must be planned
+// with that code's tile): 12 = packed, 2 targets per thread (512-target
+// tiles, more items for small requests); 24 = packed, 4 targets, sums in
+// shared memory (1024-target tiles, the single-instance kernel of large N);
+// 32 and 44 = the exact-difference versions of the two (precision 2).
+template <int V>
+__device__ __forceinline__ void ragged_item(const PairArgs& a, int item, float4* sh, float* acc) {
+  if (V == 12) pair_item_f32x2<1>(a, item, sh);
+  else if (V == 24) pair_item_f32x2s<2>(a, item, sh, acc);
+  else if (V == 32) pair_item_f32x2x<1>(a, item, sh);
+  else pair_item_f32x2xs<2>(a, item, sh, acc);
+}
+
+template <int V>
+__global__ void __launch_bounds__(kPairThreads, (V == 12 || V == 32) ? 4 : 3)
+    k_pair_ragged(const PairArgs* __restrict__ descs, const int* __restrict__ start, int n_desc,
+                  int* __restrict__ queue) {
+  __shared__ float4 sh[(V == 12 || V == 24) ? 2 * kTile32 : 4 * kTile32];
+  extern __shared__ float acc[];   // V = 24, 44: 8 * 4 * kPairThreads floats
   const int total = start[n_desc];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+  __shared__ int s_item;
+  int next = blockIdx.x;
+  for (;;) {
+    int item = next;
+    if (queue) {
+      __syncthreads();
+      if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+      __syncthreads();
+      item = s_item;
+    }
+    if (item >= total) break;
     int d = 0;
     while (d + 1 < n_desc && start[d + 1] <= item) ++d;
     const PairArgs a = descs[d];
-    pair_item_f32x2<1>(a, item - start[d], sh);
+    ragged_item<V>(a, item - start[d], sh, acc);
+    next += gridDim.x;
+  }
+  if (queue && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+    }
   }
 }
 
-// The same ragged launch for precision 2 (exact differences), 512-target tiles.
-__global__ void __launch_bounds__(kPairThreads, 4) k_pair_ragged_x(const PairArgs* __restrict__ descs,
-                                                                  const int* __restrict__ start,
-                                                                  int n_desc) {
-  __shared__ float4 sh[4 * kTile32];
-  const int total = start[n_desc];
-  for (int item = blockIdx.x; item < total; item += gridDim.x) {
-    int d = 0;
-    while (d + 1 < n_desc && start[d + 1] <= item) ++d;
-    const PairArgs a = descs[d];
-    pair_item_f32x2x<1>(a, item - start[d], sh);
-  }
+static bool ragged_code_ok(int precision, int v) {
+  return precision == 2 ? (v == 32 || v == 44) : (v == 12 || v == 24);
 }
 
 int pair_ragged_variant(int precision) { return precision == 2 ? 32 : 12; }
 
-cudaError_t launch_pair_ragged(int precision, const PairArgs* descs, const int* start, int n_desc, int grid,
-                               cudaStream_t s) {
+static const void* ragged_fn(int v) {
+  switch (v) {
+    case 24: return (const void*)k_pair_ragged<24>;
+    case 32: return (const void*)k_pair_ragged<32>;
+    case 44: return (const void*)k_pair_ragged<44>;
+    default: return (const void*)k_pair_ragged<12>;
+  }
+}
+
+static size_t ragged_smem(int v) { return (v == 24 || v == 44) ? kAccBytes2 : 0; }
+
+cudaError_t launch_pair_ragged(int precision, int variant, const PairArgs* descs, const int* start, int n_desc,
+                               int grid, int* queue, cudaStream_t s) {
   if (grid < 1) grid = 1;
-  if (precision == 2) k_pair_ragged_x<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
-  else k_pair_ragged<<<grid, kPairThreads, 0, s>>>(descs, start, n_desc);
+  if (!ragged_code_ok(precision, variant)) return cudaErrorInvalidValue;
+  const size_t smem = ragged_smem(variant);
+  if (smem) cudaFuncSetAttribute(ragged_fn(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  switch (variant) {
+    case 24: k_pair_ragged<24><<<grid, kPairThreads, smem, s>>>(descs, start, n_desc, queue); break;
+    case 32: k_pair_ragged<32><<<grid, kPairThreads, smem, s>>>(descs, start, n_desc, queue); break;
+    case 44: k_pair_ragged<44><<<grid, kPairThreads, smem, s>>>(descs, start, n_desc, queue); break;
+    default: k_pair_ragged<12><<<grid, kPairThreads, smem, s>>>(descs, start, n_desc, queue); break;
+  }
   return cudaGetLastError();
 }
 
-int pair_ragged_slots(int precision) {
+int pair_ragged_slots(int precision, int variant) {
+  if (!ragged_code_ok(precision, variant)) variant = pair_ragged_variant(precision);
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (precision == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged_x, kPairThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair_ragged, kPairThreads, 0);
+  const size_t smem = ragged_smem(variant);
+  if (smem) cudaFuncSetAttribute(ragged_fn(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ragged_fn(variant), kPairThreads, smem);
   return sms * (per < 1 ? 1 : per);
 }
 
-__global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
-  __shared__ double4_32a sh[kTile64];
+bool pair_ragged_code_ok(int precision, int variant) { return ragged_code_ok(precision, variant); }
+
+__device__ __forceinline__ void pair_item_f64(const PairArgs& a, int item, double4_32a* sh) {
   const double4_32a* __restrict__ tgt = (const double4_32a*)a.tgt;
   const double4_32a* __restrict__ src = (const double4_32a*)a.src;
   const int ns = a.sc ? a.sc->Ns : a.n_src;
   int per = (ns + a.n_chunks - 1) / a.n_chunks;
   per = (per + kTile64 - 1) / kTile64 * kTile64;
-  const int items = a.n_tiles * a.n_chunks;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int tile = item % a.n_tiles, chunk = item / a.n_tiles;
-    const int t = tile * kPairThreads + threadIdx.x;
-    const double4_32a tv = (t < a.n_tgt) ? tgt[t] : make_double4_32a(1e18, 1e18, 1e18, 0.0);
-    double p = 0, gx = 0, gy = 0, gz = 0;
-    const int s0 = chunk * per;
-    const int s1 = min(ns, s0 + per);
-    const int t0 = tile * kPairThreads;
-    for (int sb = s0; sb < s1; sb += kTile64) {
-      const int n = min(kTile64, s1 - sb);
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
-      __syncthreads();
-      const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads) && (t0 < sb + n);
-      for (int i = 0; i < n; ++i) {
-        const double4_32a s = sh[i];
-        const double dx = s.x - tv.x, dy = s.y - tv.y, dz = s.z - tv.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        double inv = rsqrt(r2);
-        if (diag && sb + i == t && t < a.n_diag) inv = 0.0;
-        const double qi = s.w * inv;
-        p += qi;
-        const double q3 = qi * inv * inv;
-        gx += q3 * dx;
-        gy += q3 * dy;
-        gz += q3 * dz;
-      }
-    }
-    if (t < a.n_tgt) {
-      double* o = a.part + (size_t)chunk * 4 * a.ld + t;
-      o[0] = p;
-      o[(size_t)a.ld] = gx;
-      o[2 * (size_t)a.ld] = gy;
-      o[3 * (size_t)a.ld] = gz;
+  int tile, chunk;
+  item_tile_chunk(a, item, &tile, &chunk);
+  const int t = tile * kPairThreads + threadIdx.x;
+  const double4_32a tv = (t < a.n_tgt) ? tgt[t] : make_double4_32a(1e18, 1e18, 1e18, 0.0);
+  double p = 0, gx = 0, gy = 0, gz = 0;
+  const int s0 = chunk * per;
+  const int s1 = min(ns, s0 + per);
+  const int t0 = tile * kPairThreads;
+  for (int sb = s0; sb < s1; sb += kTile64) {
+    const int n = min(kTile64, s1 - sb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kPairThreads) sh[i] = src[sb + i];
+    __syncthreads();
+    const bool diag = (sb < a.n_diag) && (t0 < a.n_diag) && (sb < t0 + kPairThreads) && (t0 < sb + n);
+    for (int i = 0; i < n; ++i) {
+      const double4_32a s = sh[i];
+      const double dx = s.x - tv.x, dy = s.y - tv.y, dz = s.z - tv.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      double inv = rsqrt(r2);
+      if (diag && sb + i == t && t < a.n_diag) inv = 0.0;
+      const double qi = s.w * inv;
+      p += qi;
+      const double q3 = qi * inv * inv;
+      gx += q3 * dx;
+      gy += q3 * dy;
+      gz += q3 * dz;
     }
   }
+  if (t < a.n_tgt) {
+    double* o = a.part + (size_t)chunk * 4 * a.ld + t;
+    o[0] = p;
+    o[(size_t)a.ld] = gx;
+    o[2 * (size_t)a.ld] = gy;
+    o[3 * (size_t)a.ld] = gz;
+  }
+  if (a.red) fused_reduce(a, tile, kPairThreads);
+}
+
+__global__ void __launch_bounds__(kPairThreads) k_pair_f64(PairArgs a) {
+  __shared__ double4_32a sh[kTile64];
+  for_each_item(a, [&](int item) { pair_item_f64(a, item, sh); });
 }
 
 // Kernel variants of the FP32 path, by code: 1, 2, 4 = scalar FP32 with that
@@ -859,7 +1018,25 @@ static const void* pair_fn(int precision, int tpt) {
   }
 }
 
+// The variants with compensated sums in dynamic shared memory use 48 KB or
+// more in all (static + dynamic): allow it, once per device.
+static void allow_pair_smem() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  const unsigned long long bit = 1ull << dev;
+  if (done.load() & bit) return;
+  cudaFuncSetAttribute((const void*)k_pair_f32x2s<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAccBytes2);
+  cudaFuncSetAttribute((const void*)k_pair_f32x2xs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAccBytes2);
+  cudaGetLastError();
+  done.fetch_or(bit);
+}
+
 int pair_slots(int precision, int tpt) {
+  allow_pair_smem();
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -871,6 +1048,7 @@ int pair_slots(int precision, int tpt) {
 
 cudaError_t launch_pair(int precision, int tpt, PairArgs a, int grid, cudaStream_t s) {
   if (grid < 1) grid = 1;
+  allow_pair_smem();
   if (precision == 0) k_pair_f64<<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 1) k_pair_f32<1><<<grid, kPairThreads, 0, s>>>(a);
   else if (tpt == 2) k_pair_f32<2><<<grid, kPairThreads, 0, s>>>(a);

@@ -64,6 +64,8 @@ struct BatchBuf {
   PairArgs* h_desc = nullptr;       // pinned: near descriptors, then far
   int* h_start = nullptr;           // pinned: near starts, then far starts
   DevBuf d_desc, d_start;
+  cudaEvent_t start = nullptr;      // recorded before the batch's first operation
+  cudaEvent_t phase_ev[2] = {nullptr, nullptr};   // after the near and the far ragged launch
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<Request*> reqs;
@@ -76,6 +78,47 @@ struct Slot {
   double box[3] = {0, 0, 0};
   double* h_shifts = nullptr;   // pinned staging of the shift table (no stream sync on upload)
   size_t h_shifts_n = 0;        // its capacity in doubles
+  cudaEvent_t ev = nullptr;     // joins the slot's stream into the server stream
+  cudaStream_t own_stream = nullptr;   // the slot context's own stream
+};
+
+// Pinned host buffers, reused: requests take their input and result buffers
+// from here and give them back when polled.  cudaMallocHost / cudaFreeHost
+// are slow and freeing synchronises with the device, which would drain the
+// batches in flight at every poll; the pool keeps both off the request path.
+// Buffers are kept per power-of-two size class until the server is destroyed.
+struct PinnedPool {
+  std::map<size_t, std::vector<void*>> free_;
+  std::vector<void*> all_;
+  static size_t size_class(size_t bytes) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  void* get(size_t bytes) {
+    const size_t c = size_class(bytes);
+    std::vector<void*>& v = free_[c];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    all_.push_back(p);
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    if (p) free_[size_class(bytes)].push_back(p);
+  }
+  void release() {
+    for (void* p : all_) cudaFreeHost(p);
+    all_.clear();
+    free_.clear();
+  }
 };
 
 struct Server {
@@ -93,14 +136,27 @@ struct Server {
   // host-side fault injection (tests): the request with this ticket fails as
   // if a CUDA call had failed while it was being bound to a slot
   uint64_t inject_fail_ticket = 0;
+  PinnedPool pinned;
+  // counters: batches enqueued, and how many earlier batches were still on
+  // the GPU when the last one was enqueued
+  uint64_t batches = 0;
+  int inflight_at_last = 0;
+  double gpu_ms = 0;   // summed span (first to last operation) of the retired batches
+  // the ragged pair launch: kernel code of its items (slots plan their tiles
+  // with it) and, when dynamic, a counter pair per launch (near, far)
+  int ragged_variant = 12;
+  int ragged_dynamic = 1;
+  int slot_streams = 1;   // each slot's small kernels on a stream of its own
+  DevBuf d_queue;
 };
 
-static void free_request(Request* r) {
-  if (r->hx) cudaFreeHost(r->hx);
-  if (r->hq) cudaFreeHost(r->hq);
-  if (r->hf) cudaFreeHost(r->hf);
+static void free_request(Server* s, Request* r) {
+  s->pinned.put(r->hx, (size_t)r->N * 24);
+  s->pinned.put(r->hq, (size_t)r->N * 8);
+  s->pinned.put(r->hf, (size_t)r->N * 24);
   delete r;
 }
+
 
 // Device bytes one request holds in its slot (an upper bound for admission):
 // inputs and per-ion arrays, images in B, targets, partial sums, outputs.
@@ -221,6 +277,8 @@ static void retire(Server* s) {
     if (!bb.busy) continue;
     cudaError_t q = cudaEventQuery(bb.done);
     if (q == cudaErrorNotReady) continue;
+    float ms = 0.f;
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms, bb.start, bb.done) == cudaSuccess) s->gpu_ms += ms;
     for (Request* r : bb.reqs) {
       Slot& sl = s->slots[r->slot];
       if (q != cudaSuccess) {
@@ -239,13 +297,43 @@ static void retire(Server* s) {
   }
 }
 
+// Enqueue one batch.  Each request's own small kernels (prep, fit,
+// assembly) and copies run on its slot's stream, so those of different
+// requests overlap on the GPU; the two ragged pair launches run on the server
+// stream.  Events join the streams: every slot waits for the batch start,
+// the server stream waits for every slot before each ragged launch, the slots
+// wait for that launch before their next stage, and the batch's done event
+// follows every slot's last copy.  With slot streams off (option
+// slot_streams = 0) everything runs on the server stream in this order.
 static int launch_batch(Server* s, BatchBuf& bb) {
   cudaStream_t st = s->stream;
   const int n = (int)bb.reqs.size();
+  if (cudaEventRecord(bb.start, st) != cudaSuccess) return HSMA_ERR_CUDA;
+  auto slot_of = [&](Request* r) -> Slot& { return s->slots[r->slot]; };
+  // the slot streams wait for ev (recorded on the server stream)
+  auto fan_out = [&](cudaEvent_t ev) -> bool {
+    if (!s->slot_streams) return true;
+    for (Request* r : bb.reqs)
+      if (cudaStreamWaitEvent(slot_of(r).ctx->stream, ev, 0) != cudaSuccess) return false;
+    return true;
+  };
+  // the server stream waits for every slot stream's work so far
+  auto fan_in = [&]() -> bool {
+    if (!s->slot_streams) return true;
+    for (Request* r : bb.reqs) {
+      Slot& sl = slot_of(r);
+      if (cudaEventRecord(sl.ev, sl.ctx->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(st, sl.ev, 0) != cudaSuccess)
+        return false;
+    }
+    return true;
+  };
+  if (!fan_out(bb.start)) return HSMA_ERR_CUDA;
   for (Request* r : bb.reqs) {
-    hsma_ctx* h = s->slots[r->slot].ctx;
-    cudaError_t e = cudaMemcpyAsync(h->d_x.p, r->hx, (size_t)r->N * 24, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q.p, r->hq, (size_t)r->N * 8, cudaMemcpyHostToDevice, st);
+    hsma_ctx* h = slot_of(r).ctx;
+    cudaError_t e = cudaMemcpyAsync(h->d_x.p, r->hx, (size_t)r->N * 24, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_q.p, r->hq, (size_t)r->N * 8, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return HSMA_ERR_CUDA;
     int rc = stage_prep(h, r->N);
     if (rc) return rc;
@@ -253,16 +341,17 @@ static int launch_batch(Server* s, BatchBuf& bb) {
   for (int phase = 0; phase < 2; ++phase) {
     if (phase == 1)
       for (Request* r : bb.reqs) {
-        int rc = stage_fit(s->slots[r->slot].ctx, r->N);
+        int rc = stage_fit(slot_of(r).ctx, r->N);
         if (rc) return rc;
       }
     if (s->precision >= 1) {
+      if (!fan_in()) return HSMA_ERR_CUDA;
       PairArgs* d = bb.h_desc + phase * (int)s->slots.size();
       int* start = bb.h_start + phase * ((int)s->slots.size() + 1);
       int items = 0;
       for (int k = 0; k < n; ++k) {
         Request* r = bb.reqs[k];
-        hsma_ctx* h = s->slots[r->slot].ctx;
+        hsma_ctx* h = slot_of(r).ctx;
         d[k] = phase == 0 ? near_args(h, r->N) : far_args(h, r->N);
         start[k] = items;
         items += d[k].n_tiles * d[k].n_chunks;
@@ -273,25 +362,34 @@ static int launch_batch(Server* s, BatchBuf& bb) {
       cudaError_t e = cudaMemcpyAsync(dd, d, sizeof(PairArgs) * n, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(ds, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)
-        e = launch_pair_ragged(s->precision, dd, ds, n, std::min(items, s->ragged_slots), st);
-      if (e != cudaSuccess) return HSMA_ERR_CUDA;
+        e = launch_pair_ragged(s->precision, s->ragged_variant, dd, ds, n, std::min(items, s->ragged_slots),
+                               s->ragged_dynamic ? (int*)s->d_queue.p + 2 * phase : nullptr, st);
+      if (e == cudaSuccess) e = cudaEventRecord(bb.phase_ev[phase], st);
+      if (e != cudaSuccess || !fan_out(bb.phase_ev[phase])) return HSMA_ERR_CUDA;
     } else {
+      // FP64: one launch per request, on its slot stream
       for (Request* r : bb.reqs) {
-        hsma_ctx* h = s->slots[r->slot].ctx;
-        cudaError_t e = phase == 0 ? launch_pair(0, 1, near_args(h, r->N), h->grid1, st)
-                                   : launch_pair(0, 1, far_args(h, r->N), h->grid2, st);
+        hsma_ctx* h = slot_of(r).ctx;
+        cudaError_t e = phase == 0 ? launch_pair(0, 1, near_args(h, r->N), h->grid1, h->stream)
+                                   : launch_pair(0, 1, far_args(h, r->N), h->grid2, h->stream);
         if (e != cudaSuccess) return HSMA_ERR_CUDA;
       }
     }
   }
   for (Request* r : bb.reqs) {
-    hsma_ctx* h = s->slots[r->slot].ctx;
+    hsma_ctx* h = slot_of(r).ctx;
     int rc = stage_assemble(h, r->N, (double*)h->d_forces.p, (double*)h->d_pot.p);
     if (rc) return rc;
-    if (cudaMemcpyAsync(r->hf, h->d_forces.p, (size_t)r->N * 24, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cudaMemcpyAsync(r->hf, h->d_forces.p, (size_t)r->N * 24, cudaMemcpyDeviceToHost, h->stream) !=
+        cudaSuccess)
       return HSMA_ERR_CUDA;
   }
+  if (!fan_in()) return HSMA_ERR_CUDA;
   if (cudaEventRecord(bb.done, st) != cudaSuccess) return HSMA_ERR_CUDA;
+  int inflight = 0;
+  for (const BatchBuf& b : s->bufs) inflight += b.busy ? 1 : 0;
+  s->inflight_at_last = inflight;
+  s->batches++;
   bb.busy = true;
   return HSMA_OK;
 }
@@ -331,7 +429,7 @@ static int step(Server* s) {
       int rc = launch_batch(s, *bb);
       if (rc != HSMA_OK) {
         // the batch could not be enqueued: fail its requests, free their slots
-        cudaStreamSynchronize(s->stream);
+        cudaDeviceSynchronize();
         cudaGetLastError();
         for (Request* r : bb->reqs) {
           r->status = rc;
@@ -352,10 +450,58 @@ static int step(Server* s) {
 
 using namespace hsma;
 
+int server_get_info(hsma_ctx* h, const std::string& key, double* v) {
+  if (!h->srv) return HSMA_ERR_ARG;
+  if (key == "batches") *v = (double)h->srv->batches;
+  else if (key == "inflight_at_last_batch") *v = h->srv->inflight_at_last;
+  else if (key == "queued") *v = (double)h->srv->queue.size();
+  else if (key == "gpu_ms") *v = h->srv->gpu_ms;
+  else if (key == "ragged_variant") *v = h->srv->ragged_variant;
+  else if (key == "ragged_dynamic") *v = h->srv->ragged_dynamic;
+  else if (key == "slot_streams") *v = h->srv->slot_streams;
+  else return HSMA_ERR_ARG;
+  return HSMA_OK;
+}
+
 int server_set_option(hsma_ctx* h, const std::string& key, double v) {
   if (!h->srv) return HSMA_ERR_ARG;
+  Server* s = h->srv;
   if (key == "inject_fail_ticket" && v >= 0) {
-    h->srv->inject_fail_ticket = (uint64_t)v;
+    s->inject_fail_ticket = (uint64_t)v;
+    return HSMA_OK;
+  }
+  if (key == "ragged_variant" || key == "ragged_dynamic" || key == "slot_streams") {
+    // only while no request is in the server (slots plan with the variant)
+    bool idle = s->queue.empty();
+    for (const Slot& sl : s->slots) idle = idle && !sl.req;
+    if (!idle) {
+      h->err = key + " can be changed only while the server holds no request";
+      return HSMA_ERR_ARG;
+    }
+    if (key == "ragged_dynamic" || key == "slot_streams") {
+      if (v != 0 && v != 1) {
+        h->err = key + " must be 0 or 1";
+        return HSMA_ERR_ARG;
+      }
+      if (key == "ragged_dynamic") {
+        s->ragged_dynamic = (int)v;
+        return HSMA_OK;
+      }
+      // every slot context works on its own stream, or on the server's
+      s->slot_streams = (int)v;
+      for (Slot& sl : s->slots) sl.ctx->stream = v ? sl.own_stream : s->stream;
+      return HSMA_OK;
+    }
+    if (s->precision == 0 || !pair_ragged_code_ok(s->precision, (int)v) || v != (int)v) {
+      h->err = "ragged_variant must be 12 or 24 (precision 1), 32 or 44 (precision 2)";
+      return HSMA_ERR_ARG;
+    }
+    s->ragged_variant = (int)v;
+    s->ragged_slots = pair_ragged_slots(s->precision, s->ragged_variant);
+    for (Slot& sl : s->slots) {
+      sl.ctx->tpt = s->ragged_variant;
+      sl.ctx->plan_N = -1;
+    }
     return HSMA_OK;
   }
   h->err = "unknown server option " + key;
@@ -367,8 +513,11 @@ void server_shutdown(hsma_ctx* h) {
   Server* s = h->srv;
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (Slot& sl : s->slots) {
+    if (sl.own_stream) cudaStreamSynchronize(sl.own_stream);
+    if (sl.ctx) sl.ctx->stream = sl.own_stream;   // the context destroys its own stream
     delete sl.ctx;
     if (sl.h_shifts) cudaFreeHost(sl.h_shifts);
+    if (sl.ev) cudaEventDestroy(sl.ev);
   }
   for (BatchBuf& bb : s->bufs) {
     if (bb.h_desc) cudaFreeHost(bb.h_desc);
@@ -376,6 +525,9 @@ void server_shutdown(hsma_ctx* h) {
     bb.d_desc.release();
     bb.d_start.release();
     if (bb.done) cudaEventDestroy(bb.done);
+    if (bb.start) cudaEventDestroy(bb.start);
+    for (cudaEvent_t& e : bb.phase_ev)
+      if (e) cudaEventDestroy(e);
   }
   for (auto& kv : s->geos) {
     kv.second->d_P.release();
@@ -383,7 +535,9 @@ void server_shutdown(hsma_ctx* h) {
     kv.second->d_Y.release();
     kv.second->d_C.release();
   }
-  for (auto& kv : s->all) free_request(kv.second);
+  for (auto& kv : s->all) free_request(s, kv.second);
+  s->pinned.release();
+  s->d_queue.release();
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
   h->srv = nullptr;
@@ -405,27 +559,33 @@ int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* ou
   s->budget = budget_bytes;
   int rc = HSMA_OK;
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) rc = HSMA_ERR_CUDA;
-  if (rc == HSMA_OK) s->ragged_slots = pair_ragged_slots(precision);
+  if (precision) s->ragged_variant = pair_ragged_variant(precision);
+  if (rc == HSMA_OK) s->ragged_slots = pair_ragged_slots(precision, s->ragged_variant);
+  if (rc == HSMA_OK && (s->d_queue.ensure(4 * sizeof(int)) ||
+                        cudaMemset(s->d_queue.p, 0, 4 * sizeof(int)) != cudaSuccess))
+    rc = HSMA_ERR_NOMEM;
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
     if (rc != HSMA_OK) break;
     sl.ctx = new hsma_ctx();
     sl.ctx->precision = precision;
     sl.ctx->autotune = 0;                      // a request's plan depends only on the request
-    if (precision) sl.ctx->tpt = pair_ragged_variant(precision);
-    rc = hsma_ctx_init(sl.ctx);
-    if (rc == HSMA_OK) {
-      cudaStreamDestroy(sl.ctx->stream);
-      sl.ctx->stream = s->stream;      // every slot works on the server's stream
-      sl.ctx->own_stream = false;
-    }
+    sl.ctx->fused_reduce = 0;                  // ragged launches leave the chunk sums to k_reduce_chunks
+    sl.ctx->dynamic_schedule = 0;
+    if (precision) sl.ctx->tpt = s->ragged_variant;
+    rc = hsma_ctx_init(sl.ctx);   // the slot's context owns a non-blocking stream
+    if (rc == HSMA_OK && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess)
+      rc = HSMA_ERR_CUDA;
+    if (rc == HSMA_OK) sl.own_stream = sl.ctx->stream;
   }
   for (BatchBuf& bb : s->bufs) {
     if (rc != HSMA_OK) break;
     if (cudaMallocHost((void**)&bb.h_desc, sizeof(PairArgs) * 2 * slots) != cudaSuccess ||
         cudaMallocHost((void**)&bb.h_start, sizeof(int) * 2 * (slots + 1)) != cudaSuccess ||
         bb.d_desc.ensure(sizeof(PairArgs) * 2 * slots) || bb.d_start.ensure(sizeof(int) * 2 * (slots + 1)) ||
-        cudaEventCreateWithFlags(&bb.done, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreate(&bb.done) != cudaSuccess || cudaEventCreate(&bb.start) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bb.phase_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bb.phase_ev[1], cudaEventDisableTiming) != cudaSuccess)
       rc = HSMA_ERR_NOMEM;
   }
   if (rc != HSMA_OK) {
@@ -467,18 +627,22 @@ int hsma_submit(hsma_t server, const double* x, const double* q, int64_t N, cons
     h->err = "request exceeds the memory budget";
     return HSMA_ERR_BUDGET;
   }
-  if (cudaMallocHost((void**)&r->hx, (size_t)N * 24) != cudaSuccess ||
-      cudaMallocHost((void**)&r->hq, (size_t)N * 8) != cudaSuccess ||
-      cudaMallocHost((void**)&r->hf, (size_t)N * 24) != cudaSuccess) {
-    cudaGetLastError();
-    free_request(r);
+  r->hx = (double*)s->pinned.get((size_t)N * 24);
+  r->hq = (double*)s->pinned.get((size_t)N * 8);
+  r->hf = (double*)s->pinned.get((size_t)N * 24);
+  if (!r->hx || !r->hq || !r->hf) {
+    free_request(s, r);
     h->err = "pinned host allocation failed";
     return HSMA_ERR_NOMEM;
   }
-  if (cudaMemcpy(r->hx, x, (size_t)N * 24, cudaMemcpyDefault) != cudaSuccess ||
-      cudaMemcpy(r->hq, q, (size_t)N * 8, cudaMemcpyDefault) != cudaSuccess) {
+  // host inputs are copied on the host; device inputs through the driver
+  if (!is_device_ptr(x) && !is_device_ptr(q)) {
+    std::memcpy(r->hx, x, (size_t)N * 24);
+    std::memcpy(r->hq, q, (size_t)N * 8);
+  } else if (cudaMemcpy(r->hx, x, (size_t)N * 24, cudaMemcpyDefault) != cudaSuccess ||
+             cudaMemcpy(r->hq, q, (size_t)N * 8, cudaMemcpyDefault) != cudaSuccess) {
     cudaGetLastError();
-    free_request(r);
+    free_request(s, r);
     h->err = "input copy failed";
     return HSMA_ERR_CUDA;
   }
@@ -488,7 +652,7 @@ int hsma_submit(hsma_t server, const double* x, const double* q, int64_t N, cons
     qa += std::fabs(r->hq[i]);
   }
   if (std::fabs(qs) > 1e-10 * qa) {
-    free_request(r);
+    free_request(s, r);
     h->err = "system not neutral";
     return HSMA_ERR_NOT_NEUTRAL;
   }
@@ -515,8 +679,9 @@ int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces) {
   if (st == HSMA_OK) {
     if (energy) *energy = r->energy;
     if (forces) {
-      cudaError_t e = cudaMemcpy(forces, r->hf, (size_t)r->N * 24, cudaMemcpyDefault);
-      if (e != cudaSuccess) {
+      if (!is_device_ptr(forces)) {
+        std::memcpy(forces, r->hf, (size_t)r->N * 24);
+      } else if (cudaMemcpy(forces, r->hf, (size_t)r->N * 24, cudaMemcpyDefault) != cudaSuccess) {
         cudaGetLastError();
         server->err = "result copy failed";
         return HSMA_ERR_CUDA;
@@ -526,7 +691,7 @@ int hsma_poll(hsma_t server, uint64_t ticket, double* energy, double* forces) {
     server->err = r->err;
   }
   s->all.erase(it);
-  free_request(r);
+  free_request(s, r);
   return st;
 }
 

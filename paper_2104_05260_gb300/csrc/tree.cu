@@ -427,7 +427,7 @@ struct OwnImages {
   const int* img_shift;
 };
 
-template <int P>
+template <int P, bool COUNT>
 __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
                                                                int n_ions, const int* __restrict__ tgt_start,
                                                                const int* __restrict__ tgt_order,
@@ -437,7 +437,8 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
                                                                const float* __restrict__ M,
                                                                const int* __restrict__ task_start, int n_cells,
                                                                int S, int* __restrict__ queue,
-                                                               double* __restrict__ out, int ld, OwnImages own) {
+                                                               double* __restrict__ out, int ld, OwnImages own,
+                                                               unsigned long long* __restrict__ work) {
   // Persistent warps, no block barriers: each warp takes the next item from
   // the queue, compacts each level's list itself and stages multipoles in its
   // own slice of shared memory.
@@ -457,6 +458,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
   int* slist = sid + (kTreeThreads - warp * 32) + warp * 216;                  // compacted list, 216 per warp
   const int nsideL = 1 << t.L;
   const int n_items = S * task_start[n_cells];
+  unsigned long long n_m2p = 0, n_dir = 0;   // counting instance only
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(queue, 1);
@@ -534,6 +536,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
             int ox, oy, oz;
             morton_decode(slist[b0 + c], l, &ox, &oy, &oz);
             if (l == t.L && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1) continue;
+            if (COUNT) ++n_m2p;
             const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
             const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
             const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
@@ -590,6 +593,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
             !ion || ((ti < lo || ti > hi) && (own_n == 0 || own0 + own_n <= lo || own0 > hi));
         if (__all_sync(0xffffffffu, clean)) {
           if (take) {
+            if (COUNT) n_dir += nb;
             const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y);
             const float2 npz = make_float2(-p.z, -p.z);
             for (int k = 0; k < nb; k += 2) {   // an odd tile ends on a padding slot
@@ -630,6 +634,7 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
               }
               continue;
             }
+            if (COUNT) ++n_dir;
             const float dx = tx[k] - p.x, dy = ty[k] - p.y, dz = tz[k] - p.z;
             const float r2 = dx * dx + dy * dy + dz * dz;
             const float ri = rsqrtf(r2);
@@ -653,6 +658,17 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
       o[(size_t)ld + ti] = gx;
       o[2 * (size_t)ld + ti] = gy;
       o[3 * (size_t)ld + ti] = gz;
+    }
+  }
+  if (COUNT) {
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+      n_m2p += __shfl_down_sync(0xffffffffu, n_m2p, w);
+      n_dir += __shfl_down_sync(0xffffffffu, n_dir, w);
+    }
+    if (lane == 0) {
+      atomicAdd(work, n_m2p);
+      atomicAdd(work + 1, n_dir);
     }
   }
 }
@@ -728,10 +744,17 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   const OwnImages own{T.sc, T.xc, T.q, T.shifts, T.ioff, T.icnt, T.img_shift};
   const size_t sm = tree_eval_smem(t.P);
   const int eval_grid = 5 * tree_sm_count();
-#define HSMA_TREE_EVAL(PP)                                                                                \
-  k_tree_eval<PP><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order,        \
-                                                      T.src_sorted, T.src_order, T.src_start, T.M, task_start, \
-                                                      n_cells, T.parts, queue, T.out_parts, T.ld, own)
+#define HSMA_TREE_EVAL(PP)                                                                                  \
+  if (T.work)                                                                                                \
+    k_tree_eval<PP, true><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order, \
+                                                              T.src_sorted, T.src_order, T.src_start, T.M,    \
+                                                              task_start, n_cells, T.parts, queue,            \
+                                                              T.out_parts, T.ld, own, T.work);                \
+  else                                                                                                       \
+    k_tree_eval<PP, false><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order, \
+                                                               T.src_sorted, T.src_order, T.src_start, T.M,    \
+                                                               task_start, n_cells, T.parts, queue,            \
+                                                               T.out_parts, T.ld, own, nullptr)
   switch (t.P) {
     case 4: HSMA_TREE_EVAL(4); break;
     case 6: HSMA_TREE_EVAL(6); break;

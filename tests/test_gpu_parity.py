@@ -443,3 +443,29 @@ def test_exact_difference_variants_agree(P):
             if ref is None:
                 ref = (E, F, pot)
             assert E == ref[0] and np.array_equal(F, ref[1]) and np.array_equal(pot, ref[2]), (tpt, graphs)
+
+
+@pytest.mark.parametrize("prec,tpt", [(0, 1), (1, 12), (1, 24), (1, 1), (2, 44)])
+def test_fused_reduction_and_dynamic_schedule_change_nothing(P, prec, tpt):
+    # the chunk partials summed inside the pair launch (in the fixed order of
+    # the separate reduction) and items taken from a counter instead of a
+    # static round-robin: bitwise the same results, on a ragged size with
+    # several target tiles, at several chunk counts
+    c = workloads.small_case(2050, dims=3, box=(12.7, 12.7, 12.7), p=6, M=800, valences=(3, -1), seed=7)
+    x, q = workloads.electrolyte(c)
+    for chunks in (1, 5, 13):
+        ref = None
+        for fused in (0, 1):
+            for dyn in (0, 1):
+                opt = dict(chunks=chunks, fused_reduce=fused, dynamic_schedule=dyn)
+                if prec:
+                    opt["targets_per_thread"] = tpt
+                h = P.HSMA(c.box, 3, c.p, c.M, precision=prec, **opt)
+                E, F, pot = h.eval(x, q, potential=True)
+                E2, F2, _ = h.eval(x, q)            # the counters were left at zero
+                assert h.info("fused_reduce") == fused and h.info("dynamic_schedule") == dyn
+                h.close()
+                assert E == E2 and np.array_equal(F, F2)
+                if ref is None:
+                    ref = (E, F, pot)
+                assert E == ref[0] and np.array_equal(F, ref[1]) and np.array_equal(pot, ref[2]), opt

@@ -169,3 +169,77 @@ def test_failed_request_does_not_disturb_the_others(P):
         E0, _, _ = h.eval(x, q)
         h.close()
         assert abs(results[i][0] - E0) <= 1e-6 * abs(E0)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_request_admitted_while_another_batch_runs(P, prec):
+    # continuous batching: B is submitted after A's batch has been enqueued and
+    # while it is still on the GPU; B joins a later batch, and its result is
+    # bitwise the one B gets alone
+    a = request(40000, 10, 21)
+    b = request(1500, 6, 22)
+    s1 = P.hsma_server_create(8, 8e9, prec)
+    Eb0, Fb0 = serve_all(P, s1, [b])[0]
+    P.hsma_destroy(s1)
+    s2 = P.hsma_server_create(8, 8e9, prec)
+    # the same two requests once, so that both shapes' geometry exists and
+    # the two slots they land in already hold buffers of their size (a
+    # growing buffer would wait for the device)
+    serve_all(P, s2, [a, b])
+    n0 = P.hsma_get_info(s2, "batches")
+    ta = P.hsma_submit(s2, a[1], a[2], a[0].box, a[0].p, a[0].M)
+    tb = P.hsma_submit(s2, b[1], b[2], b[0].box, b[0].p, b[0].M)
+    assert P.hsma_get_info(s2, "batches") == n0 + 2          # A's batch, then B's
+    assert P.hsma_get_info(s2, "inflight_at_last_batch") >= 1  # A's was still on the GPU
+    out = {}
+    for _ in range(200000):
+        for name, t, N in (("a", ta, a[0].N), ("b", tb, b[0].N)):
+            if name not in out:
+                r = P.hsma_poll(s2, t, N)
+                if r is not None:
+                    out[name] = r
+        if len(out) == 2:
+            break
+    P.hsma_destroy(s2)
+    Eb, Fb = out["b"]
+    assert Eb == Eb0 and np.array_equal(Fb, Fb0)
+
+
+@pytest.mark.parametrize("prec,variant", [(1, 12), (1, 24), (2, 32), (2, 44)])
+def test_ragged_variants_and_schedules(P, prec, variant):
+    # every ragged kernel variant, with items from a device counter or in a
+    # static round-robin: the same results (bitwise between the schedules and
+    # between alone and a mix), within the FP32 bounds of hsma_eval
+    reqs = [request(N, p, s) for N, p, s in ((2500, 8, 31), (900, 6, 32), (12000, 10, 33))]
+    res = {}
+    for dyn, ss in ((1, 1), (0, 0), (1, 0)):     # item schedule, slot streams
+        s = P.hsma_server_create(8, 8e9, prec)
+        P.hsma_set_option(s, "ragged_variant", variant)
+        P.hsma_set_option(s, "ragged_dynamic", dyn)
+        P.hsma_set_option(s, "slot_streams", ss)
+        assert P.hsma_get_info(s, "ragged_variant") == variant and P.hsma_get_info(s, "slot_streams") == ss
+        res[dyn, ss] = serve_all(P, s, reqs)
+        alone = serve_all(P, s, [reqs[1]])[0]
+        P.hsma_destroy(s)
+        assert alone[0] == res[dyn, ss][1][0] and np.array_equal(alone[1], res[dyn, ss][1][1])
+    for key in ((0, 0), (1, 0)):
+        for (E1, F1), (E0, F0) in zip(res[1, 1], res[key]):
+            assert E1 == E0 and np.array_equal(F1, F0), key
+    for (c, x, q), (E, F) in zip(reqs, res[1, 1]):
+        h = P.HSMA(c.box, 3, c.p, c.M, precision=prec)
+        Er, Fr, _ = h.eval(x, q)
+        h.close()
+        assert abs(E - Er) <= 1e-6 * abs(Er)
+        assert frms(F, Fr) <= 1e-5 and fmax(F, Fr) <= FMAX * 1e-5
+
+
+def test_server_options_are_checked(P):
+    s = P.hsma_server_create(4, 4e9, 1)
+    for key, bad in (("ragged_variant", 32), ("ragged_variant", 13), ("ragged_dynamic", 2), ("slot_streams", 3)):
+        with pytest.raises(P.HSMAError):
+            P.hsma_set_option(s, key, bad)
+    P.hsma_destroy(s)
+    s = P.hsma_server_create(4, 4e9, 0)
+    with pytest.raises(P.HSMAError):
+        P.hsma_set_option(s, "ragged_variant", 12)   # FP64 serving has no ragged launch
+    P.hsma_destroy(s)

@@ -185,3 +185,22 @@ def test_tree_leaf_modes(P, mode):
     with pytest.raises(P.HSMAError):
         h.set_option("tree_leaf_mode", 3)
     h.close()
+
+
+def test_tree_work_counts(P):
+    # the counting instance of the evaluation (option tree_count) computes the
+    # same sums, bitwise, and reports work within its structural bounds: at
+    # most 189 multipole evaluations per target and level, and at most every
+    # image as a direct pair of every target
+    c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
+    x, q = workloads.electrolyte(c)
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1, near_tree=1)
+    E0, F0, _ = h.eval(x, q)
+    h.set_option("tree_count", 1)
+    E1, F1, _ = h.eval(x, q)
+    m2p, direct = h.info("tree_m2p"), h.info("tree_direct_pairs")
+    L, Ns, nt = int(h.info("tree_levels")), int(h.info("Ns")), c.N + int(h.info("n_check"))
+    h.close()
+    assert E1 == E0 and np.array_equal(F1, F0)
+    assert 0 < m2p <= 189 * (L - 1) * nt
+    assert 0 < direct < nt * Ns
