@@ -119,6 +119,21 @@ __device__ void fused_reduce(const PairArgs& a, int tile, int tile_targets) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) a.red[(size_t)c * ld + t] = s[c];
   }
+  // The tile's partials are dead now: drop their lines from L2 without
+  // writing them back (discard.global.L2), so that partials that were summed
+  // while still in L2 never reach DRAM.  Only lines wholly inside this tile's
+  // target range: the boundary lines are shared with the neighbouring tiles,
+  // whose partials may still be pending.
+  __syncthreads();   // every thread of the CTA has read its partials
+  const int lines = tile_targets / 16;   // 128-byte lines per row of tile_targets doubles
+  const int rows = 4 * a.n_chunks;
+  for (int idx = threadIdx.x; idx < rows * lines; idx += blockDim.x) {
+    const int row = idx / lines, line = idx - row * lines;
+    const uintptr_t r0 = (uintptr_t)(a.part + (size_t)row * ld + t0);
+    const uintptr_t r1 = (uintptr_t)(a.part + (size_t)row * ld + t1);
+    const uintptr_t p = ((r0 + 127) & ~(uintptr_t)127) + 128 * (uintptr_t)line;
+    if (p + 128 <= r1) asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+  }
   if (threadIdx.x == 0) a.ticket[tile] = 0;
 }
 
