@@ -256,7 +256,8 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * buffer is freed and, for live buffers, when this key is read; waits for
  * the device first), "fused_reduce", "dynamic_schedule" (the options),
  * "tree_m2p", "tree_direct_pairs" (the tree evaluation's work at the last
- * evaluation with option tree_count = 1).
+ * evaluation with option tree_count = 1), "t_tree_eval_ms" (the tree's
+ * evaluation kernel alone, with option timing = 1).
  * On a server handle (hsma_server_create) the keys are "batches" (batches
  * enqueued so far), "inflight_at_last_batch" (earlier batches still on the
  * GPU when the last one was enqueued), "queued" (requests waiting for a

@@ -190,6 +190,8 @@ hsma_ctx::~hsma_ctx() {
   if (h_sc) cudaFreeHost(h_sc);
   for (int i = 0; i < hsma_ctx::kEvents; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
+  for (cudaEvent_t e : tree_ev)
+    if (e) cudaEventDestroy(e);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -397,6 +399,15 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
       return fail(h, HSMA_ERR_CUDA, "tree work counters");
     }
     T.work = (unsigned long long*)h->d_twork.p;
+  }
+  if (h->timing) {
+    for (cudaEvent_t& ev : h->tree_ev)
+      if (!ev && cudaEventCreate(&ev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, HSMA_ERR_CUDA, "tree timing events");
+      }
+    T.eval_ev[0] = h->tree_ev[0];
+    T.eval_ev[1] = h->tree_ev[1];
   }
   cudaError_t e = launch_tree(T, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "tree launch");
@@ -680,6 +691,11 @@ int finish_eval(hsma_ctx* h, double* energy) {
       }
       h->times[i] = t;
     }
+    float tt = 0.f;
+    if (h->near_tree && h->tree_ev[0] && cudaEventElapsedTime(&tt, h->tree_ev[0], h->tree_ev[1]) == cudaSuccess)
+      h->t_tree_eval = tt;
+    else
+      cudaGetLastError();
   }
   if (h->tree_count && h->near_tree && h->d_twork.p) {
     unsigned long long w[2] = {0, 0};
@@ -1048,6 +1064,7 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "tree_levels") *value = h->near_tree ? h->tree_L : 0;
   else if (k == "tree_direct_leaf") *value = h->near_tree ? h->tree_args.direct_leaf : 0;
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
+  else if (k == "t_tree_eval_ms") *value = h->t_tree_eval;
   else if (k == "tree_m2p") *value = h->tree_work[0];
   else if (k == "tree_direct_pairs") *value = h->tree_work[1];
   else if (k == "fused_reduce") *value = h->fused_reduce;

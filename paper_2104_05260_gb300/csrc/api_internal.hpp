@@ -101,6 +101,8 @@ struct hsma_ctx {
   int tree_count = 0;
   hsma::DevBuf d_twork;
   double tree_work[2] = {0, 0};
+  cudaEvent_t tree_ev[2] = {nullptr, nullptr};   // around the tree evaluation kernel (timing mode)
+  double t_tree_eval = 0;
   hsma::DevBuf d_ticket;     // per-tile counters of both launches, then two queues
   int ticket_far = 0;        // offset of the far launch's counters in d_ticket
   int ticket_queue = 0;      // offset of the two queue pairs in d_ticket

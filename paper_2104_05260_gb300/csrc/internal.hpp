@@ -145,6 +145,8 @@ struct TreeLaunch {
   // work[0] the multipole evaluations (M2P) and to work[1] the FP32 direct
   // pairs it sums (the algorithmic work behind the tree's roofline)
   unsigned long long* work = nullptr;
+  // when not NULL, recorded just before and after the evaluation kernel
+  cudaEvent_t eval_ev[2] = {nullptr, nullptr};
 };
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
 size_t tree_eval_smem(int P);

@@ -744,6 +744,7 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   const OwnImages own{T.sc, T.xc, T.q, T.shifts, T.ioff, T.icnt, T.img_shift};
   const size_t sm = tree_eval_smem(t.P);
   const int eval_grid = 5 * tree_sm_count();
+  if (T.eval_ev[0]) cudaEventRecord(T.eval_ev[0], s);
 #define HSMA_TREE_EVAL(PP)                                                                                  \
   if (T.work)                                                                                                \
     k_tree_eval<PP, true><<<eval_grid, kTreeThreads, sm, s>>>(t, T.tgt, T.n_ions, T.tgt_start, T.tgt_order, \
@@ -767,6 +768,7 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
 #undef HSMA_TREE_EVAL
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (T.eval_ev[1]) cudaEventRecord(T.eval_ev[1], s);
   return launch_reduce_chunks(T.out_parts, T.parts, T.ld, T.n_tgt, T.out, s);
 }
 
