@@ -360,6 +360,11 @@ const char* hsma_last_error(hsma_t h);
  * precision as for hsma_set_option (0, 1 or 2).  Requests that arrive while others run
  * are admitted as slots and memory free up; their pair sums share launches.
  * Each request's result is identical to an evaluation of it alone.
+ * Each slot runs its request's own small kernels on a stream of its own.
+ * Host memory: every request holds pinned copies of its inputs and result
+ * from submit to poll; these buffers are pooled by size and kept, for reuse,
+ * until hsma_destroy of the server (the pool's size is that of the most
+ * requests ever held at once).
  */
 int hsma_server_create(int slots, double budget_bytes, int precision, hsma_t* out);
 

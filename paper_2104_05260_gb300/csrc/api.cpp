@@ -779,7 +779,7 @@ static int tune_near(hsma_ctx* h, int64_t N) {
     if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
     if (ci > 0) cudaEventElapsedTime(&c.ms, h->ev[0], h->ev[1]);
   }
-  // The fastest plan, except that plans within 1 % of it (the spread of one
+  // The fastest plan, except that plans within 2 % of it (the spread of one
   // timed launch) are ranked by a fixed preference, so that runs settle on
   // the same plan: the shared-memory-sum variants first, then the packed 2-
   // and 4-target ones, then the scalar one; at equal variant the chunk count
@@ -794,7 +794,7 @@ static int tune_near(hsma_ctx* h, int64_t N) {
   };
   const Cand* best = nullptr;
   for (const Cand& c : cands) {
-    if (c.ms > 1.01f * fastest) continue;
+    if (c.ms > 1.02f * fastest) continue;
     if (!best) {
       best = &c;
       continue;
