@@ -781,16 +781,20 @@ def tree_roofline(P, h, xd, qd, N, e, f, near_ms, order, peak_instr):
     P.hsma_eval_into(h.h, xd, qd, N, e, f)
     torch.cuda.synchronize()
     m2p = P.hsma_get_info(h.h, "tree_m2p")
+    m2p_low = P.hsma_get_info(h.h, "tree_m2p_low")
     direct = P.hsma_get_info(h.h, "tree_direct_pairs")
     P.hsma_set_option(h.h, "tree_count", 0)
     terms = (order + 1) * (order + 2) // 2
-    ops = m2p * terms * M2P_OPS_PER_TERM + direct * FP32_INSTR_PER_PAIR
+    low = order - 4 if order >= 8 else order
+    terms_low = (low + 1) * (low + 2) // 2
+    ops = (m2p * terms + m2p_low * terms_low) * M2P_OPS_PER_TERM + direct * FP32_INSTR_PER_PAIR
     achieved = ops / (eval_ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": f"k_tree_eval<{order}> (near field + check points)",
             "achieved": achieved, "peak": peak_instr, "unit": "T FP32-pipe instr/s", "frac": achieved / peak_instr,
-            "traffic": None, "m2p_per_eval": m2p, "direct_pairs_per_eval": direct,
-            "algorithmic": f"M2P x {terms} terms x {M2P_OPS_PER_TERM} + direct pairs x {FP32_INSTR_PER_PAIR} "
-                           f"FP32 operations = {ops:.4g} per evaluation",
+            "traffic": None, "m2p_per_eval": m2p, "m2p_low_order_per_eval": m2p_low,
+            "direct_pairs_per_eval": direct,
+            "algorithmic": f"(M2P x {terms} + far-cell M2P x {terms_low}) terms x {M2P_OPS_PER_TERM} + direct "
+                           f"pairs x {FP32_INSTR_PER_PAIR} FP32 operations = {ops:.4g} per evaluation",
             "eval_kernel_ms": eval_ms, "near_stage_ms": near_ms,
             "near_stage_frac": ops / (near_ms / 1e3) / 1e12 / peak_instr}
 

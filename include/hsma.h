@@ -121,6 +121,12 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       shared memory) for precision 2; turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
+ *   "tree_far_order"    1 (default) = above the leaf level, listed cells whose
+ *                       centre lies at least sqrt(8) cell widths from the
+ *                       target's cell are evaluated to order P - 4 (for
+ *                       tree_order >= 8): their truncation bound stays well
+ *                       below that of the nearest listed cells at order P.
+ *                       0 = every cell to order P.
  *   "tree_count"        1 = the tree evaluation runs its counting instance,
  *                       which also counts the multipole evaluations (M2P)
  *                       and FP32 direct pairs it performs (info keys
@@ -255,8 +261,10 @@ int hsma_eval_ex(hsma_t h, const double* x, const double* q, int64_t N,
  * allocated with such a band holding a fixed pattern, compared when the
  * buffer is freed and, for live buffers, when this key is read; waits for
  * the device first), "fused_reduce", "dynamic_schedule" (the options),
- * "tree_m2p", "tree_direct_pairs" (the tree evaluation's work at the last
- * evaluation with option tree_count = 1), "t_tree_eval_ms" (the tree's
+ * "tree_m2p", "tree_m2p_low", "tree_direct_pairs" (the tree evaluation's
+ * work at the last evaluation with option tree_count = 1: multipole
+ * evaluations to order P and to the lower far-cell order, direct pairs),
+ * "tree_far_order" (the option), "t_tree_eval_ms" (the tree's
  * evaluation kernel alone, with option timing = 1).
  * On a server handle (hsma_server_create) the keys are "batches" (batches
  * enqueued so far), "inflight_at_last_batch" (earlier batches still on the

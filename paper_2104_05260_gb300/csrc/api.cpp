@@ -317,6 +317,13 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   }
   const double occupied = h->ns_est / (frac * (double)((size_t)1 << (3 * L)));
   t.direct_leaf = h->tree_leaf_mode == 1 ? 1 : h->tree_leaf_mode == 2 ? 0 : (occupied <= 48.0 ? 1 : 0);
+  // listed cells at least sqrt(8) cell widths from the target's cell: order
+  // P - 4.  A cell of half-diagonal 0.866 w seen from anywhere in a cell at
+  // centre distance D converges with ratio 0.866 / (D - 0.866); the nearest
+  // listed cells (D = 2) give 0.764, whose P + 1 = 11th power is 0.05, and
+  // D = sqrt(8) gives 0.441, whose 7th power is 0.003: the truncation bound
+  // of every far cell stays well below that of the nearest cells
+  t.far_d2 = h->tree_far_order ? 8 : 0;
   t.Rs = (float)half;
   t.D = (float)(2.0 * half);
   t.inv_wL = (float)((double)(1 << L) / (2.0 * half));
@@ -394,7 +401,7 @@ static int launch_near_tree(hsma_ctx* h, int64_t N) {
   T.icnt = (const int*)h->d_cnt.p;
   T.img_shift = (const int*)h->d_imgshift.p;
   if (h->tree_count && h->d_twork.p) {   // allocated when the option is set (this may run under capture)
-    if (cudaMemsetAsync(h->d_twork.p, 0, 2 * sizeof(unsigned long long), h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->d_twork.p, 0, 3 * sizeof(unsigned long long), h->stream) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, HSMA_ERR_CUDA, "tree work counters");
     }
@@ -698,10 +705,9 @@ int finish_eval(hsma_ctx* h, double* energy) {
       cudaGetLastError();
   }
   if (h->tree_count && h->near_tree && h->d_twork.p) {
-    unsigned long long w[2] = {0, 0};
+    unsigned long long w[3] = {0, 0, 0};
     if (cudaMemcpy(w, h->d_twork.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) cudaGetLastError();
-    h->tree_work[0] = (double)w[0];
-    h->tree_work[1] = (double)w[1];
+    for (int i = 0; i < 3; ++i) h->tree_work[i] = (double)w[i];
   }
   if (r.flags & FLAG_OUT_OF_SLAB) return fail(h, HSMA_ERR_OUT_OF_SLAB, "some z outside (0, Lz)");
   if (r.flags & FLAG_NOT_NEUTRAL) return fail(h, HSMA_ERR_NOT_NEUTRAL, "system not neutral");
@@ -999,9 +1005,13 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
   } else if (k == "graphs") {
     h->use_graphs = (v != 0);
     drop_graph(h);
+  } else if (k == "tree_far_order") {
+    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "tree_far_order must be 0 or 1");
+    h->tree_far_order = (int)v;
+    h->plan_N = -1;
   } else if (k == "tree_count") {
     if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, "tree_count must be 0 or 1");
-    if (v == 1 && h->d_twork.ensure(2 * sizeof(unsigned long long)))
+    if (v == 1 && h->d_twork.ensure(3 * sizeof(unsigned long long)))
       return fail(h, HSMA_ERR_NOMEM, "tree work counters");
     h->tree_count = (int)v;
     drop_graph(h);
@@ -1094,6 +1104,8 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "kernels_per_eval") *value = h->kernels_per_eval;
   else if (k == "t_tree_eval_ms") *value = h->t_tree_eval;
   else if (k == "tree_m2p") *value = h->tree_work[0];
+  else if (k == "tree_m2p_low") *value = h->tree_work[2];
+  else if (k == "tree_far_order") *value = h->tree_far_order;
   else if (k == "tree_direct_pairs") *value = h->tree_work[1];
   else if (k == "fused_reduce") *value = h->fused_reduce;
   else if (k == "dynamic_schedule") *value = h->dynamic_schedule;

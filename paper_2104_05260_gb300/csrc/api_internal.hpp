@@ -100,7 +100,8 @@ struct hsma_ctx {
   // direct pairs of the last evaluation
   int tree_count = 0;
   hsma::DevBuf d_twork;
-  double tree_work[2] = {0, 0};
+  double tree_work[3] = {0, 0, 0};
+  int tree_far_order = 1;    // far cells above the leaf level to order P - 4 (P >= 8)
   cudaEvent_t tree_ev[2] = {nullptr, nullptr};   // around the tree evaluation kernel (timing mode)
   double t_tree_eval = 0;
   hsma::DevBuf d_ticket;     // per-tile counters of both launches, then two queues

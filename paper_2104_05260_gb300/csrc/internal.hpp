@@ -118,6 +118,10 @@ struct TreeArgs {
   const float* norm;     // (P+1)^2: c_n0, sqrt(2) c_nm (2m-1)!! at n*(P+1) + m
   const float* fac;      // (P+1)^2: 4 pi/(2n+1) * norm^2 at k = n^2 + n + m
   int direct_leaf;       // 1: the leaf level is summed directly (no leaf multipoles)
+  // Above the leaf level, a listed cell whose centre lies at least
+  // sqrt(far_d2) cell widths from the target's cell is evaluated to order
+  // P - 4 instead of P (P >= 8); 0 = every cell to order P.
+  int far_d2;
 };
 struct TreeLaunch {
   TreeArgs t;
@@ -142,8 +146,9 @@ struct TreeLaunch {
   const int* icnt;       // n_ions: its number of section-1 images
   const int* img_shift;  // section-1 image (index - n_ions) -> shift index
   // when not NULL, the evaluation runs its counting instance, which adds to
-  // work[0] the multipole evaluations (M2P) and to work[1] the FP32 direct
-  // pairs it sums (the algorithmic work behind the tree's roofline)
+  // work[0] the multipole evaluations (M2P) to order P, to work[1] the FP32
+  // direct pairs it sums and to work[2] the M2P to the lower order of far
+  // cells (the algorithmic work behind the tree's roofline)
   unsigned long long* work = nullptr;
   // when not NULL, recorded just before and after the evaluation kernel
   cudaEvent_t eval_ev[2] = {nullptr, nullptr};

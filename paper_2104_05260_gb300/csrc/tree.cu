@@ -458,7 +458,9 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
   int* slist = sid + (kTreeThreads - warp * 32) + warp * 216;                  // compacted list, 216 per warp
   const int nsideL = 1 << t.L;
   const int n_items = S * task_start[n_cells];
-  unsigned long long n_m2p = 0, n_dir = 0;   // counting instance only
+  unsigned long long n_m2p = 0, n_dir = 0, n_m2p_low = 0;   // counting instance only
+  // far cells of the levels above the leaf level: order PL (see TreeArgs)
+  constexpr int PL = P >= 8 ? P - 4 : P;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(queue, 1);
@@ -536,11 +538,19 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
             int ox, oy, oz;
             morton_decode(slist[b0 + c], l, &ox, &oy, &oz);
             if (l == t.L && abs(ox - lx) <= 1 && abs(oy - ly) <= 1 && abs(oz - lz) <= 1) continue;
-            if (COUNT) ++n_m2p;
             const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
             const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
             const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
-            m2p_accumulate<P>(sM + c * nc4, dx, dy, dz, &fp, &fx, &fy, &fz);
+            // the same cell for every lane (levels above the leaf level are
+            // listed for G's ancestor), so the choice does not diverge
+            const int ex = ox - cx, ey = oy - cy, ez = oz - cz;
+            if (PL < P && t.far_d2 > 0 && l < t.L && ex * ex + ey * ey + ez * ez >= t.far_d2) {
+              if (COUNT) ++n_m2p_low;
+              m2p_accumulate<PL>(sM + c * nc4, dx, dy, dz, &fp, &fx, &fy, &fz);
+            } else {
+              if (COUNT) ++n_m2p;
+              m2p_accumulate<P>(sM + c * nc4, dx, dy, dz, &fp, &fx, &fy, &fz);
+            }
           }
       }
       phi += (double)fp * (double)inv_w;
@@ -665,10 +675,12 @@ __global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const
     for (int w = 16; w > 0; w >>= 1) {
       n_m2p += __shfl_down_sync(0xffffffffu, n_m2p, w);
       n_dir += __shfl_down_sync(0xffffffffu, n_dir, w);
+      n_m2p_low += __shfl_down_sync(0xffffffffu, n_m2p_low, w);
     }
     if (lane == 0) {
       atomicAdd(work, n_m2p);
       atomicAdd(work + 1, n_dir);
+      atomicAdd(work + 2, n_m2p_low);
     }
   }
 }

@@ -362,19 +362,39 @@ def test_cfg2_energy_fp32_vs_fp64(P):
     assert rel(E32, E64) <= E_TOL[1]
 
 
-def test_cfg5_262k_sampled(P):
-    sampled(P, workloads.case(5), 1, 24)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cfg5_262k_sampled(P, prec):
+    # the bench workload (N = 262,144, p = 10, M = 4000) at every precision
+    sampled(P, workloads.case(5), prec, 24)
 
 
-@pytest.mark.parametrize("gam", [-0.95, 0.0, 0.95])
+def test_cfg5_exact_differences_reach_fp64_class_forces(P):
+    # precision 2 at the bench workload: FP32 pair arithmetic with exactly
+    # formed differences agrees with the oracle like an FP64 path (force RMS
+    # and every sampled ion within 1e-6 / 2e-5 of the RMS force)
+    c = workloads.case(5)
+    x, q = workloads.electrolyte(c)
+    rng = np.random.default_rng(321)
+    idx = np.sort(rng.choice(c.N, 24, replace=False))
+    st = O.make_setup(c.box, 3, c.p, c.M, lam=c.lam)
+    ref = O.evaluate(st, x, q, targets=idx)
+    h, E, F, pot = run(P, c, x, q, 2)
+    h.close()
+    assert frms(F[idx], ref["forces"]) <= 1e-6, frms(F[idx], ref["forces"])
+    assert fmax(F[idx], ref["forces"]) <= 2e-5, fmax(F[idx], ref["forces"])
+
+
+@pytest.mark.parametrize("gam", [-0.95, 0.0, 0.95, (0.6, -0.3)])
 def test_cfg3_2d_20k_stagewise(P, gam):
     # 2D, N = 20000, G = 80: the oracle cannot redo all 13124 check targets in
     # seconds, so each step is checked on its own: check-point sums on a
     # sample, the fit + map from the GPU's own check values, and near + far at
-    # sampled particles.
-    c = workloads.case(3, gamma=gam)
+    # sampled particles.  The last case has unequal interfaces.
+    import dataclasses
+    gt, gb = gam if isinstance(gam, tuple) else (gam, gam)
+    c = dataclasses.replace(workloads.case(3, gamma=gt), gammas=(gt, gb))
     x, q = workloads.electrolyte(c)
-    st = O.make_setup(c.box, 2, c.p, c.M, gam, gam, lam=c.lam, dtn_grid=c.dtn_grid)
+    st = O.make_setup(c.box, 2, c.p, c.M, gt, gb, lam=c.lam, dtn_grid=c.dtn_grid)
     h, E, F, pot = run(P, c, x, q, 1)
     xc, qc = O.prepare_inputs(st, x, q)
     ipos, iq, isrc, isid = O.near_set(st, xc, qc)

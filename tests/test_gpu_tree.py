@@ -204,3 +204,27 @@ def test_tree_work_counts(P):
     assert E1 == E0 and np.array_equal(F1, F0)
     assert 0 < m2p <= 189 * (L - 1) * nt
     assert 0 < direct < nt * Ns
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tree_far_cells_at_lower_order(P, mode):
+    # option tree_far_order: above the leaf level, listed cells at least
+    # sqrt(8) cell widths away are evaluated to order P - 4.  Both settings
+    # meet the oracle bounds, the split shows in the counted work, and the
+    # lower order costs no more than the FP32 rounding of the pair sums
+    c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
+    x, q = workloads.electrolyte(c)
+    ref = O.evaluate(O.make_setup(c.box, 3, 6, 800), x, q)
+    res = {}
+    for far in (0, 1):
+        h = P.HSMA(c.box, 3, 6, 800, precision=1, near_tree=1, tree_order=10, tree_leaf_mode=mode,
+                   tree_far_order=far, tree_count=1)
+        E, F, _ = h.eval(x, q)
+        res[far] = (E, F, h.info("tree_m2p"), h.info("tree_m2p_low"))
+        assert h.info("tree_far_order") == far
+        h.close()
+        assert frms(F, ref["forces"]) <= 2e-5 and abs(E - ref["energy"]) <= 1e-5 * abs(ref["energy"])
+        assert fmax(F, ref["forces"]) <= FMAX * 2e-5
+    assert res[0][3] == 0 and res[1][3] > 0
+    assert res[1][2] + res[1][3] == res[0][2]            # the same cells, split by order
+    assert frms(res[1][1], res[0][1]) <= 5e-6
