@@ -432,8 +432,14 @@ struct OwnImages {
   const int* img_shift;
 };
 
+// Resident blocks of the evaluation kernel per SM: 6 (80 registers a thread)
+// up to order 10; the higher orders need more registers and keep 5.  Six
+// blocks measured 2 % faster than 5 at P = 10; 7 and 8 (72 and 64 registers)
+// were slower.
+constexpr int tree_eval_blocks(int P) { return P <= 10 ? 6 : 5; }
+
 template <int P, bool COUNT>
-__global__ void __launch_bounds__(kTreeThreads, 5) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
+__global__ void __launch_bounds__(kTreeThreads, tree_eval_blocks(P)) k_tree_eval(TreeArgs t, const float4* __restrict__ tgt,
                                                                int n_ions, const int* __restrict__ tgt_start,
                                                                const int* __restrict__ tgt_order,
                                                                const float4* __restrict__ srcs,
@@ -759,7 +765,7 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const OwnImages own{T.sc, T.xc, T.q, T.shifts, T.ioff, T.icnt, T.img_shift};
   const size_t sm = tree_eval_smem(t.P);
-  const int eval_grid = 5 * tree_sm_count();
+  const int eval_grid = tree_eval_blocks(t.P) * tree_sm_count();
   if (T.eval_ev[0]) cudaEventRecord(T.eval_ev[0], s);
 #define HSMA_TREE_EVAL(PP)                                                                                  \
   if (T.work)                                                                                                \
