@@ -936,6 +936,8 @@ def main():
     ap.add_argument("--md-eq", type=int, default=20000, help="equilibration steps of --md")
     ap.add_argument("--md-slab", type=int, default=0, choices=[0, 1, 2],
                     help="run the Sec. 4.3 confined-electrolyte MD with this cation valence and exit")
+    ap.add_argument("--serve-only", type=int, default=0, metavar="N_REQ",
+                    help="run only the served stream (precision 1) with this many requests and exit")
     ap.add_argument("--near-tree", type=int, default=0, choices=[0, 1],
                     help="1: tree evaluation of the near-field sums (option near_tree, order 10)")
     ap.add_argument("--far-field", type=int, default=0, choices=[0, 1],
@@ -977,6 +979,12 @@ def main():
         if rank == 0:
             print(json.dumps({"md_slab": md_e3(P, valence=args.md_slab, steps_eq=args.md_eq,
                                                steps_prod=args.md_steps)}), flush=True)
+        if dist:
+            dist.barrier()
+        return
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serve": serve_bench(P, n_req=args.serve_only)}), flush=True)
         if dist:
             dist.barrier()
         return
