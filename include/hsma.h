@@ -214,6 +214,14 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *   "ragged_dynamic"    1 (default) = the ragged launches' CTAs take items
  *                       from a device counter; 0 = static round-robin.
  *                       Results are the same either way.
+ *   "slot_streams"      1 (default) = each slot's small kernels and copies on
+ *                       a stream of its own; 0 = everything on the server's
+ *                       stream.  Only while the server holds no request.
+ *   "max_batch"         requests per batch at most; 0 (default) = every
+ *                       request a free slot admits.  Below the slot count,
+ *                       several batches are in flight and a batch's prep
+ *                       overlaps the earlier batches' launches.  Results are
+ *                       the same either way.
  * Errors: HSMA_ERR_ARG (unknown key or value out of range).
  */
 int hsma_set_option(hsma_t h, const char* key, double value);

@@ -147,6 +147,7 @@ struct Server {
   int ragged_variant = 12;
   int ragged_dynamic = 1;
   int slot_streams = 1;   // each slot's small kernels on a stream of its own
+  int max_batch = 0;      // requests per batch at most (0: every free slot)
   DevBuf d_queue;
 };
 
@@ -300,11 +301,14 @@ static void retire(Server* s) {
 // Enqueue one batch.  Each request's own small kernels (prep, fit,
 // assembly) and copies run on its slot's stream, so those of different
 // requests overlap on the GPU; the two ragged pair launches run on the server
-// stream.  Events join the streams: every slot waits for the batch start,
-// the server stream waits for every slot before each ragged launch, the slots
-// wait for that launch before their next stage, and the batch's done event
-// follows every slot's last copy.  With slot streams off (option
-// slot_streams = 0) everything runs on the server stream in this order.
+// stream.  Events join the streams: the server stream waits for every slot
+// before each ragged launch, the slots wait for that launch before their next
+// stage, and the batch's done event follows every slot's last copy.  A slot's
+// first stage (input copies, prep) waits for nothing: the slot's buffers
+// belong to its request alone, so with several batches in flight (option
+// max_batch) a batch's prep runs while an earlier batch is still on the GPU.
+// With slot streams off (option slot_streams = 0) everything runs on the
+// server stream in this order.
 static int launch_batch(Server* s, BatchBuf& bb) {
   cudaStream_t st = s->stream;
   const int n = (int)bb.reqs.size();
@@ -328,7 +332,6 @@ static int launch_batch(Server* s, BatchBuf& bb) {
     }
     return true;
   };
-  if (!fan_out(bb.start)) return HSMA_ERR_CUDA;
   for (Request* r : bb.reqs) {
     hsma_ctx* h = slot_of(r).ctx;
     cudaError_t e = cudaMemcpyAsync(h->d_x.p, r->hx, (size_t)r->N * 24, cudaMemcpyHostToDevice, h->stream);
@@ -401,7 +404,7 @@ static int step(Server* s) {
     if (!b.busy) { bb = &b; break; }
   if (bb) {
     // admit in arrival order while a slot and the budget allow
-    while (!s->queue.empty()) {
+    while (!s->queue.empty() && (s->max_batch <= 0 || (int)bb->reqs.size() < s->max_batch)) {
       Request* r = s->queue.front();
       int free_slot = -1;
       for (size_t i = 0; i < s->slots.size(); ++i)
@@ -459,6 +462,7 @@ int server_get_info(hsma_ctx* h, const std::string& key, double* v) {
   else if (key == "ragged_variant") *v = h->srv->ragged_variant;
   else if (key == "ragged_dynamic") *v = h->srv->ragged_dynamic;
   else if (key == "slot_streams") *v = h->srv->slot_streams;
+  else if (key == "max_batch") *v = h->srv->max_batch;
   else return HSMA_ERR_ARG;
   return HSMA_OK;
 }
@@ -468,6 +472,15 @@ int server_set_option(hsma_ctx* h, const std::string& key, double v) {
   Server* s = h->srv;
   if (key == "inject_fail_ticket" && v >= 0) {
     s->inject_fail_ticket = (uint64_t)v;
+    return HSMA_OK;
+  }
+  if (key == "max_batch") {
+    // takes effect at the next batch; requests already admitted keep theirs
+    if (v < 0 || v != (int)v) {
+      h->err = "max_batch must be an integer >= 0";
+      return HSMA_ERR_ARG;
+    }
+    s->max_batch = (int)v;
     return HSMA_OK;
   }
   if (key == "ragged_variant" || key == "ragged_dynamic" || key == "slot_streams") {

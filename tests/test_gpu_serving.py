@@ -233,9 +233,30 @@ def test_ragged_variants_and_schedules(P, prec, variant):
         assert frms(F, Fr) <= 1e-5 and fmax(F, Fr) <= FMAX * 1e-5
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_cap_changes_nothing_but_the_batches(P, prec):
+    # with at most 2 requests a batch, several batches are in flight and a
+    # batch's prep overlaps the earlier ones' launches; every result stays
+    # bitwise the one of the uncapped server
+    reqs = [request(N, p, s) for N, p, s in ((2500, 8, 51), (900, 6, 52), (12000, 10, 53), (1800, 8, 54),
+                                             (640, 6, 55))]
+    res, batches = {}, {}
+    for cap in (0, 2):
+        s = P.hsma_server_create(8, 8e9, prec)
+        P.hsma_set_option(s, "max_batch", cap)
+        assert P.hsma_get_info(s, "max_batch") == cap
+        res[cap] = serve_all(P, s, reqs)
+        batches[cap] = P.hsma_get_info(s, "batches")
+        P.hsma_destroy(s)
+    assert batches[2] >= (len(reqs) + 1) // 2
+    for (E0, F0), (E2, F2) in zip(res[0], res[2]):
+        assert E0 == E2 and np.array_equal(F0, F2)
+
+
 def test_server_options_are_checked(P):
     s = P.hsma_server_create(4, 4e9, 1)
-    for key, bad in (("ragged_variant", 32), ("ragged_variant", 13), ("ragged_dynamic", 2), ("slot_streams", 3)):
+    for key, bad in (("ragged_variant", 32), ("ragged_variant", 13), ("ragged_dynamic", 2), ("slot_streams", 3),
+                     ("max_batch", -1), ("max_batch", 1.5)):
         with pytest.raises(P.HSMAError):
             P.hsma_set_option(s, key, bad)
     P.hsma_destroy(s)
