@@ -310,12 +310,13 @@ __global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_c
 //
 // Multipoles hold 4 pi/(2n+1) norm^2 sum q V'T, so the evaluation multiplies
 // by the irregular polynomial U'T alone; 1/(n-m) comes from a table.
-template <int P>
-__device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, float x, float y, float z, int pm,
+template <int P, int PL>
+__device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, float x, float y, float z, bool full,
                                                float* phi, float* gx, float* gy, float* gz) {
-  // pm <= P: the order actually summed (the terms n <= pm); one code body
-  // serves every order, so that warps at different orders share the
-  // instruction cache
+  // The terms n <= P when full, else n <= PL (PL <= P).  One code body serves
+  // both orders, so that warps at different orders share the instruction
+  // cache: the terms n > PL are the tail of each m-chain (m <= PL) and the
+  // whole chains m > PL, each skipped by one test of full, not one per term.
   // P is a compile-time constant: both loops unroll and the recursion
   // coefficients fold.  A term is u(r^2, z) (C_m Mc + S_m Ms) with
   // C_m + i S_m = (x + iy)^m, so its gradient is
@@ -337,13 +338,13 @@ __device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, flo
   float p = 0.f, sq = 0.f, sz = 0.f, sx = 0.f, sy = 0.f;
 #pragma unroll
   for (int m = 0; m <= P; ++m) {
-    if (m > pm) break;
+    if (m == PL + 1 && !full) break;
     float u1 = um, z1 = 0.0f, q1 = -((float)m + 0.5f) * rho * um;   // v, dv/dz, dv/d(r^2)
     float u2 = 0.0f, z2 = 0.0f, q2 = 0.0f;
     float uc = 0.f, us = 0.f, qc = 0.f, qs = 0.f, zc = 0.f, zs = 0.f;
 #pragma unroll
     for (int n = m; n <= P; ++n) {
-      if (n > pm) break;
+      if (m <= PL && n == PL + 1 && !full) break;
       float u, uz, uq;
       if (n == m) {
         u = u1; uz = z1; uq = q1;
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(kTreeThreads, tree_eval_blocks(P)) k_tree_eval
               if (far) ++n_m2p_low;
               else ++n_m2p;
             }
-            m2p_accumulate<P>(sM + c * nc4, dx, dy, dz, far ? PL : P, &fp, &fx, &fy, &fz);
+            m2p_accumulate<P, PL>(sM + c * nc4, dx, dy, dz, !far, &fp, &fx, &fy, &fz);
           }
       }
       phi += (double)fp * (double)inv_w;
