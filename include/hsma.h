@@ -132,12 +132,16 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       and FP32 direct pairs it performs (info keys
  *                       "tree_m2p", "tree_direct_pairs"); slower, for the
  *                       roofline only.  0 (default) = off.
- *   "fused_reduce"      1 (default) = each pair launch sums its per-chunk
- *                       partials itself: the CTA that finishes a target
- *                       tile's last chunk adds that tile's partials in the
- *                       fixed order of the separate reduction (bitwise the
- *                       same result, one launch fewer, partials read back
- *                       while still in L2); 0 = a separate reduction launch.
+ *   "fused_reduce"      2 = each pair launch sums its per-chunk partials
+ *                       itself: the CTA that finishes a target tile's last
+ *                       chunk adds that tile's partials in the fixed order
+ *                       of the separate reduction (bitwise the same result,
+ *                       one launch fewer, partials read back while still in
+ *                       L2); 0 = a separate reduction launch; 1 (default) =
+ *                       per launch, the fused form where the tile sums are
+ *                       short beside the launch's pair work (long launches),
+ *                       else the separate one.  Info keys "fused_near" and
+ *                       "fused_far" give the choice of the current plan.
  *   "dynamic_schedule"  1 (default) = pair-launch CTAs take (tile, chunk)
  *                       items from a device counter; 0 = a static
  *                       round-robin.  Either way each item writes its own

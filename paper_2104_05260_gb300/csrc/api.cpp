@@ -431,6 +431,23 @@ static int eff_tpt(const hsma_ctx* h) {
   return h->tpt;
 }
 
+// Whether a pair launch sums its own chunk partials (option fused_reduce).
+// In the fused form one CTA sums a tile's partials after its last chunk: about
+// n_chunks x tile_targets / 1024 us of L2 round trips that a short launch
+// cannot hide (the last tiles' sums form its tail), while the separate
+// reduction spreads the same reads over the whole GPU.  With the default
+// (1) the launch fuses when that estimate is under a tenth of the launch's
+// pair time at the kernel's rate (pairs x 13 FP32 operations at about
+// 30e12 a second): at N = 3,000 with 108 chunks the fused form made an
+// MD step 30 % slower, at N >= 1e5 it saves DRAM traffic for a few tenths
+// of a percent of time.  Both forms give bitwise the same sums.
+static bool use_fused(const hsma_ctx* h, int n_chunks, int tile_targets, double pairs) {
+  if (h->fused_reduce != 1) return h->fused_reduce == 2;
+  const double reduce_us = (double)n_chunks * tile_targets / 1024.0;
+  const double launch_us = pairs * 13.0 / 30e12 * 1e6;
+  return reduce_us < 0.1 * launch_us;
+}
+
 // Launch plan and buffers for N particles.
 int ensure_plan(hsma_ctx* h, int64_t N) {
   if (h->plan_N == N) return HSMA_OK;
@@ -450,6 +467,8 @@ int ensure_plan(hsma_ctx* h, int64_t N) {
   h->chunks2 = choose_chunks(h->tiles2, slots, g.par.M, 128);
   h->grid2 = (int)std::min<long>((long)h->tiles2 * h->chunks2, slots);
   h->slots = slots;
+  h->fuse1 = use_fused(h, h->chunks1, tile, (double)h->n_tgt1 * (double)h->ns_est);
+  h->fuse2 = use_fused(h, h->chunks2, tile, (double)N * (double)g.par.M);
   const size_t n = (size_t)N, nt = (size_t)h->n_tgt1;
   const size_t nblk = (size_t)prep_blocks((int)n, g.n_check) + (n + 255) / 256;
   const size_t simg = n * g.shifts.size();  // upper bound on images in B
@@ -564,7 +583,7 @@ PairArgs near_args(hsma_ctx* h, int64_t N) {
   p1.icnt = prec ? (const int*)h->d_cnt.p : nullptr;
   p1.src_lo = prec == 2 ? (const float4*)h->d_src32lo.p : nullptr;
   p1.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;
-  if (h->fused_reduce) {
+  if (h->fuse1) {
     p1.red = (double*)h->d_red1.p;
     p1.ticket = (int*)h->d_ticket.p;
   }
@@ -579,7 +598,7 @@ int stage_fit(hsma_ctx* h, int64_t N) {
   // the near/check partials summed over chunks once; the fit and the
   // assembly read the single row set
   cudaError_t e = cudaSuccess;
-  if (!h->near_tree && !h->fused_reduce)   // the tree and the fused launch write one row set
+  if (!h->near_tree && !h->fuse1)   // the tree and the fused launch write one row set
     e = launch_reduce_chunks((const double*)h->d_part.p, h->chunks1, h->n_tgt1, h->n_tgt1,
                              (double*)h->d_red1.p, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "chunk reduction");
@@ -608,7 +627,7 @@ PairArgs far_args(hsma_ctx* h, int64_t N) {
   p2.part = (double*)h->d_fpart.p;
   p2.ld = (int)N;
   p2.tgt_lo = prec == 2 ? (const float4*)h->d_tgt32lo.p : nullptr;   // surface charges: no lo part
-  if (h->fused_reduce) {
+  if (h->fuse2) {
     p2.red = (double*)h->d_red2.p;
     p2.ticket = (int*)h->d_ticket.p + h->ticket_far;
   }
@@ -621,8 +640,8 @@ int stage_assemble(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) 
   const int prec = h->precision;
   // the far field's single row set: the series writes it, the fused launch
   // sums its chunks itself, one chunk needs no sum
-  const bool far_one = h->far_series || (!h->fused_reduce && h->chunks2 == 1);
-  const bool far_sum = !h->far_series && !h->fused_reduce && h->chunks2 > 1;
+  const bool far_one = h->far_series || (!h->fuse2 && h->chunks2 == 1);
+  const bool far_sum = !h->far_series && !h->fuse2 && h->chunks2 > 1;
   cudaError_t e = cudaSuccess;
   if (far_sum)
     e = launch_reduce_chunks((const double*)h->d_fpart.p, h->chunks2, (int)N, (int)N, (double*)h->d_red2.p,
@@ -678,10 +697,10 @@ int enqueue_eval(hsma_ctx* h, int64_t N, double* forces_dev, double* pot_dev) {
   // 2..L-1 with a direct leaf level), task count and scan, evaluation and
   // part reduction; fit 3; far 1; far reduction 1 (not with one far chunk);
   // assembly 2
-  const bool far_sum = !h->far_series && !h->fused_reduce && h->chunks2 > 1;
+  const bool far_sum = !h->far_series && !h->fuse2 && h->chunks2 > 1;
   const int m_levels = h->near_tree ? std::max(0, h->tree_L - 1 - h->tree_args.direct_leaf) : 0;
   h->kernels_per_eval =
-      3 + (h->near_tree ? 13 + 2 * m_levels : (h->fused_reduce ? 1 : 2)) + 3 + 1 + (far_sum ? 1 : 0) + 2;
+      3 + (h->near_tree ? 13 + 2 * m_levels : (h->fuse1 ? 1 : 2)) + 3 + 1 + (far_sum ? 1 : 0) + 2;
   return HSMA_OK;
 }
 
@@ -773,12 +792,16 @@ static int tune_near(hsma_ctx* h, int64_t N) {
     const int tile = pair_tile_targets(prec, c.tpt);
     a.n_tiles = (h->n_tgt1 + tile - 1) / tile;
     a.n_chunks = c.chunks;
+    // each candidate with the reduction form it would run with
+    const bool fused = use_fused(h, c.chunks, tile, (double)h->n_tgt1 * (double)h->ns_est);
+    a.red = fused ? (double*)h->d_red1.p : nullptr;
+    a.ticket = fused ? (int*)h->d_ticket.p : nullptr;
     const int grid = (int)std::min<long>((long)a.n_tiles * a.n_chunks, pair_slots(prec, c.tpt));
     // timed with the chunk reduction that consumes its partials: more
     // chunks fill the GPU at small N but cost partial traffic
     cudaEventRecord(h->ev[0], s);
     cudaError_t e = launch_pair(prec, prec ? c.tpt : 1, a, grid, s);
-    if (e == cudaSuccess && !h->fused_reduce)
+    if (e == cudaSuccess && !fused)
       e = launch_reduce_chunks(a.part, a.n_chunks, a.ld, h->n_tgt1, (double*)h->d_red1.p, s);
     cudaEventRecord(h->ev[1], s);
     if (e == cudaSuccess) e = cudaEventSynchronize(h->ev[1]);
@@ -1016,7 +1039,8 @@ int hsma_set_option(hsma_t h, const char* key, double v) {
     h->tree_count = (int)v;
     drop_graph(h);
   } else if (k == "fused_reduce" || k == "dynamic_schedule") {
-    if (v != 0 && v != 1) return fail(h, HSMA_ERR_ARG, k + " must be 0 or 1");
+    if (v != 0 && v != 1 && !(v == 2 && k == "fused_reduce"))
+      return fail(h, HSMA_ERR_ARG, k == "fused_reduce" ? "fused_reduce must be 0, 1 or 2" : k + " must be 0 or 1");
     (k == "fused_reduce" ? h->fused_reduce : h->dynamic_schedule) = (int)v;
     h->tuned_N = -1;
     h->tuned_chunks = 0;
@@ -1108,6 +1132,8 @@ int hsma_get_info(hsma_t h, const char* key, double* value) {
   else if (k == "tree_far_order") *value = h->tree_far_order;
   else if (k == "tree_direct_pairs") *value = h->tree_work[1];
   else if (k == "fused_reduce") *value = h->fused_reduce;
+  else if (k == "fused_near") *value = h->fuse1;
+  else if (k == "fused_far") *value = h->fuse2;
   else if (k == "dynamic_schedule") *value = h->dynamic_schedule;
   else if (k == "guard_violations") *value = (double)guard_violations();
   else if (k == "grid") *value = h->grid1;

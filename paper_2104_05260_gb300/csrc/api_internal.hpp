@@ -93,9 +93,12 @@ struct hsma_ctx {
   int tuned_chunks = 0;
   int part_chunks_min = 0;   // d_part holds at least this many chunks
   // pair launches: chunk partials summed inside the launch by the last CTA of
-  // each tile (fused_reduce), items taken from a counter (dynamic_schedule)
+  // each tile (fused_reduce: 0 never, 1 where it pays, 2 always), items taken
+  // from a counter (dynamic_schedule); fuse1 / fuse2: the choice for the
+  // near/check and the far launch of the current plan
   int fused_reduce = 1;
   int dynamic_schedule = 1;
+  bool fuse1 = false, fuse2 = false;
   // tree evaluation work counts (option tree_count): M2P evaluations and FP32
   // direct pairs of the last evaluation
   int tree_count = 0;

@@ -475,7 +475,7 @@ def test_fused_reduction_and_dynamic_schedule_change_nothing(P, prec, tpt):
     x, q = workloads.electrolyte(c)
     for chunks in (1, 5, 13):
         ref = None
-        for fused in (0, 1):
+        for fused in (0, 1, 2):                     # never, where it pays, always
             for dyn in (0, 1):
                 opt = dict(chunks=chunks, fused_reduce=fused, dynamic_schedule=dyn)
                 if prec:
@@ -484,6 +484,8 @@ def test_fused_reduction_and_dynamic_schedule_change_nothing(P, prec, tpt):
                 E, F, pot = h.eval(x, q, potential=True)
                 E2, F2, _ = h.eval(x, q)            # the counters were left at zero
                 assert h.info("fused_reduce") == fused and h.info("dynamic_schedule") == dyn
+                if fused != 1:
+                    assert h.info("fused_near") == (fused == 2) and h.info("fused_far") == (fused == 2)
                 h.close()
                 assert E == E2 and np.array_equal(F, F2)
                 if ref is None:
