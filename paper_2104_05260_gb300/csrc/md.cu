@@ -266,27 +266,51 @@ __global__ void __launch_bounds__(kMdThreads) k_md_finish(MdArgs a, int nblk_k, 
 
 // RDF pair counts: hist[kind * bins + b], kind 0 = (+, -), 1 = (+, +),
 // 2 = (-, -); all pairs i < j, minimum image
+// Pair counts for the RDF: one warp per particle i, its lanes over j > i.
+// The minimum image multiplies by 1/L (a division per pair is a long
+// sequence on the FP64 pipe); the quotient can differ from dx / L in its
+// last bit only where it rounds at a half-integer, i.e. |dx| near L/2, and
+// such a pair lies at r >= L/2 >= rdf_rmax either way, so the counts are
+// those of the division.  Counts go to a per-block histogram in shared
+// memory when it fits (kRdfSmemBins bins), then once per bin to the global
+// one; integer sums, so the order does not matter.
+constexpr int kRdfSmemBins = 4096;
+
 __global__ void __launch_bounds__(kMdThreads) k_md_rdf(MdArgs a) {
-  const int i = blockIdx.x * kMdThreads + threadIdx.x;
-  if (i >= a.N) return;
-  const double qi = a.q[i];
-  if (qi == 0.0) return;
-  const double xi = a.x[3 * (size_t)i], yi = a.x[3 * (size_t)i + 1], zi = a.x[3 * (size_t)i + 2];
-  const double rmax2 = a.rdf_rmax * a.rdf_rmax;
-  const double scale = a.rdf_bins / a.rdf_rmax;
-  for (int j = i + 1; j < a.N; ++j) {
-    const double qj = a.q[j];
-    if (qj == 0.0) continue;
-    double dx = a.x[3 * (size_t)j] - xi, dy = a.x[3 * (size_t)j + 1] - yi, dz = a.x[3 * (size_t)j + 2] - zi;
-    dx -= a.L[0] * rint(dx / a.L[0]);
-    dy -= a.L[1] * rint(dy / a.L[1]);
-    if (!a.slab) dz -= a.L[2] * rint(dz / a.L[2]);
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 < rmax2) {
-      const int b = min(a.rdf_bins - 1, (int)(sqrt(r2) * scale));
-      const int kind = (qi > 0.0) != (qj > 0.0) ? 0 : (qi > 0.0 ? 1 : 2);
-      atomicAdd(&a.rdf[kind * a.rdf_bins + b], 1ULL);
+  extern __shared__ unsigned int rdf_local[];   // 3 x rdf_bins when local
+  const bool local = a.rdf_bins <= kRdfSmemBins;
+  if (local) {
+    for (int k = threadIdx.x; k < 3 * a.rdf_bins; k += blockDim.x) rdf_local[k] = 0u;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kLjWarps + (threadIdx.x >> 5);
+  const double qi = i < a.N ? a.q[i] : 0.0;
+  if (qi != 0.0) {
+    const double xi = a.x[3 * (size_t)i], yi = a.x[3 * (size_t)i + 1], zi = a.x[3 * (size_t)i + 2];
+    const double rmax2 = a.rdf_rmax * a.rdf_rmax;
+    const double scale = a.rdf_bins / a.rdf_rmax;
+    const double ix = 1.0 / a.L[0], iy = 1.0 / a.L[1], iz = 1.0 / a.L[2];
+    for (int j = i + 1 + lane; j < a.N; j += 32) {
+      const double qj = a.q[j];
+      if (qj == 0.0) continue;
+      double dx = a.x[3 * (size_t)j] - xi, dy = a.x[3 * (size_t)j + 1] - yi, dz = a.x[3 * (size_t)j + 2] - zi;
+      dx -= a.L[0] * rint(dx * ix);
+      dy -= a.L[1] * rint(dy * iy);
+      if (!a.slab) dz -= a.L[2] * rint(dz * iz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < rmax2) {
+        const int b = min(a.rdf_bins - 1, (int)(sqrt(r2) * scale));
+        const int kind = (qi > 0.0) != (qj > 0.0) ? 0 : (qi > 0.0 ? 1 : 2);
+        if (local) atomicAdd(&rdf_local[kind * a.rdf_bins + b], 1u);
+        else atomicAdd(&a.rdf[kind * a.rdf_bins + b], 1ULL);
+      }
     }
+  }
+  if (local) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * a.rdf_bins; k += blockDim.x)
+      if (rdf_local[k]) atomicAdd(&a.rdf[k], (unsigned long long)rdf_local[k]);
   }
 }
 
@@ -333,7 +357,8 @@ cudaError_t md_launch_start(const MdArgs& a, cudaStream_t s) {
 }
 
 cudaError_t md_launch_rdf(const MdArgs& a, cudaStream_t s) {
-  k_md_rdf<<<blocks(a.N), kMdThreads, 0, s>>>(a);
+  const size_t smem = a.rdf_bins <= kRdfSmemBins ? (size_t)3 * a.rdf_bins * sizeof(unsigned int) : 0;
+  k_md_rdf<<<(a.N + kLjWarps - 1) / kLjWarps, kMdThreads, smem, s>>>(a);
   if (a.slab) k_md_zhist<<<blocks(a.N), kMdThreads, 0, s>>>(a);
   k_md_rdf_count<<<1, 1, 0, s>>>(a);
   return cudaGetLastError();
