@@ -215,8 +215,8 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
     arrival, host clock; after one untimed pass over the stream, so that the
     slot buffers are at their steady sizes) and the one-at-a-time FP64 and FP32 forms on a
     stratified sample, extrapolated to the whole stream; then the served
-    capacity, with all requests submitted at once (the second of two such
-    passes, once slot buffers have grown to their steady sizes).
+    capacity, with all requests submitted at once (the median of three such
+    passes, after one that lets the slot buffers grow to their steady sizes).
     """
     shapes = workloads.serving_stream(n_req, seed=seed)
     reqs = []
@@ -306,20 +306,23 @@ def serve_bench(P, n_req=512, slots=16, budget=40e9, seed=4, n_sample=32, log=No
         t = P.hsma_submit(server, x, q, c.box, c.p, c.M)
         while P.hsma_poll(server, t, c.N) is None:
             pass
-    # two passes over the stream: the first lets the slots' buffers grow to
+    # four passes over the stream: the first lets the slots' buffers grow to
     # their steady-state sizes (as the one-at-a-time handles are warmed up),
-    # the second is timed; results are collected in submission order, and
-    # each poll also advances the server
-    for timed in (False, True):
+    # the other three are timed and the median pass is reported (one pass is
+    # under a second); results are collected in submission order, and each
+    # poll also advances the server
+    passes = []
+    for rep in range(4):
         g0 = P.hsma_get_info(server, "gpu_ms")
         t_sat = time.perf_counter()
         sat_tickets = [P.hsma_submit(server, x, q, c.box, c.p, c.M) for c, x, q in reqs]
         for i in range(n_req):
             while P.hsma_poll(server, sat_tickets[i], reqs[i][0].N, out=fbuf[i]) is None:
                 pass
-        sat_span = time.perf_counter() - t_sat
-        sat_gpu_s = (P.hsma_get_info(server, "gpu_ms") - g0) / 1e3
+        if rep > 0:
+            passes.append((time.perf_counter() - t_sat, (P.hsma_get_info(server, "gpu_ms") - g0) / 1e3))
     P.hsma_destroy(server)
+    sat_span, sat_gpu_s = sorted(passes)[len(passes) // 2]
     de = [abs(out[i][0] - r64[i][1]) / abs(r64[i][1]) for i in sample]
     # the same error against the energy scale 1/2 sum |q_i Phi_i| (|E| itself can
     # nearly cancel in a random neutral configuration)
