@@ -1071,9 +1071,10 @@ def main():
     e2e_s = float(np.median(e2e_t))
     e2e_s = max_over_ranks(dist, e2e_s, dev)
 
-    # the plain FP64 GPU form, for the record
+    # the plain FP64 GPU form, for the record (one GPU only: with several,
+    # every rank would repeat the same single-GPU figure)
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and ws == 1:
         h64 = P.HSMA(c.box, c.dims, c.p, c.M, c.gammas[0], c.gammas[1], precision=0, timing=1,
                      dtn_grid=c.dtn_grid)
         P.hsma_set_stream(h64.h, stream.cuda_stream)
@@ -1131,7 +1132,11 @@ def main():
                     "d2h_bytes_per_step": N * 24 + 8},
             "gpu_launches": int(P.hsma_get_info(h.h, "kernels_per_eval")) * args.steps, "clocks": clk.summary(),
             "fp64_path": fp64}
-    if not args.no_cpu_baseline:
+    # the oracle baseline, the other workloads and the served stream are
+    # single-GPU figures: taken at N = 1 only, so that a run on several GPUs
+    # holds them no longer than its timed region needs
+    single = ws == 1
+    if not args.no_cpu_baseline and single:
         n_s = 512
         t_full, d = oracle_sample(c, x, q, n_s)
         Fg = fd.cpu().numpy()[d["idx"]]
@@ -1148,7 +1153,7 @@ def main():
             "max_ion_force_err_over_rms": float(np.sqrt(np.sum((Fg - Fo) ** 2, 1)).max()
                                                 / math.sqrt(np.mean(np.sum(Fo ** 2, 1)))),
             "rel_energy_vs_fp64_gpu": fp64["fp32_vs_fp64_rel_energy"] if fp64 else None}
-    if not args.no_other_cases:
+    if not args.no_other_cases and single:
         if args.case != 2:
             line["case2"] = secondary_case(P, torch, dev, stream, workloads.case(2), peak_instr, mhz_txt, sms)
         line["case3_2d"] = secondary_case(P, torch, dev, stream, workloads.case(3, 0.95), peak_instr, mhz_txt,
@@ -1176,7 +1181,7 @@ def main():
             h2b.close()
         line["other_cases"] = other_cases(P, torch, dev, stream, peak_instr)
         line["paper_like"] = paper_like(P, torch, dev, stream)
-    if not args.no_serve:
+    if not args.no_serve and single:
         # last, so that the end of the line (what a log tail keeps) shows them
         line["serve"] = serve_bench(P)
         line["serve_precision2"] = serve_bench(P, precision=2)
