@@ -330,7 +330,7 @@ static int plan_tree(hsma_ctx* h, size_t n, size_t nt, size_t simg) {
   size_t off = 0;
   for (int l = 0; l < 8; ++l) {
     t.moff[l] = (int)off;
-    if (l >= 2 && l <= L) off += ((size_t)1 << (3 * l)) * nc;
+    if (l >= 2 && l <= L) off += ((size_t)1 << (3 * l)) * tree_paired_floats(P);
   }
   std::vector<float> norm(nc), fac(nc);
   for (int nn = 0; nn <= P; ++nn)

@@ -155,6 +155,8 @@ struct TreeLaunch {
 };
 cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s);
 size_t tree_eval_smem(int P);
+// floats of one cell's multipole in the evaluation's paired layout
+int tree_paired_floats(int P);
 int tree_max_order();
 int tree_sm_count();
 

@@ -284,15 +284,29 @@ __global__ void __launch_bounds__(kP2mThreads) k_tree_p2m(TreeArgs t, int l, int
   }
 }
 
-// M[cell][k] = sum over the cell's items (contiguous in Morton order) of part
-__global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_cell, int n_cells, int nc,
+// Multipoles are stored in rows n = 0..P of 2n + 2 floats starting at
+// n (n + 1): the cos coefficient of m = 0, one unused slot, then the (cos,
+// sin) pair of each m = 1..n, so that the evaluation reads a pair with one
+// 8-byte load.  Slot of the harmonic index k = n^2 + n +- m:
+__device__ __forceinline__ int paired_slot(int k) {
+  int n = (int)sqrtf((float)k);
+  while ((n + 1) * (n + 1) <= k) ++n;
+  while (n * n > k) --n;
+  const int off = k - n * n - n;   // +m (cos) or -m (sin)
+  const int m = off < 0 ? -off : off;
+  return n * (n + 1) + (m == 0 ? 0 : 2 * m + (off < 0 ? 1 : 0));
+}
+
+// M[cell][paired_slot(k)] = sum over the cell's items (contiguous in Morton
+// order) of part[.][k]; ncp = (P + 1)(P + 2) floats a cell
+__global__ void k_tree_m_reduce(const double* __restrict__ part, int items_per_cell, int n_cells, int nc, int ncp,
                                 float* __restrict__ M) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cells * nc) return;
   const int c = i / nc, k = i - c * nc;
   double s = 0.0;
   for (int j = 0; j < items_per_cell; ++j) s += part[((size_t)c * items_per_cell + j) * nc + k];
-  M[i] = (float)s;
+  M[(size_t)c * ncp + paired_slot(k)] = (float)s;
 }
 
 // ---------------------------------------------------------------- M2P + P2P
@@ -362,16 +376,20 @@ __device__ __forceinline__ void m2p_accumulate(const float* __restrict__ Mc, flo
         u2 = u1; z2 = z1; q2 = q1;
         u1 = u; z1 = uz; q1 = uq;
       }
-      const int base = n * n + n;
-      const float ac = Mc[base + m];
-      uc += u * ac;
-      qc += uq * ac;
-      zc += uz * ac;
-      if (m > 0) {
-        const float as = Mc[base - m];
-        us += u * as;
-        qs += uq * as;
-        zs += uz * as;
+      const int row = n * (n + 1);   // paired layout (see k_tree_m_reduce)
+      if (m == 0) {
+        const float ac = Mc[row];
+        uc += u * ac;
+        qc += uq * ac;
+        zc += uz * ac;
+      } else {
+        const float2 a = *reinterpret_cast<const float2*>(Mc + row + 2 * m);
+        uc += u * a.x;
+        qc += uq * a.x;
+        zc += uz * a.x;
+        us += u * a.y;
+        qs += uq * a.y;
+        zs += uz * a.y;
       }
     }
     if (m == 0) {
@@ -455,7 +473,7 @@ __global__ void __launch_bounds__(kTreeThreads, tree_eval_blocks(P)) k_tree_eval
   // the queue, compacts each level's list itself and stages multipoles in its
   // own slice of shared memory.
   extern __shared__ __align__(16) float tree_smem[];
-  constexpr int nc = (P + 1) * (P + 1);
+  constexpr int nc = (P + 1) * (P + 2);   // floats a cell (paired layout)
   constexpr int nc4 = (nc + 3) & ~3;
   constexpr int kWarps = kTreeThreads / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -696,8 +714,10 @@ __global__ void __launch_bounds__(kTreeThreads, tree_eval_blocks(P)) k_tree_eval
   }
 }
 
+int tree_paired_floats(int P) { return (P + 1) * (P + 2); }
+
 size_t tree_eval_smem(int P) {
-  const int nc4 = ((P + 1) * (P + 1) + 3) & ~3;
+  const int nc4 = ((P + 1) * (P + 2) + 3) & ~3;
   const int warps = kTreeThreads / 32;
   return (size_t)warps * kBatch * nc4 * 4 + kTreeThreads * 16 + kTreeThreads * 4 + (size_t)warps * 216 * 4;
 }
@@ -753,7 +773,8 @@ cudaError_t launch_tree(const TreeLaunch& T, cudaStream_t s) {
 #undef HSMA_TREE_P2M
     const int cells = 1 << (3 * l);
     const int per = items / cells;
-    k_tree_m_reduce<<<(cells * nc + 255) / 256, 256, 0, s>>>(T.part, per, cells, nc, T.M + t.moff[l]);
+    k_tree_m_reduce<<<(cells * nc + 255) / 256, 256, 0, s>>>(T.part, per, cells, nc, tree_paired_floats(t.P),
+                                                              T.M + t.moff[l]);
   }
   // tasks per cell of level L-1 (the cursors are free again after the fills)
   const int n_cells = nleaf / 8;
