@@ -121,10 +121,9 @@ int hsma_create(const double box[3], int dims, int p, int M,
  *                       shared memory) for precision 2; turns autotune off.
  *   "graphs"            1 (default) = replay the per-evaluation pipeline as a
  *                       CUDA graph captured on the first evaluation of each N.
- *   "tree_far_order"    1 (default) = listed cells whose centre lies at
- *                       least sqrt(8) cell widths from the target's cell (at
- *                       the leaf level: from every leaf of the target's
- *                       parent cell) are evaluated to order P - 4 (for
+ *   "tree_far_order"    1 (default) = above the leaf level, listed cells whose
+ *                       centre lies at least sqrt(8) cell widths from the
+ *                       target's cell are evaluated to order P - 4 (for
  *                       tree_order >= 8): their truncation bound stays well
  *                       below that of the nearest listed cells at order P.
  *                       0 = every cell to order P.

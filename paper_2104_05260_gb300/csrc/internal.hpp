@@ -118,9 +118,9 @@ struct TreeArgs {
   const float* norm;     // (P+1)^2: c_n0, sqrt(2) c_nm (2m-1)!! at n*(P+1) + m
   const float* fac;      // (P+1)^2: 4 pi/(2n+1) * norm^2 at k = n^2 + n + m
   int direct_leaf;       // 1: the leaf level is summed directly (no leaf multipoles)
-  // A listed cell whose centre lies at least sqrt(far_d2) cell widths from
-  // the target's cell (at the leaf level: from the nearest child of G) is
-  // evaluated to order P - 4 instead of P (P >= 8); 0 = every cell to order P.
+  // Above the leaf level, a listed cell whose centre lies at least
+  // sqrt(far_d2) cell widths from the target's cell is evaluated to order
+  // P - 4 instead of P (P >= 8); 0 = every cell to order P.
   int far_d2;
 };
 struct TreeLaunch {

@@ -571,22 +571,10 @@ __global__ void __launch_bounds__(kTreeThreads, tree_eval_blocks(P)) k_tree_eval
             const float dx = (p.x - (-t.Rs + (ox + 0.5f) * w)) * inv_w;
             const float dy = (p.y - (-t.Rs + (oy + 0.5f) * w)) * inv_w;
             const float dz = (p.z - (-t.Rs + (oz + 0.5f) * w)) * inv_w;
-            // the order follows the distance in cell widths from the target's
-            // cell, taken the same for every lane so that the choice does not
-            // diverge: above the leaf level the lanes share that cell (G's
-            // ancestor); at the leaf level each lane's leaf is a child of G,
-            // so the distance from the nearest child of G bounds every lane's
-            int ex, ey, ez;
-            if (l < t.L) {
-              ex = ox - cx;
-              ey = oy - cy;
-              ez = oz - cz;
-            } else {
-              ex = ox < 2 * gx0 ? 2 * gx0 - ox : (ox > 2 * gx0 + 1 ? ox - 2 * gx0 - 1 : 0);
-              ey = oy < 2 * gy0 ? 2 * gy0 - oy : (oy > 2 * gy0 + 1 ? oy - 2 * gy0 - 1 : 0);
-              ez = oz < 2 * gz0 ? 2 * gz0 - oz : (oz > 2 * gz0 + 1 ? oz - 2 * gz0 - 1 : 0);
-            }
-            const bool far = PL < P && t.far_d2 > 0 && ex * ex + ey * ey + ez * ez >= t.far_d2;
+            // the same cell for every lane (levels above the leaf level are
+            // listed for G's ancestor), so the choice does not diverge
+            const int ex = ox - cx, ey = oy - cy, ez = oz - cz;
+            const bool far = PL < P && t.far_d2 > 0 && l < t.L && ex * ex + ey * ey + ez * ez >= t.far_d2;
             if (COUNT) {
               if (far) ++n_m2p_low;
               else ++n_m2p;

@@ -208,9 +208,8 @@ def test_tree_work_counts(P):
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_tree_far_cells_at_lower_order(P, mode):
-    # option tree_far_order: listed cells at least sqrt(8) cell widths away
-    # (at the leaf level, from every leaf of the target's parent cell) are
-    # evaluated to order P - 4.  Both settings
+    # option tree_far_order: above the leaf level, listed cells at least
+    # sqrt(8) cell widths away are evaluated to order P - 4.  Both settings
     # meet the oracle bounds, the split shows in the counted work, and the
     # lower order costs no more than the FP32 rounding of the pair sums
     c = workloads.small_case(4000, dims=3, box=(20.0, 20.0, 20.0), p=6, M=800, seed=8)
