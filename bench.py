@@ -1136,6 +1136,12 @@ def main():
     # single-GPU figures: taken at N = 1 only, so that a run on several GPUs
     # holds them no longer than its timed region needs
     single = ws == 1
+    # the served stream first among the single-GPU extras, while the process
+    # holds only the main handle (its host-driven loop is sensitive to what
+    # ran before it on the host); reported at the end of the line
+    serve_res = None
+    if not args.no_serve and single:
+        serve_res = (serve_bench(P), serve_bench(P, precision=2))
     if not args.no_cpu_baseline and single:
         n_s = 512
         t_full, d = oracle_sample(c, x, q, n_s)
@@ -1181,10 +1187,9 @@ def main():
             h2b.close()
         line["other_cases"] = other_cases(P, torch, dev, stream, peak_instr)
         line["paper_like"] = paper_like(P, torch, dev, stream)
-    if not args.no_serve and single:
+    if serve_res:
         # last, so that the end of the line (what a log tail keeps) shows them
-        line["serve"] = serve_bench(P)
-        line["serve_precision2"] = serve_bench(P, precision=2)
+        line["serve"], line["serve_precision2"] = serve_res
         line["serve_summary"] = {
             f"precision{k}": {key: round(float(line[name][key]), 4) for key in
                               ("evals_per_s", "p50_ms", "p99_ms", "one_at_a_time_evals_per_s",
