@@ -96,6 +96,42 @@ def test_tree_is_repeatable_and_matches_dense_at_bench_size(P):
     assert abs(E1 - Ed) <= 1e-5 * abs(Ed)
 
 
+def test_tree_at_the_largest_workload(P):
+    # N = 262,144, p = 10, M = 4000 (leaf multipoles at this density): against
+    # the dense path over every ion, and against the oracle on sampled ions
+    # with every sampled ion's force within the per-ion bound
+    c = workloads.case(5)
+    x, q = workloads.electrolyte(c)
+    E, F, pot, L = run(P, c, x, q)
+    assert L == 5
+    h = P.HSMA(c.box, 3, c.p, c.M, precision=1)
+    Ed, Fd, _ = h.eval(x, q)
+    h.close()
+    assert frms(F, Fd) <= 2e-5 and abs(E - Ed) <= 1e-5 * abs(Ed)
+    assert fmax(F, Fd) <= FMAX * 2e-5
+    # sampled ions with no neighbour closer than 0.8: at this size the FP32
+    # pair arithmetic itself (box-centred coordinates up to |x| = 69, about
+    # 4e-6 absolute) errs above the FP32 bound for a closer pair, tree or not
+    rng = np.random.default_rng(321)
+    cand = rng.choice(c.N, 64, replace=False)
+    box = np.asarray(c.box)
+    keep = []
+    for i in cand:
+        d = x - x[i]
+        d -= box * np.round(d / box)
+        r2 = np.sum(d * d, 1)
+        r2[i] = np.inf
+        if r2.min() >= 0.64:
+            keep.append(i)
+    idx = np.sort(np.array(keep[:16]))
+    assert len(idx) == 16
+    st = O.make_setup(c.box, 3, c.p, c.M, lam=c.lam)
+    ref = O.evaluate(st, x, q, targets=idx)
+    assert frms(F[idx], ref["forces"]) <= 2e-5
+    assert fmax(F[idx], ref["forces"]) <= FMAX * 2e-5
+    assert pmax(pot[idx], ref["phi"]) <= FMAX * 2e-5
+
+
 def test_tree_rejects_fp64_and_bad_order(P):
     c = workloads.case(1)
     x, q = workloads.electrolyte(c)
