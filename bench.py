@@ -1140,6 +1140,7 @@ def main():
     # holds only the main handle (its host-driven loop is sensitive to what
     # ran before it on the host); reported at the end of the line
     serve_res = None
+    h.close()     # the large system's buffers are not needed beyond this point
     if not args.no_serve and single:
         serve_res = (serve_bench(P), serve_bench(P, precision=2))
     if not args.no_cpu_baseline and single:
