@@ -788,9 +788,10 @@ M2P_OPS_PER_TERM = 17     # FP32 operations per (n, m >= 0) term of a multipole 
 def tree_roofline(P, h, xd, qd, N, e, f, near_ms, order, peak_instr):
     """FP32 issue-rate roofline of the tree evaluation of the near field and
     check points: one extra evaluation with the counting kernel gives the
-    multipole evaluations (M2P) and FP32 direct pairs it performs; the
-    algorithmic work is M2P x (P+1)(P+2)/2 terms x 17 + pairs x 13 FP32
-    operations, over the evaluation kernel's CUDA-event time (h must have
+    multipole evaluations (M2P) at each order and the FP32 direct pairs it
+    performs; the algorithmic work is (M2P x (P+1)(P+2)/2 + far-cell M2P x
+    (P-3)(P-2)/2) terms x 17 + pairs x 13 FP32 operations (far cells are
+    evaluated to order P - 4), over the evaluation kernel's CUDA-event time (h must have
     option timing = 1); the whole near stage (binning and multipoles too) is
     given beside it."""
     import torch
