@@ -51,7 +51,9 @@ extern "C" {
 #define HSMA_PENDING          1
 #define HSMA_ERR_ARG        (-1)  /* bad argument: p outside 1..40, M < (p+1)^2 or
                                      M (p+1)^2 > 2^31, |gamma| > 1,
-                                     N < 1, dims not 2 or 3, box <= 0, NULL pointer,
+                                     N < 1 or N > 2^28, N times the image shifts
+                                     at or above 2^31 (device indices are 32-bit),
+                                     dims not 2 or 3, box <= 0, NULL pointer,
                                      unknown option or ticket */
 #define HSMA_ERR_NOT_NEUTRAL (-2) /* |sum q| > 1e-10 sum |q| */
 #define HSMA_ERR_OUT_OF_SLAB (-3) /* 2D: some z not strictly inside (0, Lz) */

@@ -452,6 +452,11 @@ static bool use_fused(const hsma_ctx* h, int n_chunks, int tile_targets, double 
 int ensure_plan(hsma_ctx* h, int64_t N) {
   if (h->plan_N == N) return HSMA_OK;
   const Geometry& g = h->geo;
+  // image and target indices are 32-bit on the device: every image of the
+  // shift table (the most B can hold) and every target must stay below 2^31
+  if ((double)N * (double)g.shifts.size() + (double)g.n_check >= 2147483647.0)
+    return fail(h, HSMA_ERR_ARG, "N = " + std::to_string(N) + " times " + std::to_string(g.shifts.size()) +
+                                     " image shifts exceeds the 32-bit index range");
   const int prec = h->precision;
   const int tpt = eff_tpt(h);
   const int tile = pair_tile_targets(prec, tpt);
