@@ -1,5 +1,7 @@
 """The seeded input generators: sizes, neutrality, determinism and the
 hard-core (paper-like) variant's minimum distance."""
+import math
+
 import numpy as np
 import pytest
 
@@ -45,3 +47,21 @@ def test_hard_core_variant(dims):
     # the uniform draw of the same case has closer pairs
     x0, _ = workloads.electrolyte(c, margin=0.4)
     assert min_image_dist(x0, box, (True, True, dims == 3)) < 0.8
+
+
+def test_serving_stream_recipe():
+    # 512 requests: N log-uniform in [1e3, 5e4] and even, p in {6, 8, 10},
+    # M = 4 p^2 + 400, cubic boxes at density 0.1; seeded and repeatable
+    s = workloads.serving_stream(512, seed=4)
+    assert s == workloads.serving_stream(512, seed=4)
+    N = np.array([r["N"] for r in s])
+    assert len(s) == 512 and np.all(N % 2 == 0) and N.min() >= 1000 and N.max() <= 50000
+    # log-uniform: about half the requests below the geometric mean sqrt(5e7)
+    assert 0.4 < np.mean(N < math.sqrt(1000 * 50000)) < 0.6
+    assert {r["p"] for r in s} == {6, 8, 10}
+    assert all(r["M"] == 4 * r["p"] ** 2 + 400 for r in s)
+    for r in s:
+        L = np.asarray(r["box"])
+        assert np.allclose(L, L[0]) and abs(r["N"] / L.prod() - 0.1) < 1e-9
+    t = workloads.poisson_arrivals(512, 100.0, seed=4)
+    assert np.all(np.diff(t) > 0) and abs(np.mean(np.diff(t)) - 0.01) < 0.002
