@@ -1,4 +1,4 @@
-"""Host logic of bench.py's DRAM-traffic records: parsing an ncu CSV of
+"""Host logic of bench.py's DRAM-traffic records and roofline: parsing an ncu CSV of
 several launches, picking the near-field launch, and keeping one record per
 (kernel, chunk count).  No GPU: the CSV is written here in ncu's layout."""
 import csv
@@ -70,3 +70,38 @@ def test_committed_records_are_well_formed():
     for r in recs:
         assert r["bytes_per_launch"] == r["read_bytes"] + r["write_bytes"] > 0
         assert r["command"].startswith("ncu ") and "--clock-control none" in r["command"]
+
+
+class _FakeLib:
+    """Stands in for the binding: the plan's info keys of one handle."""
+
+    def __init__(self, info):
+        self.info = info
+
+    def hsma_get_info(self, h, key):
+        return self.info[key]
+
+
+class _FakeHandle:
+    h = object()
+
+
+def test_pair_roofline_arithmetic_and_traffic_record():
+    # 13 FP32-pipe operations per pair over the launch time, against the
+    # issue peak; the traffic record of the same (workload, kernel, chunks)
+    # and kernel source is attached, any other plan reports null
+    import workloads
+    c = workloads.case(5)
+    rec = next(r for r in bench.traffic_records() if r["workload"] == c.name
+               and r["kernel"].startswith("k_pair_f32x2s<2>"))
+    P = _FakeLib({"kernel": 24, "chunks": rec["chunks"], "grid": 456, "tile_targets": 1024})
+    pairs, near_ms, peak = 4.115e11, 167.0, 40.27392
+    roof, plan = bench.pair_roofline(P, _FakeHandle(), c, pairs, near_ms, peak, "2070 MHz", 152)
+    assert plan["kernel"] == "k_pair_f32x2s<2>" and plan["chunks"] == rec["chunks"]
+    assert abs(roof["achieved"] - pairs * 13 / (near_ms / 1e3) / 1e12) < 1e-9
+    assert abs(roof["frac"] - roof["achieved"] / peak) < 1e-12
+    if rec.get("pair_sources_sha1") == bench.pair_sources_sha1():
+        assert roof["traffic"] == rec["bytes_per_launch"]
+    P2 = _FakeLib({"kernel": 24, "chunks": 9999, "grid": 456, "tile_targets": 1024})
+    roof2, _ = bench.pair_roofline(P2, _FakeHandle(), c, pairs, near_ms, peak, "2070 MHz", 152)
+    assert roof2["traffic"] is None
