@@ -1,6 +1,8 @@
-"""Host logic of bench.py's DRAM-traffic records and roofline: parsing an ncu CSV of
-several launches, picking the near-field launch, and keeping one record per
-(kernel, chunk count).  No GPU: the CSV is written here in ncu's layout."""
+"""Host logic of bench.py: the DRAM-traffic records (parsing an ncu CSV of
+several launches, picking the near-field launch, keeping one record per
+kernel and chunk count), the pair roofline's arithmetic, and the timed oracle
+sample behind the CPU baseline.  No GPU: the CSV is written here in ncu's
+layout and the binding is faked."""
 import csv
 import json
 import os
@@ -105,3 +107,22 @@ def test_pair_roofline_arithmetic_and_traffic_record():
     P2 = _FakeLib({"kernel": 24, "chunks": 9999, "grid": 456, "tile_targets": 1024})
     roof2, _ = bench.pair_roofline(P2, _FakeHandle(), c, pairs, near_ms, peak, "2070 MHz", 152)
     assert roof2["traffic"] is None
+
+
+def test_oracle_sample_reproduces_the_oracle():
+    # the bench's timed oracle sample (pair sums split over host threads) gives
+    # the oracle's own forces and potentials on its sampled ions: the
+    # reference of the bench's accuracy_vs_oracle figure
+    import numpy as np
+    import workloads
+    from oracle import hsma as O
+    c = workloads.case(1)
+    x, q = workloads.electrolyte(c)
+    _, d = bench.oracle_sample(c, x, q, 48, threads=3)
+    st = O.make_setup(c.box, c.dims, c.p, c.M, lam=c.lam)
+    ref = O.evaluate(st, x, q, targets=d["idx"])
+    scale = np.sqrt(np.mean(np.sum(ref["forces"] ** 2, 1)))
+    assert np.abs(d["F"] - ref["forces"]).max() <= 1e-12 * scale
+    dphi = d["phi"] - ref["phi"]
+    assert np.abs(dphi - dphi.mean()).max() <= 1e-12 * np.abs(ref["phi"]).max()
+    assert d["Ns"] == ref["Ns"] and d["threads"] == 3
